@@ -1,0 +1,367 @@
+#!/usr/bin/env python
+"""Benchmark of the Chebyshev random-probe tight-binding path on GB300.
+
+One step = the whole path on one synthetic workload: neighbour list, H assembly, Lanczos
+spectral bounds, Chebyshev moments with random probes, chemical potential and Omega / E / N,
+then the adjoint (sampled density matrix dOmega/dH on the pattern) and the atomic forces.
+
+Default workload: a 10,000-atom copper-like fcc sphere (9-orbital Slater-Koster model, 4.0 A
+cutoff, 90,000 orbitals), kT = 0.025 eV, 11 electrons/atom, 512 Rademacher probes, FP32
+recurrence with FP64 moments; the number of Chebyshev terms p follows the error model
+exp(-6.4 p kT / W) of Sec. II.B.1 with eps = 1e-7.
+
+Metric: atom*vector*Chebyshev-steps/s = N_atoms * probes * p / (time of one full step, energies
+and forces).  `roofline` reports the fused recurrence kernel (cheb_step_kernel) against the
+measured HBM copy bandwidth; `cpu_baseline` times the FP64 oracle on a bounded sub-cluster.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun (N > 1) every rank runs an independent replica (replicas only: the path has no
+exchange step), value = units of all ranks / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as wl  # noqa: E402
+
+METRIC = "atom*vector*Chebyshev-steps/s"
+UNIT = "atom*vector*steps/s"
+
+
+def make_workload(name: str, rank: int = 0):
+    if name == "fcc10k":
+        return wl.fcc_cu(10000, kT=0.025, n_probes=512, seed=5264, probe_seed=52640 + rank)
+    if name == "fcc1k":
+        return wl.fcc_cu(1000, kT=0.5, n_probes=256, seed=5264, probe_seed=52640 + rank)
+    if name == "sc1k":
+        return wl.sc_disorder(L=10, probe_seed=18120 + rank)
+    if name == "sc9-48":
+        return wl.sc9_periodic(L=48, probe_seed=48480 + rank)
+    raise SystemExit(f"unknown workload {name}")
+
+
+def order_rule(W: float, kT: float) -> int:
+    return max(64, int(math.ceil((W / kT) * math.log(1e7) / 6.4)))
+
+
+# ---------------------------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines: list[str] = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.device)], stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------------------------
+# oracle timing (cpu_baseline and the reference arm)
+# ---------------------------------------------------------------------------------------------
+
+SAMPLE_ATOMS = 400
+
+
+def oracle_sample(wk_full, n_atoms: int = SAMPLE_ATOMS):
+    """The same model, kT, probes and electron density on the first n_atoms of the cluster."""
+    wk = wl.fcc_cu(n_atoms, kT=wk_full.kT, n_probes=wk_full.n_probes, seed=5264,
+                   probe_seed=wk_full.probe_seed) if wk_full.sk_V is not None else None
+    return wk
+
+
+def oracle_step(wk):
+    """Exact estimator energies + forces for wk by the oracle (dense FP64); returns (units, s)."""
+    from oracle import chebyshev as och, hamiltonian as oham, neighbors as onb, physics as oph
+    t0 = time.perf_counter()
+    rp, col = onb.neighbor_csr(wk.positions, wk.cutoff, wk.box)
+    H = oham.dense_sk(wk.positions, rp, col, wk.sk_V, wl.SK_R0, wl.SK_DECAY, wl.SK_ONSITE, wk.box)
+    w, V = np.linalg.eigh(H)
+    W = w.max() - w.min()
+    emin, emax = w.min() - 0.01 * W, w.max() + 0.01 * W
+    p = order_rule(emax - emin, wk.kT)
+    R = och.probes(H.shape[0], wk.n_probes, wk.probe_seed)
+    mom = och.exact_moments(w, V, R, emin, emax, p)
+    mu = och.estimator_mu(mom, emin, emax, wk.n_electrons, wk.kT)
+    och.estimator_observables(mom, emin, emax, mu, wk.kT)
+    G = och.estimator_gradient(w, V, R, emin, emax, mu, wk.kT, p=p)
+    a, b, dH = oham.sk_bond_grads(wk.positions, rp, col, wk.sk_V, wl.SK_R0, wl.SK_DECAY, wk.box)
+    oph.forces_from_blocks(G, a, b, dH, wk.n_atoms, 9)
+    dt = time.perf_counter() - t0
+    return wk.n_atoms * wk.n_probes * p, dt, p
+
+
+def cpu_cores() -> int:
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS"):
+        if os.environ.get(k, "").isdigit():
+            return int(os.environ[k])
+    return os.cpu_count() or 1
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    wk = oracle_sample(make_workload(args.workload))
+    if wk is None:
+        print(json.dumps({"impl": "reference", "unavailable": "oracle sample defined for the fcc workloads only"}))
+        return 0
+    for _ in range(args.warmup):
+        oracle_step(wk)
+    units, tot, p = 0, 0.0, 0
+    for _ in range(args.steps):
+        u, dt, p = oracle_step(wk)
+        units += u
+        tot += dt
+    v = units / tot
+    sample = (f"FP64 oracle (dense eigh + exact estimator + Daleckii-Krein forces) on the first "
+              f"{wk.n_atoms} atoms of the same cluster, {wk.n_probes} probes, p={p}")
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": wk.name, "sample_of": args.workload},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------------------------
+
+def traffic_from_profile(kernel_file: str):
+    """Per-launch DRAM bytes of the recurrence kernel from the committed ncu summary, if it was
+    taken on the current kernel source (matching sha256 prefix); else None."""
+    import hashlib
+    src = os.path.join(ROOT, "paper_1812_05264_gb300", "csrc", "recurrence.cu")
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    path = os.path.join(ROOT, "profiles", kernel_file)
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    for ln in open(path):
+        if ":" in ln and ln.strip().startswith("- "):
+            k, v = ln.strip()[2:].split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("recurrence.cu sha256[:16]") != sha:
+        return None
+    try:
+        return float(vals["dram bytes per launch (full size)"])
+    except (KeyError, ValueError):
+        return None
+
+
+def run_ours(args, rank, world):
+    import torch
+    from paper_1812_05264_gb300 import build as _build
+    _build.build()
+    from paper_1812_05264_gb300 import api
+
+    dist = world > 1
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if dist:
+        import torch.distributed as td
+        td.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+
+    def barrier():
+        if dist:
+            torch.distributed.barrier()
+
+    wk = make_workload(args.workload, rank)
+    ctx = api.Context()
+    solver = api.Solver(wk, ctx)
+    stream = ctx.stream
+    pos_host = torch.from_numpy(np.ascontiguousarray(wk.positions)).pin_memory()
+    pos = pos_host.to(f"cuda:{local}")
+    box = solver.box
+    fp64 = not wk.mixed
+    esz = 8 if fp64 else 4
+    mom_ev = []
+
+    def step(p_dev, record=False):
+        g = api.build_neighbors(ctx, p_dev, wk.cutoff, box)
+        H = api.assemble_H(ctx, solver.model, p_dev, g, box)
+        emin, emax = api.spectral_bounds(ctx, H)
+        p = wk.order or order_rule(emax - emin, wk.kT)
+        if record:
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+        mom = api.chebyshev_moments(ctx, H, emin, emax, wk.probe_seed, wk.n_probes, p, fp64)
+        if record:
+            e1.record(stream)
+            mom_ev.append((e0, e1, p // 2, H.graph.nnzb))
+        mu, Om, E, N = api.fermi_level(ctx, mom, emin, emax, wk.n_electrons, wk.kT, wk.jackson)
+        G, F = api.density_and_forces(ctx, H, solver.model, p_dev, box, emin, emax, wk.probe_seed,
+                                      wk.n_probes, p, mu, wk.kT, wk.jackson, fp64,
+                                      want_G=not solver.model.is_sk, want_forces=solver.model.is_sk)
+        return p, (mu, Om, E, N), F
+
+    for _ in range(max(args.warmup, 0)):
+        p, _, _ = step(pos)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    launches0 = ctx.launches
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t0.record(stream)
+    for _ in range(args.steps):
+        p, obs, F = step(pos, record=True)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    launches = ctx.launches - launches0
+    barrier()
+    ms = t0.elapsed_time(t1) / args.steps
+    # end to end: positions from pinned host memory in, energies and forces back to the host
+    e_ms = []
+    h2d = pos_host.numel() * 8
+    d2h = 0
+    for _ in range(max(1, min(args.steps, 3))):
+        s0 = torch.cuda.Event(enable_timing=True)
+        s1 = torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        pos_e = pos_host.to(f"cuda:{local}", non_blocking=True)
+        p_e, obs_e, F_e = step(pos_e)
+        out = F_e.cpu() if F_e is not None else None
+        s1.record(stream)
+        torch.cuda.synchronize()
+        d2h = (out.numel() * 8 if out is not None else 0) + 4 * 8
+        e_ms.append(s0.elapsed_time(s1))
+    clk = clocks.stop()
+    if dist:
+        tt = torch.tensor([ms, statistics.median(e_ms)], dtype=torch.float64, device=f"cuda:{local}")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        ms, e_med = tt.tolist()
+    else:
+        e_med = statistics.median(e_ms)
+    units = wk.n_atoms * wk.n_probes * p
+    value = units * world / (ms / 1e3)
+    # roofline of the recurrence kernel from the moments phase of the timed steps
+    mom_ms = sum(a.elapsed_time(b) for a, b, _, _ in mom_ev)
+    launches_k = sum(k for _, _, k, _ in mom_ev)
+    nnzb = mom_ev[-1][3]
+    n_rows = wk.n_atoms * wk.n_orb
+    bytes_per_launch = 3 * n_rows * wk.n_probes * esz + nnzb * wk.n_orb ** 2 * esz
+    achieved = bytes_per_launch * launches_k / (mom_ms / 1e3) / 1e9
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if fp64 else "f32", "data": "synthetic",
+        "config": {"workload": wk.name, "n_atoms": wk.n_atoms, "orbitals": n_rows,
+                   "probes": wk.n_probes, "order_p": p, "kT": wk.kT, "nnzb": nnzb,
+                   "moments": "FP64", "recurrence": "FP64" if fp64 else "FP32",
+                   "l2": "panels (%.0f MB each) larger than L2" % (n_rows * wk.n_probes * esz / 1e6),
+                   "parallelism": f"replicas x{world}", "seeds": [5264, wk.probe_seed]},
+        "e2e": {"value": units * world / (e_med / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic_from_profile("cheb_step_fcc10000.md"),
+                     "kernel": "cheb_step_kernel", "algorithmic_bytes_per_launch": bytes_per_launch,
+                     "avg_launch_ms": mom_ms / launches_k, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"},
+        "clocks": clk,
+        "observables_per_atom": {"mu": obs[0], "Omega": obs[1] / wk.n_atoms,
+                                 "E": obs[2] / wk.n_atoms, "N": obs[3] / wk.n_atoms},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        swk = oracle_sample(wk)
+        if swk is not None:
+            u, dt, ps = oracle_step(swk)
+            line["cpu_baseline"] = {
+                "value": u / dt, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+                "sample": (f"FP64 oracle (dense eigh, exact estimator, Daleckii-Krein forces) on "
+                           f"the first {swk.n_atoms} atoms of the cluster, {swk.n_probes} probes, "
+                           f"p={ps}, {dt:.1f} s")}
+    if rank == 0:
+        print(json.dumps(line))
+    if dist:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="fcc10k")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    return run_ours(args, rank, world)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

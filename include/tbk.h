@@ -1,0 +1,197 @@
+/*
+ * tbk.h -- C ABI of libtbk, a GB300 (sm_103a) implementation of the Chebyshev random-probe
+ * path of arXiv 1812.05264 ("Assessment of localized and randomized algorithms for
+ * electronic structure"): a Chebyshev expansion of the Fermi-Dirac and free-energy functions
+ * of a block-sparse orthogonal tight-binding Hamiltonian, applied to a block of Rademacher
+ * probe vectors, giving the grand potential, band energy, electron count, the sampled
+ * density matrix on the sparsity pattern and Hellmann-Feynman forces.
+ *
+ * Conventions (all entry points):
+ *  - Every call returns a tbk_status (0 = TBK_OK).  On failure tbk_last_error() returns a
+ *    message for the calling thread; no exception, exit or trap crosses the ABI.
+ *  - "device" pointers are CUDA global-memory addresses on the context's device; "host"
+ *    pointers are ordinary CPU memory.  Inputs are owned by the caller and not retained after
+ *    the call returns; outputs go into caller-allocated buffers of the stated size.
+ *  - Work is enqueued on the context's stream.  Calls that return values in host memory
+ *    synchronise that stream before returning; the others are asynchronous.
+ *  - Energies are in the units of the model (eV for the Slater-Koster model), lengths in the
+ *    units of the positions (Angstrom).
+ *  - Block-sparse matrices use BSR with square n_orb x n_orb blocks (n_orb = 1 or 9): row_ptr
+ *    (int32, n_atoms + 1), col (int32, nnzb, ascending within a row, the diagonal block
+ *    present), values FP64 row-major per block (nnzb * n_orb * n_orb).  Row i of a dense
+ *    vector block is orbital i = n_orb * atom + orbital-in-atom; probe panels are row-major
+ *    (n_rows x s, probe index fastest).
+ *  - The library allocates its own scratch (panels, partial sums, checkpoints) from the
+ *    context on first use and keeps it for later calls; tbk_destroy frees it.
+ */
+#ifndef TBK_H
+#define TBK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TBK_OK = 0,
+  TBK_ERR_ARG = -1,       /* invalid argument (null pointer, size, inconsistent shapes) */
+  TBK_ERR_CUDA = -2,      /* a CUDA runtime call or kernel launch failed */
+  TBK_ERR_OOM = -3,       /* device scratch could not be allocated */
+  TBK_ERR_SPECTRUM = -4,  /* a recurrence left [-1, 1]: spectral bounds too narrow */
+  TBK_ERR_NOCONV = -5,    /* bisection lost its sign change */
+  TBK_ERR_TIMEOUT = -6    /* a bounded device-side wait gave up */
+} tbk_status;
+
+/* Precision / algorithm flags of the recurrence. */
+#define TBK_MIXED 0            /* FP32 panels and FP32 mapped H, FP64 moment sums (default) */
+#define TBK_FP64 1             /* FP64 panels and FP64 mapped H throughout */
+#define TBK_MOMENTS_DIRECT 2   /* mu_k = <r, y_k> for every k instead of the doubling identity */
+
+/* Damping of the Chebyshev series. */
+#define TBK_DAMP_NONE 0
+#define TBK_DAMP_JACKSON 1
+
+/* Which function the coefficients expand (tbk_chebyshev_coefficients). */
+#define TBK_FN_FERMI 0         /* f(e) = 2 / (1 + exp((e - mu)/kT)) */
+#define TBK_FN_ENERGY 1        /* e f(e) */
+#define TBK_FN_FREE 2          /* g(e) = -2 kT ln(1 + exp(-(e - mu)/kT)) */
+
+/* Tight-binding models (tbk_model.kind). */
+#define TBK_MODEL_SK 1         /* Slater-Koster s/p/d two-centre blocks (n_orb = 9) */
+#define TBK_MODEL_TABLE 2      /* blocks looked up by bond displacement (lattice models) */
+
+typedef struct tbk_ctx tbk_ctx;
+
+/* Model parameters of tbk_assemble_H.  Plain data; pointers are read during the call only. */
+typedef struct {
+  int32_t kind;              /* TBK_MODEL_SK or TBK_MODEL_TABLE */
+  int32_t n_orb;             /* 9 for SK; 1 or 9 for TABLE */
+  /* SK: bond integrals ss_sigma, sp_sigma, sd_sigma, pp_sigma, pp_pi, pd_sigma, pd_pi,
+     dd_sigma, dd_pi, dd_delta, each scaled by exp(-sk_decay (r / sk_r0 - 1)); on-site
+     energies of the s, p and d orbitals. */
+  double sk_V[10];
+  double sk_r0;
+  double sk_decay;
+  double onsite_spd[3];
+  /* TABLE: n_disp bond displacements (host, n_disp x 3) and their blocks (host,
+     n_disp x n_orb x n_orb); a bond matches an entry when every component differs by at
+     most disp_tol.  Every off-diagonal neighbour pair must match exactly one entry. */
+  int32_t n_disp;
+  const double* disp;
+  const double* disp_blocks;
+  double disp_tol;
+  /* Optional per-site on-site diagonal energies (device, n_atoms x n_orb), added to the
+     diagonal blocks of either model; NULL for none. */
+  const double* onsite_site;
+} tbk_model;
+
+/* A block-sparse matrix on the device (see the conventions above). */
+typedef struct {
+  int32_t n_atoms;
+  int32_t n_orb;
+  int64_t nnzb;
+  const int32_t* row_ptr;    /* device, n_atoms + 1 */
+  const int32_t* col;        /* device, nnzb */
+  const double* val;         /* device, nnzb * n_orb * n_orb */
+} tbk_bsr;
+
+/* ---- context ------------------------------------------------------------------------ */
+
+/* Create a context on CUDA device `device` that enqueues on `stream` (a cudaStream_t; NULL =
+   the legacy default stream).  *out receives the handle. */
+int tbk_create(tbk_ctx** out, int device, void* stream);
+/* Free the context and all its device scratch. */
+int tbk_destroy(tbk_ctx* ctx);
+/* Message of the last failed call on this thread ("" if none).  Valid until the next call. */
+const char* tbk_last_error(void);
+/* Number of kernel launches this context has issued (for launch accounting). */
+int64_t tbk_launch_count(tbk_ctx* ctx);
+
+/* ---- a1: neighbour list (Sec. II.A mask M; Sec. II.E uniform-cube cell lists) ---------- */
+
+/* Pairs (i, j) with |r_j - r_i|^2 <= cutoff^2, self included, as CSR with ascending columns.
+   r^2 is evaluated in FP64 as ((dx*dx) + (dy*dy)) + (dz*dz) with one rounding per operation;
+   with a periodic box the displacement is the minimum image dx - L rint(dx / L).
+   pos: device, n_atoms x 3 FP64.  box: host, 3 FP64 box lengths, or NULL for an open
+   cluster (a periodic box must be longer than 2 cutoffs in every direction).
+   row_ptr: device, n_atoms + 1 int32, always written.  col: device int32 of col_capacity
+   entries, or NULL to count only.  *nnzb (host) receives the number of pairs; if col is not
+   NULL and col_capacity < *nnzb the call fails with TBK_ERR_ARG and col is untouched.
+   Synchronises the stream. */
+int tbk_build_neighbors(tbk_ctx* ctx, const double* pos, int32_t n_atoms, const double* box,
+                        double cutoff, int32_t* row_ptr, int32_t* col, int64_t col_capacity,
+                        int64_t* nnzb);
+
+/* ---- a2: Hamiltonian assembly (Sec. II.A, Slater-Koster form of the NRL model) --------- */
+
+/* Fill H (device, nnzb * n_orb^2 FP64) for the pattern (row_ptr, col) of n_atoms atoms at pos
+   (device FP64 n_atoms x 3; box as in tbk_build_neighbors).  Off-diagonal block (a, b) is the
+   model's block for the bond d = R_b - R_a; diagonal blocks carry the on-site energies. */
+int tbk_assemble_H(tbk_ctx* ctx, const tbk_model* model, const double* pos, int32_t n_atoms,
+                   const double* box, const int32_t* row_ptr, const int32_t* col, int64_t nnzb,
+                   double* H);
+
+/* ---- a3: spectral bounds (Sec. II.B.1 spectral interval [e_min, e_max]) ----------------- */
+
+/* FP64 Lanczos with `steps` iterations from a Rademacher start vector drawn from `seed`.  The
+   bounds are the extreme Ritz values widened by their residual norms, then by rel_margin times
+   the width on each side.  emin, emax: host.  Synchronises the stream. */
+int tbk_spectral_bounds(tbk_ctx* ctx, const tbk_bsr* H, int32_t steps, double rel_margin,
+                        uint64_t seed, double* emin, double* emax);
+
+/* ---- a4: Chebyshev coefficients (Sec. II.B.1) ------------------------------------------- */
+
+/* out (device, order FP64) = the first `order` Chebyshev coefficients of fn on [emin, emax]
+   by max(4 order, 256)-point Chebyshev-Gauss quadrature, times the damping factors. */
+int tbk_chebyshev_coefficients(tbk_ctx* ctx, int32_t fn, int32_t order, double emin,
+                               double emax, double mu, double kT, int32_t damping, double* out);
+
+/* ---- a5-a7: fused recurrence and moments (Sec. II.B.1 Eq. poly_PQ; Sec. II.C.2) -------- */
+
+/* moments (device, order FP64) = (1/s) sum_i r_i^T C_k(H^) r_i for k < order, with
+   H^ = (2H - (emax + emin) I)/(emax - emin) and s = n_probes Rademacher probes r_i whose entry
+   (row, j) is the sign of the top bit of SplitMix64 output number (row 2^32 + j + 1) of a stream
+   seeded with probe_seed.  The probes are regenerated inside the kernels and never stored.
+   flags: TBK_MIXED or TBK_FP64, optionally | TBK_MOMENTS_DIRECT.  n_probes must be a
+   multiple of 4.  Fails with TBK_ERR_SPECTRUM if a panel grows beyond the bound that holds
+   when the spectrum of H^ lies in [-1, 1]. */
+int tbk_chebyshev_moments(tbk_ctx* ctx, const tbk_bsr* H, double emin, double emax,
+                          uint64_t probe_seed, int32_t n_probes, int32_t order, int32_t flags,
+                          double* moments);
+
+/* ---- a8: chemical potential and observables (Sec. II.A Eqs. free_energy, density_matrix)
+
+   From the moments of tbk_chebyshev_moments: N(mu) = sum_k d_k alpha_k[f] mu_k with damping
+   factors d_k is solved for N(mu) = n_electrons by bisection on [emin, emax] (stopping when
+   the bracket is narrower than 1e-13 (emax - emin) or after 200 halvings; result = midpoint).
+   out (host, 4 FP64) = {mu, Omega, E, N} with Omega = sum d_k beta_k[g] mu_k and
+   E = sum d_k alpha_k[e f] mu_k.  If n_electrons < 0 the bisection is skipped and mu_fixed is
+   used.  moments: device.  Synchronises the stream. */
+int tbk_fermi_level(tbk_ctx* ctx, const double* moments, int32_t order, double emin,
+                    double emax, double n_electrons, double mu_fixed, double kT,
+                    int32_t damping, double* out);
+
+/* ---- a9-a10: sampled density matrix and forces (Sec. II.D Eq. polynomial_response) -----
+
+   The analytic derivative of the probe estimate Omega^ = (1/s) sum_i r_i^T q(H^) r_i,
+   q = sum_k d_k beta_k[g] C_k, with the bounds held fixed:
+     G = dOmega^/dH = (2/W)(1/s) sum_i sum_{j<order-1} y_ij x_ij^T on the pattern of H,
+     y_ij = C_j(H^) r_i,  x_ij = (2 - delta_j0) sum_{k>j} d_k beta_k U_{k-j-1}(H^) r_i,
+   returned symmetrised, G_ab <- (G_ab + G_ba^T)/2.  The panels y_j are recomputed from
+   checkpoints when they do not fit in max_panel_bytes of scratch (0 = choose automatically).
+   G: device, nnzb * n_orb^2 FP64, or NULL.  forces: device, n_atoms x 3 FP64, or NULL;
+   F_c = -sum_ab <G_ab, dH_ab/dR_c> needs model->kind == TBK_MODEL_SK and pos (device) / box as
+   in tbk_assemble_H.  flags: TBK_MIXED or TBK_FP64. */
+int tbk_density_and_forces(tbk_ctx* ctx, const tbk_bsr* H, const tbk_model* model,
+                           const double* pos, const double* box, double emin, double emax,
+                           uint64_t probe_seed, int32_t n_probes, int32_t order, double mu,
+                           double kT, int32_t damping, int32_t flags, int64_t max_panel_bytes,
+                           double* G, double* forces);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TBK_H */

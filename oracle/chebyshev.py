@@ -185,16 +185,21 @@ def poly_derivative(coef: np.ndarray, x: np.ndarray) -> np.ndarray:
     return (coef * np.arange(p)) @ U
 
 
-def divided_differences(coef: np.ndarray, x: np.ndarray, close: float = 1e-4) -> np.ndarray:
-    """Gamma_mn = (q(x_m) - q(x_n))/(x_m - x_n); for |x_m - x_n| < close the mean-value form
-    int_0^1 q'(x_n + t (x_m - x_n)) dt by Gauss-Legendre quadrature exact for degree p - 2."""
+def divided_differences(coef: np.ndarray, x: np.ndarray, close: float = 1e-6,
+                        max_nodes: int = 8) -> np.ndarray:
+    """Gamma_mn = (q(x_m) - q(x_n))/(x_m - x_n).
+
+    For |x_m - x_n| < close the difference quotient loses digits, so the mean-value form
+    int_0^1 q'(x_n + t (x_m - x_n)) dt is used instead, by Gauss-Legendre quadrature with
+    min(p/2 + 1, max_nodes) nodes: exact for p <= 2 max_nodes - 1, otherwise in error by
+    O(|x_m - x_n|^(2 max_nodes) max|q^(2 max_nodes + 1)|), far below rounding for |dx| < 1e-6."""
     q = poly_values(coef, x)
     dx = x[:, None] - x[None, :]
     with np.errstate(divide="ignore", invalid="ignore"):
         G = (q[:, None] - q[None, :]) / dx
     mi, ni = np.nonzero(np.abs(dx) < close)
     if mi.size:
-        nq = max(1, (len(coef) + 1) // 2 + 1)
+        nq = max(1, min((len(coef) + 1) // 2 + 1, max_nodes))
         t, w = np.polynomial.legendre.leggauss(nq)
         t = 0.5 * (t + 1.0)
         w = 0.5 * w

@@ -1,0 +1,294 @@
+"""PyTorch-facing wrappers of libtbk: device memory and streams come from torch, every step of
+the computation runs in the library's CUDA kernels.
+
+Pipeline (arXiv 1812.05264, Sec. II): neighbour list -> H assembly -> spectral bounds ->
+Chebyshev moments with random probes -> chemical potential and Omega, E, N -> analytic adjoint
+giving the sampled density matrix dOmega/dH on the pattern and the forces.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+
+def _ptr(t: torch.Tensor | None) -> int | None:
+    return None if t is None else t.data_ptr()
+
+
+class Context:
+    """A libtbk context bound to one CUDA device and the torch stream current at creation."""
+
+    def __init__(self, device: int | None = None, stream: torch.cuda.Stream | None = None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("libtbk needs a CUDA device")
+        self.device = torch.cuda.current_device() if device is None else int(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self._h = C.c_void_p()
+        L.call("tbk_create", C.byref(self._h), self.device, C.c_void_p(self.stream.cuda_stream))
+
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def launches(self) -> int:
+        return int(L.load().tbk_launch_count(self._h))
+
+    def close(self):
+        if self._h:
+            L.load().tbk_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+@dataclass
+class Graph:
+    n_atoms: int
+    nnzb: int
+    row_ptr: torch.Tensor   # int32 (n_atoms + 1,)
+    col: torch.Tensor       # int32 (nnzb,)
+
+
+@dataclass
+class BSR:
+    graph: Graph
+    n_orb: int
+    val: torch.Tensor       # float64 (nnzb, n_orb, n_orb)
+
+    def struct(self) -> L.tbk_bsr:
+        return L.tbk_bsr(self.graph.n_atoms, self.n_orb, self.graph.nnzb,
+                         _ptr(self.graph.row_ptr), _ptr(self.graph.col), _ptr(self.val))
+
+
+class Model:
+    """A tbk_model plus the arrays it points to (kept alive with it)."""
+
+    def __init__(self, kind: int, n_orb: int, sk_V=None, r0=2.55, decay=2.0, onsite_spd=(0, 0, 0),
+                 disp=None, blocks=None, tol=1e-6, onsite_site: torch.Tensor | None = None):
+        self.s = L.tbk_model()
+        self.s.kind = kind
+        self.s.n_orb = n_orb
+        if sk_V is not None:
+            for i in range(10):
+                self.s.sk_V[i] = float(sk_V[i])
+        self.s.sk_r0 = r0
+        self.s.sk_decay = decay
+        for i in range(3):
+            self.s.onsite_spd[i] = float(onsite_spd[i])
+        self._disp = None if disp is None else np.ascontiguousarray(disp, dtype=np.float64)
+        self._blocks = None if blocks is None else np.ascontiguousarray(blocks, dtype=np.float64)
+        self.s.n_disp = 0 if disp is None else int(self._disp.shape[0])
+        self.s.disp = None if disp is None else self._disp.ctypes.data
+        self.s.disp_blocks = None if blocks is None else self._blocks.ctypes.data
+        self.s.disp_tol = tol
+        self._onsite = onsite_site
+        self.s.onsite_site = _ptr(onsite_site)
+
+    @property
+    def is_sk(self) -> bool:
+        return self.s.kind == L.TBK_MODEL_SK
+
+    @staticmethod
+    def from_workload(wk, device) -> "Model":
+        import workloads as wl
+        if wk.sk_V is not None:
+            return Model(L.TBK_MODEL_SK, 9, sk_V=wk.sk_V, r0=wl.SK_R0, decay=wl.SK_DECAY,
+                         onsite_spd=wl.SK_ONSITE)
+        ons = None
+        if wk.onsite_site is not None:
+            a = np.asarray(wk.onsite_site, np.float64).reshape(wk.n_atoms, -1)
+            ons = torch.as_tensor(np.broadcast_to(a, (wk.n_atoms, wk.n_orb)).copy(), device=device)
+        return Model(L.TBK_MODEL_TABLE, wk.n_orb, disp=wk.disp, blocks=wk.blocks, onsite_site=ons)
+
+
+def _box_arg(box):
+    if box is None:
+        return None, None
+    arr = (C.c_double * 3)(*[float(x) for x in box])
+    return arr, C.cast(arr, C.c_void_p)
+
+
+def build_neighbors(ctx: Context, pos: torch.Tensor, cutoff: float, box=None) -> Graph:
+    """a1: CSR of all pairs with |r_j - r_i| <= cutoff (self included), ascending columns."""
+    assert pos.is_cuda and pos.dtype == torch.float64 and pos.is_contiguous()
+    n = pos.shape[0]
+    row_ptr = torch.empty(n + 1, dtype=torch.int32, device=pos.device)
+    nnz = C.c_int64()
+    _keep, bx = _box_arg(box)
+    L.call("tbk_build_neighbors", ctx.handle, _ptr(pos), n, bx, float(cutoff), _ptr(row_ptr), None,
+           0, C.byref(nnz))
+    col = torch.empty(max(1, nnz.value), dtype=torch.int32, device=pos.device)
+    L.call("tbk_build_neighbors", ctx.handle, _ptr(pos), n, bx, float(cutoff), _ptr(row_ptr),
+           _ptr(col), col.numel(), C.byref(nnz))
+    return Graph(n, nnz.value, row_ptr, col[:nnz.value])
+
+
+def assemble_H(ctx: Context, model: Model, pos: torch.Tensor, graph: Graph, box=None) -> BSR:
+    """a2: BSR values of H on the neighbour pattern."""
+    b = model.s.n_orb
+    val = torch.empty((max(1, graph.nnzb), b, b), dtype=torch.float64, device=pos.device)
+    _keep, bx = _box_arg(box)
+    L.call("tbk_assemble_H", ctx.handle, C.byref(model.s), _ptr(pos), graph.n_atoms, bx,
+           _ptr(graph.row_ptr), _ptr(graph.col), graph.nnzb, _ptr(val))
+    return BSR(graph, b, val[:graph.nnzb])
+
+
+def spectral_bounds(ctx: Context, H: BSR, steps: int = 64, margin: float = 0.01,
+                    seed: int = 0x5EED) -> tuple[float, float]:
+    """a3: [emin, emax] enclosing the spectrum (Lanczos + residual + relative margin)."""
+    lo, hi = C.c_double(), C.c_double()
+    L.call("tbk_spectral_bounds", ctx.handle, C.byref(H.struct()), int(steps), float(margin),
+           C.c_uint64(seed), C.byref(lo), C.byref(hi))
+    return lo.value, hi.value
+
+
+def chebyshev_coefficients(ctx: Context, fn: int, order: int, emin: float, emax: float, mu: float,
+                           kT: float, jackson: bool = False, device=None) -> torch.Tensor:
+    """a4: damped Chebyshev coefficients of f, e f or g on [emin, emax]."""
+    out = torch.empty(order, dtype=torch.float64, device=device or f"cuda:{ctx.device}")
+    L.call("tbk_chebyshev_coefficients", ctx.handle, fn, order, emin, emax, mu, kT,
+           L.TBK_DAMP_JACKSON if jackson else L.TBK_DAMP_NONE, _ptr(out))
+    return out
+
+
+def chebyshev_moments(ctx: Context, H: BSR, emin: float, emax: float, seed: int, n_probes: int,
+                      order: int, fp64: bool = False, direct: bool = False,
+                      out: torch.Tensor | None = None) -> torch.Tensor:
+    """a5-a7: mu_k = (1/s) sum_i r_i^T C_k(H^) r_i for k < order."""
+    if out is None:
+        out = torch.empty(order, dtype=torch.float64, device=H.val.device)
+    flags = (L.TBK_FP64 if fp64 else L.TBK_MIXED) | (L.TBK_MOMENTS_DIRECT if direct else 0)
+    L.call("tbk_chebyshev_moments", ctx.handle, C.byref(H.struct()), emin, emax, C.c_uint64(seed),
+           int(n_probes), int(order), flags, _ptr(out))
+    return out
+
+
+def fermi_level(ctx: Context, moments: torch.Tensor, emin: float, emax: float,
+                n_electrons: float | None, kT: float, jackson: bool = False,
+                mu: float | None = None) -> tuple[float, float, float, float]:
+    """a8: (mu, Omega, E, N); mu from N(mu) = n_electrons unless `mu` is given."""
+    out = (C.c_double * 4)()
+    ne = -1.0 if n_electrons is None else float(n_electrons)
+    L.call("tbk_fermi_level", ctx.handle, _ptr(moments), moments.numel(), emin, emax, ne,
+           0.0 if mu is None else float(mu), kT, L.TBK_DAMP_JACKSON if jackson else L.TBK_DAMP_NONE,
+           out)
+    return out[0], out[1], out[2], out[3]
+
+
+def density_and_forces(ctx: Context, H: BSR, model: Model | None, pos: torch.Tensor | None, box,
+                       emin: float, emax: float, seed: int, n_probes: int, order: int, mu: float,
+                       kT: float, jackson: bool = False, fp64: bool = False, want_G: bool = True,
+                       want_forces: bool = True, max_panel_bytes: int = 0):
+    """a9-a10: (G, F) with G = dOmega^/dH (nnzb, b, b) and F = -dOmega^/dR (N, 3)."""
+    dev = H.val.device
+    G = torch.empty_like(H.val) if want_G else None
+    F = torch.empty((H.graph.n_atoms, 3), dtype=torch.float64, device=dev) if want_forces else None
+    _keep, bx = _box_arg(box)
+    L.call("tbk_density_and_forces", ctx.handle, C.byref(H.struct()),
+           C.byref(model.s) if model is not None else None, _ptr(pos), bx, emin, emax,
+           C.c_uint64(seed), int(n_probes), int(order), float(mu), float(kT),
+           L.TBK_DAMP_JACKSON if jackson else L.TBK_DAMP_NONE, L.TBK_FP64 if fp64 else L.TBK_MIXED,
+           int(max_panel_bytes), _ptr(G), _ptr(F))
+    return G, F
+
+
+def order_for(W: float, kT: float, eps: float = 1e-7, p_min: int = 64) -> int:
+    """Chebyshev terms from the paper's error model eps_poly ~ exp(-6.4 p kT / W) (Sec. II.B.1)."""
+    return max(p_min, int(math.ceil((W / kT) * math.log(1.0 / eps) / 6.4)))
+
+
+# ----------------------------------------------------------------------------------------------
+# End-to-end solver and the autograd entry point
+# ----------------------------------------------------------------------------------------------
+
+@dataclass
+class Result:
+    emin: float
+    emax: float
+    order: int
+    mu: float
+    Omega: float
+    E: float
+    N: float
+    moments: torch.Tensor
+    H: BSR
+    G: torch.Tensor | None = None
+    forces: torch.Tensor | None = None
+
+    @property
+    def A(self) -> float:
+        return self.Omega + self.mu * self.N
+
+
+class Solver:
+    """Runs the whole path for one workload (see ``workloads``) on one device."""
+
+    def __init__(self, wk, ctx: Context | None = None, lanczos_steps: int = 64,
+                 margin: float = 0.01, bounds_seed: int = 0x5EED):
+        self.wk = wk
+        self.ctx = ctx or Context()
+        self.device = torch.device(f"cuda:{self.ctx.device}")
+        self.model = Model.from_workload(wk, self.device)
+        self.box = None if wk.box is None else [float(x) for x in wk.box]
+        self.lanczos_steps = lanczos_steps
+        self.margin = margin
+        self.bounds_seed = bounds_seed
+        self.graph = None
+
+    def energies(self, pos: torch.Tensor, order: int | None = None, fp64: bool | None = None,
+                 bounds=None, direct: bool = False) -> Result:
+        wk = self.wk
+        fp64 = (not wk.mixed) if fp64 is None else fp64
+        self.graph = build_neighbors(self.ctx, pos, wk.cutoff, self.box)
+        H = assemble_H(self.ctx, self.model, pos, self.graph, self.box)
+        emin, emax = bounds if bounds is not None else spectral_bounds(
+            self.ctx, H, self.lanczos_steps, self.margin, self.bounds_seed)
+        p = order or wk.order or order_for(emax - emin, wk.kT)
+        mom = chebyshev_moments(self.ctx, H, emin, emax, wk.probe_seed, wk.n_probes, p, fp64, direct)
+        mu, Om, E, N = fermi_level(self.ctx, mom, emin, emax, wk.n_electrons, wk.kT, wk.jackson)
+        return Result(emin, emax, p, mu, Om, E, N, mom, H)
+
+    def forces(self, pos: torch.Tensor, res: Result, fp64: bool | None = None, want_G=False,
+               max_panel_bytes: int = 0) -> Result:
+        wk = self.wk
+        fp64 = (not wk.mixed) if fp64 is None else fp64
+        G, F = density_and_forces(self.ctx, res.H, self.model, pos, self.box, res.emin, res.emax,
+                                  wk.probe_seed, wk.n_probes, res.order, res.mu, wk.kT, wk.jackson,
+                                  fp64, want_G=want_G or not self.model.is_sk,
+                                  want_forces=self.model.is_sk, max_panel_bytes=max_panel_bytes)
+        res.G, res.forces = G, F
+        return res
+
+
+class FreeEnergy(torch.autograd.Function):
+    """A^(R) = Omega^ + mu^ N_e of the probe estimate; backward returns -F (bounds held fixed).
+
+    At fixed electron count dA^/dR = dOmega^/dR at fixed mu (the polynomial coefficients satisfy
+    d beta[g]/d mu = -alpha[f] exactly), which the adjoint kernel evaluates.
+    """
+
+    @staticmethod
+    def forward(fctx, pos: torch.Tensor, solver: Solver):
+        res = solver.energies(pos.detach().contiguous())
+        fctx.solver = solver
+        fctx.res = res
+        fctx.save_for_backward(pos)
+        return torch.tensor(res.Omega + res.mu * solver.wk.n_electrons, dtype=torch.float64,
+                            device=pos.device)
+
+    @staticmethod
+    def backward(fctx, grad):
+        (pos,) = fctx.saved_tensors
+        res = fctx.solver.forces(pos.detach().contiguous(), fctx.res)
+        return -res.forces * grad, None

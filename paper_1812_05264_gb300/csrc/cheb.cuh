@@ -1,0 +1,53 @@
+// The mapped operator H^ = (2H - (emax + emin) I)/(emax - emin) (Sec. II.B.1) in the layout the
+// recurrence kernels read, and the fused block-SpMM step shared by the forward recurrence
+// (moments) and the adjoint (Clenshaw) passes.
+#pragma once
+#include "common.cuh"
+
+namespace tbk {
+
+// Row stride (elements) of one block row inside a stored block: rows are padded so that every
+// row starts on a 16-byte boundary and can be read with 128-bit loads.
+template <typename T, int B>
+struct Layout {
+  static constexpr int RS = B == 1 ? 1 : (sizeof(T) == 4 ? 12 : 10);
+  static constexpr int BS = B * RS;  // elements per stored block
+};
+
+struct HOp {
+  int n_atoms = 0, B = 0, prec = 0;  // prec: TBK_MIXED or TBK_FP64
+  int64_t nnzb = 0, n_rows = 0;
+  const int32_t* row_ptr = nullptr;
+  const int32_t* col = nullptr;
+  const void* hv = nullptr;          // mapped blocks, Layout<T,B>
+};
+
+// Validate a tbk_bsr and build H^ in scratch slot `slot` with precision `prec`.
+HOp prepare_hop(tbk_ctx* ctx, const tbk_bsr* H, double emin, double emax, int prec, Slot slot);
+
+// One fused step over all rows and probes:
+//   y_out = alpha * (H^ y_in) + c_r * r - y_prev
+// where y_in is a panel or (cur_is_probe) the probe block r regenerated from the seed, and the
+// y_prev term is present only when `yprev` is not NULL.  `yout` may equal `yprev` (in-place
+// update: each element is read and then written by the same thread).
+// With `partials` not NULL the CTA writes two FP64 partial sums at partials + 2 * cta:
+//   [0] = sum y_out . y_in   (or sum y_out . r when `direct`),   [1] = sum y_out . y_out.
+struct StepArgs {
+  const void* yin = nullptr;
+  void* yprev = nullptr;
+  void* yout = nullptr;
+  int cur_is_probe = 0;
+  double alpha = 2.0;
+  double c_r = 0.0;
+  uint64_t seed = 0;
+  int s = 0;
+  int direct = 0;
+  double* partials = nullptr;
+};
+// CTAs a step launches for this operator and probe count.
+int step_grid_ctas(tbk_ctx* ctx, const HOp& op, int s);
+void launch_step(tbk_ctx* ctx, const HOp& op, const StepArgs& a);
+// panel = c * r (probe block) for all rows.
+void launch_scaled_probe(tbk_ctx* ctx, const HOp& op, void* panel, double c, uint64_t seed, int s);
+
+}  // namespace tbk

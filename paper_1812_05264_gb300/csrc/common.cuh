@@ -1,0 +1,120 @@
+// Internal helpers shared by the libtbk translation units: the context, device scratch,
+// error handling across the C ABI, and small device utilities.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdio>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/tbk.h"
+
+namespace tbk {
+
+struct Error : std::runtime_error {
+  int code;
+  Error(int c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+void set_error(const char* msg);
+
+#define TBK_CHECK_ARG(cond, msg)                                              \
+  do {                                                                        \
+    if (!(cond)) throw ::tbk::Error(TBK_ERR_ARG, std::string(__func__) + ": " + (msg)); \
+  } while (0)
+
+#define TBK_CUDA(call)                                                        \
+  do {                                                                        \
+    cudaError_t _e = (call);                                                  \
+    if (_e != cudaSuccess)                                                    \
+      throw ::tbk::Error(_e == cudaErrorMemoryAllocation ? TBK_ERR_OOM : TBK_ERR_CUDA, \
+                         std::string(#call) + ": " + cudaGetErrorString(_e)); \
+  } while (0)
+
+// Named scratch slots.  Each slot is a grow-only device buffer owned by the context.
+enum Slot {
+  WS_PANEL0 = 0, WS_PANEL1, WS_PANEL2, WS_PANEL3, WS_HHAT, WS_PARTIALS, WS_FLAGS, WS_COEF,
+  WS_TABLE, WS_NODES, WS_CELLS, WS_CELLS2, WS_CELLS3, WS_LANCZOS, WS_GACC, WS_TRANSPOSE,
+  WS_CHECKPOINTS, WS_SEGMENT, WS_MISC, WS_NSLOTS
+};
+
+}  // namespace tbk
+
+struct tbk_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int num_sms = 0;
+  int64_t launches = 0;
+  void* slot_ptr[tbk::WS_NSLOTS] = {};
+  size_t slot_bytes[tbk::WS_NSLOTS] = {};
+  void* pinned = nullptr;        // small pinned host buffer for scalar read-back
+  size_t pinned_bytes = 0;
+};
+
+namespace tbk {
+
+// Device scratch of at least `bytes` in slot s (contents undefined after growth).
+void* scratch(tbk_ctx* ctx, Slot s, size_t bytes);
+// Pinned host staging of at least `bytes`.
+void* pinned(tbk_ctx* ctx, size_t bytes);
+// Check the launch that was just enqueued and count it.
+void post_launch(tbk_ctx* ctx, const char* what);
+// Make ctx->device current for the scope.
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(tbk_ctx* ctx);
+  ~DeviceGuard();
+};
+void sync(tbk_ctx* ctx);
+
+inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+}  // namespace tbk
+
+#define TBK_API_BEGIN try {
+#define TBK_API_END                                                           \
+  }                                                                           \
+  catch (const ::tbk::Error& e) {                                             \
+    ::tbk::set_error(e.what());                                               \
+    return e.code;                                                            \
+  }                                                                           \
+  catch (const std::exception& e) {                                           \
+    ::tbk::set_error(e.what());                                               \
+    return TBK_ERR_CUDA;                                                      \
+  }                                                                           \
+  ::tbk::set_error("");                                                       \
+  return TBK_OK;
+
+// ---------------------------------------------------------------------------------------
+// Device utilities
+// ---------------------------------------------------------------------------------------
+
+// Rademacher probe entry for (row, probe): SplitMix64 output number (row * 2^32 + probe + 1)
+// of a stream seeded with `seed` (Steele, Lea & Flood, OOPSLA 2014; mix64 finaliser of
+// java.util.SplittableRandom).  Returns +1 or -1.
+__device__ __forceinline__ float tbk_probe_sign(uint64_t seed, uint64_t row, uint64_t probe) {
+  uint64_t z = seed + ((row << 32) + probe + 1ull) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z = z ^ (z >> 31);
+  return (z >> 63) ? -1.0f : 1.0f;
+}
+
+// Fixed-order block reduction of one double (blockDim.x a multiple of 32, <= 1024).
+__device__ __forceinline__ double tbk_block_sum(double v, double* smem32) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nwarps = (blockDim.x + 31) >> 5;
+  __syncthreads();
+  if (lane == 0) smem32[warp] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (warp == 0) {
+    t = lane < nwarps ? smem32[lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  }
+  return t;  // valid in thread 0
+}

@@ -1,0 +1,440 @@
+// a5-a7: the fused block-SpMM Chebyshev recurrence with in-kernel probe generation and moment
+// partial sums (Sec. II.B.1 Eq. poly_PQ with S = I; Sec. II.C.2 random approximation).
+#include <algorithm>
+#include <cmath>
+
+#include "cheb.cuh"
+
+namespace tbk {
+
+template <typename T> struct Vec16;
+template <> struct Vec16<float> { using type = float4; static constexpr int N = 4; };
+template <> struct Vec16<double> { using type = double2; static constexpr int N = 2; };
+
+template <typename T>
+__device__ __forceinline__ void ld16(const T* p, T* x) {
+  if constexpr (sizeof(T) == 4) {
+    float4 v = *reinterpret_cast<const float4*>(p);
+    x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w;
+  } else {
+    double2 v = *reinterpret_cast<const double2*>(p);
+    x[0] = v.x; x[1] = v.y;
+  }
+}
+template <typename T>
+__device__ __forceinline__ void ldg16(const T* p, T* x) {
+  if constexpr (sizeof(T) == 4) {
+    float4 v = __ldg(reinterpret_cast<const float4*>(p));
+    x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w;
+  } else {
+    double2 v = __ldg(reinterpret_cast<const double2*>(p));
+    x[0] = v.x; x[1] = v.y;
+  }
+}
+template <typename T>
+__device__ __forceinline__ void st16(T* p, const T* x) {
+  if constexpr (sizeof(T) == 4) {
+    *reinterpret_cast<float4*>(p) = make_float4(x[0], x[1], x[2], x[3]);
+  } else {
+    *reinterpret_cast<double2*>(p) = make_double2(x[0], x[1]);
+  }
+}
+
+// ---- H^ in the padded kernel layout --------------------------------------------------------
+
+template <typename T, int B>
+__global__ void map_h_kernel(int n_atoms, const int32_t* __restrict__ row_ptr,
+                             const int32_t* __restrict__ col, const double* __restrict__ H,
+                             double shift, double inv_half_w, T* __restrict__ out) {
+  constexpr int RS = Layout<T, B>::RS, BS = Layout<T, B>::BS;
+  const int a = blockIdx.x * blockDim.y + threadIdx.y;
+  if (a >= n_atoms) return;
+  for (int k = row_ptr[a] + threadIdx.x; k < row_ptr[a + 1]; k += blockDim.x) {
+    const bool diag = col[k] == a;
+    for (int i = 0; i < B; ++i)
+      for (int j = 0; j < RS; ++j) {
+        double v = 0.0;
+        if (j < B) {
+          v = H[(int64_t)k * B * B + i * B + j];
+          if (diag && i == j) v -= shift;
+          v *= inv_half_w;
+        }
+        out[(int64_t)k * BS + i * RS + j] = (T)v;
+      }
+  }
+}
+
+HOp prepare_hop(tbk_ctx* ctx, const tbk_bsr* H, double emin, double emax, int prec, Slot slot) {
+  TBK_CHECK_ARG(H != nullptr, "H is NULL");
+  TBK_CHECK_ARG(H->n_orb == 1 || H->n_orb == 9, "n_orb must be 1 or 9");
+  TBK_CHECK_ARG(H->n_atoms >= 1 && H->nnzb >= H->n_atoms, "empty or inconsistent matrix");
+  TBK_CHECK_ARG(H->row_ptr && H->col && H->val, "NULL matrix array");
+  TBK_CHECK_ARG(H->nnzb < INT32_MAX, "nnzb must be below 2^31");
+  TBK_CHECK_ARG(std::isfinite(emin) && std::isfinite(emax) && emax > emin, "need emax > emin");
+  TBK_CHECK_ARG(prec == TBK_MIXED || prec == TBK_FP64, "unknown precision");
+  HOp op;
+  op.n_atoms = H->n_atoms;
+  op.B = H->n_orb;
+  op.prec = prec;
+  op.nnzb = H->nnzb;
+  op.n_rows = (int64_t)H->n_atoms * H->n_orb;
+  op.row_ptr = H->row_ptr;
+  op.col = H->col;
+  const double shift = 0.5 * (emax + emin), inv = 2.0 / (emax - emin);
+  dim3 blk(8, 16);
+  const int grid = ceil_div(op.n_atoms, 16);
+#define TBK_MAP(TT, BB)                                                                        \
+  {                                                                                            \
+    TT* out = (TT*)scratch(ctx, slot, sizeof(TT) * (size_t)op.nnzb * Layout<TT, BB>::BS);      \
+    map_h_kernel<TT, BB><<<grid, blk, 0, ctx->stream>>>(op.n_atoms, op.row_ptr, op.col, H->val, \
+                                                        shift, inv, out);                      \
+    post_launch(ctx, "map_h_kernel");                                                          \
+    op.hv = out;                                                                               \
+  }
+  if (prec == TBK_MIXED) {
+    if (op.B == 9) TBK_MAP(float, 9) else TBK_MAP(float, 1)
+  } else {
+    if (op.B == 9) TBK_MAP(double, 9) else TBK_MAP(double, 1)
+  }
+#undef TBK_MAP
+  return op;
+}
+
+// ---- the fused step --------------------------------------------------------------------------
+
+constexpr int STEP_THREADS = 128;
+
+template <typename T, int B, bool PROBE_IN>
+__global__ void __launch_bounds__(STEP_THREADS)
+cheb_step_kernel(const int n_atoms, const int32_t* __restrict__ row_ptr,
+                 const int32_t* __restrict__ col, const T* __restrict__ hv,
+                 const T* __restrict__ yin, const T* yprev, T* yout, const T alpha,
+                 const T c_r, const uint64_t seed, const int s, const int direct,
+                 double* __restrict__ partials) {
+  constexpr int VEC = Vec16<T>::N;
+  constexpr int RS = Layout<T, B>::RS, BS = Layout<T, B>::BS;
+  const int p0 = (blockIdx.y * blockDim.x + threadIdx.x) * VEC;
+  double sum0 = 0.0, sum1 = 0.0;
+  if (p0 < s) {
+    for (int a = blockIdx.x * blockDim.y + threadIdx.y; a < n_atoms; a += gridDim.x * blockDim.y) {
+      T acc[B][VEC];
+#pragma unroll
+      for (int i = 0; i < B; ++i)
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) acc[i][v] = T(0);
+      const int k1 = __ldg(row_ptr + a + 1);
+      for (int k = __ldg(row_ptr + a); k < k1; ++k) {
+        const int b = __ldg(col + k);
+        T x[B][VEC];
+#pragma unroll
+        for (int l = 0; l < B; ++l) {
+          const int64_t row = (int64_t)b * B + l;
+          if constexpr (PROBE_IN) {
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) x[l][v] = (T)tbk_probe_sign(seed, row, p0 + v);
+          } else {
+            ldg16(yin + row * s + p0, x[l]);
+          }
+        }
+        const T* h = hv + (int64_t)k * BS;
+#pragma unroll
+        for (int i = 0; i < B; ++i) {
+          T hr[RS];
+          if constexpr (B == 1) {
+            hr[0] = __ldg(h);
+          } else {
+#pragma unroll
+            for (int j = 0; j < RS; j += VEC) ldg16(h + i * RS + j, hr + j);
+          }
+#pragma unroll
+          for (int l = 0; l < B; ++l)
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) acc[i][v] = fma(hr[l], x[l][v], acc[i][v]);
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < B; ++i) {
+        const int64_t row = (int64_t)a * B + i;
+        const int64_t off = row * s + p0;
+        T yo[VEC], r[VEC];
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) yo[v] = alpha * acc[i][v];
+        if (c_r != T(0) || direct || PROBE_IN) {
+#pragma unroll
+          for (int v = 0; v < VEC; ++v) r[v] = (T)tbk_probe_sign(seed, row, p0 + v);
+        }
+        if (c_r != T(0)) {
+#pragma unroll
+          for (int v = 0; v < VEC; ++v) yo[v] = fma(c_r, r[v], yo[v]);
+        }
+        if (yprev) {
+          T t[VEC];
+          ld16(yprev + off, t);
+#pragma unroll
+          for (int v = 0; v < VEC; ++v) yo[v] -= t[v];
+        }
+        st16(yout + off, yo);
+        if (partials) {
+          T xin[VEC];
+          if (direct || PROBE_IN) {
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) xin[v] = r[v];
+          } else {
+            ldg16(yin + off, xin);
+          }
+          T q0 = T(0), q1 = T(0);
+#pragma unroll
+          for (int v = 0; v < VEC; ++v) {
+            q0 = fma(yo[v], xin[v], q0);
+            q1 = fma(yo[v], yo[v], q1);
+          }
+          sum0 += (double)q0;
+          sum1 += (double)q1;
+        }
+      }
+    }
+  }
+  if (partials) {
+    __shared__ double red[2][STEP_THREADS / 32];
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    const int nthreads = blockDim.x * blockDim.y;
+    for (int o = 16; o > 0; o >>= 1) {
+      sum0 += __shfl_xor_sync(0xffffffffu, sum0, o);
+      sum1 += __shfl_xor_sync(0xffffffffu, sum1, o);
+    }
+    if ((tid & 31) == 0) {
+      red[0][tid >> 5] = sum0;
+      red[1][tid >> 5] = sum1;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double a0 = 0.0, a1 = 0.0;
+      for (int w = 0; w < (nthreads + 31) / 32; ++w) {
+        a0 += red[0][w];
+        a1 += red[1][w];
+      }
+      const int cta = blockIdx.y * gridDim.x + blockIdx.x;
+      partials[2 * cta] = a0;
+      partials[2 * cta + 1] = a1;
+    }
+  }
+}
+
+struct StepGeom {
+  dim3 block, grid;
+};
+
+template <typename T, int B, bool P>
+static int occupancy() {
+  static int occ[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  if (!occ[dev]) {
+    int n = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, cheb_step_kernel<T, B, P>, STEP_THREADS, 0);
+    occ[dev] = n > 0 ? n : 1;
+  }
+  return occ[dev];
+}
+
+template <typename T, int B>
+static StepGeom step_geom(tbk_ctx* ctx, const HOp& op, int s) {
+  constexpr int VEC = Vec16<T>::N;
+  const int lanes_needed = s / VEC;
+  int lanes = 1;  // a power of two, so that every warp of the CTA is complete
+  while (lanes < lanes_needed && lanes < STEP_THREADS) lanes <<= 1;
+  const int rows = STEP_THREADS / lanes;
+  StepGeom g;
+  g.block = dim3(lanes, rows);
+  const int gy = ceil_div(lanes_needed, lanes);
+  const int64_t row_groups = (op.n_atoms + rows - 1) / rows;
+  const int occ = std::min(occupancy<T, B, false>(), occupancy<T, B, true>());
+  const int64_t wave = (int64_t)occ * ctx->num_sms;
+  const int64_t gx = std::max<int64_t>(1, std::min<int64_t>(row_groups, std::max<int64_t>(1, wave / gy)));
+  g.grid = dim3((unsigned)gx, (unsigned)gy);
+  return g;
+}
+
+static StepGeom geom_for(tbk_ctx* ctx, const HOp& op, int s) {
+  if (op.prec == TBK_MIXED) return op.B == 9 ? step_geom<float, 9>(ctx, op, s) : step_geom<float, 1>(ctx, op, s);
+  return op.B == 9 ? step_geom<double, 9>(ctx, op, s) : step_geom<double, 1>(ctx, op, s);
+}
+
+int step_grid_ctas(tbk_ctx* ctx, const HOp& op, int s) {
+  StepGeom g = geom_for(ctx, op, s);
+  return (int)(g.grid.x * g.grid.y);
+}
+
+template <typename T, int B>
+static void launch_typed(tbk_ctx* ctx, const HOp& op, const StepArgs& a) {
+  StepGeom g = step_geom<T, B>(ctx, op, a.s);
+  const T* hv = (const T*)op.hv;
+  if (a.cur_is_probe)
+    cheb_step_kernel<T, B, true><<<g.grid, g.block, 0, ctx->stream>>>(
+        op.n_atoms, op.row_ptr, op.col, hv, (const T*)a.yin, (const T*)a.yprev, (T*)a.yout, (T)a.alpha,
+        (T)a.c_r, a.seed, a.s, a.direct, a.partials);
+  else
+    cheb_step_kernel<T, B, false><<<g.grid, g.block, 0, ctx->stream>>>(
+        op.n_atoms, op.row_ptr, op.col, hv, (const T*)a.yin, (const T*)a.yprev, (T*)a.yout, (T)a.alpha,
+        (T)a.c_r, a.seed, a.s, a.direct, a.partials);
+  post_launch(ctx, "cheb_step_kernel");
+}
+
+void launch_step(tbk_ctx* ctx, const HOp& op, const StepArgs& a) {
+  if (op.prec == TBK_MIXED) {
+    if (op.B == 9) launch_typed<float, 9>(ctx, op, a); else launch_typed<float, 1>(ctx, op, a);
+  } else {
+    if (op.B == 9) launch_typed<double, 9>(ctx, op, a); else launch_typed<double, 1>(ctx, op, a);
+  }
+}
+
+template <typename T>
+__global__ void scaled_probe_kernel(int64_t n_rows, int s, double c, uint64_t seed, T* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_rows * s) return;
+  const int64_t row = i / s;
+  const int p = (int)(i - row * s);
+  out[i] = (T)(c * (double)tbk_probe_sign(seed, row, p));
+}
+
+void launch_scaled_probe(tbk_ctx* ctx, const HOp& op, void* panel, double c, uint64_t seed, int s) {
+  const int64_t n = op.n_rows * s;
+  const unsigned grid = (unsigned)((n + 255) / 256);
+  if (op.prec == TBK_MIXED)
+    scaled_probe_kernel<float><<<grid, 256, 0, ctx->stream>>>(op.n_rows, s, c, seed, (float*)panel);
+  else
+    scaled_probe_kernel<double><<<grid, 256, 0, ctx->stream>>>(op.n_rows, s, c, seed, (double*)panel);
+  post_launch(ctx, "scaled_probe_kernel");
+}
+
+// ---- moment reduction ------------------------------------------------------------------------
+
+// sums[2 j + c] = sum over CTAs of partials[(j * nctas + cta) * 2 + c], Kahan-compensated per
+// thread over a fixed strided set, then a fixed-order tree.
+__global__ void reduce_partials(const double* __restrict__ partials, int nctas, double* __restrict__ sums) {
+  const int j = blockIdx.x;
+  __shared__ double sh[2][256];
+  double s0 = 0, c0 = 0, s1 = 0, c1 = 0;
+  for (int t = threadIdx.x; t < nctas; t += blockDim.x) {
+    const double* p = partials + ((int64_t)j * nctas + t) * 2;
+    double y = p[0] - c0, u = s0 + y;
+    c0 = (u - s0) - y;
+    s0 = u;
+    y = p[1] - c1;
+    u = s1 + y;
+    c1 = (u - s1) - y;
+    s1 = u;
+  }
+  sh[0][threadIdx.x] = s0;
+  sh[1][threadIdx.x] = s1;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      sh[0][threadIdx.x] += sh[0][threadIdx.x + o];
+      sh[1][threadIdx.x] += sh[1][threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    sums[2 * j] = sh[0][0];
+    sums[2 * j + 1] = sh[1][0];
+  }
+}
+
+// Moments from the per-step sums (step j = 1..K stored at index j - 1):
+//   direct:   mu_j = S0_j / s
+//   doubling: mu_1 = S0_1 / s, mu_2j = 2 S1_j / s - mu_0, mu_2j-1 = 2 S0_j / s - mu_1 (j >= 2)
+// (C_m C_n = (C_{m+n} + C_{|m-n|})/2).  mu_0 = n_rows exactly for +-1 probes.  flag = 1 when a
+// panel norm exceeds ||r|| (a spectrum outside [-1, 1]) or a sum is not finite.
+__global__ void finish_moments(const double* __restrict__ sums, int K, int order, int s,
+                               int64_t n_rows, int direct, double* __restrict__ mom,
+                               int* __restrict__ flag) {
+  const double mu0 = (double)n_rows;
+  const double inv_s = 1.0 / s;
+  const double mu1 = K >= 1 ? sums[0] * inv_s : 0.0;
+  for (int k = threadIdx.x; k < order; k += blockDim.x) {
+    double v;
+    if (k == 0) v = mu0;
+    else if (direct) v = sums[2 * (k - 1)] * inv_s;
+    else if (k == 1) v = mu1;
+    else if ((k & 1) == 0) v = 2.0 * sums[2 * (k / 2 - 1) + 1] * inv_s - mu0;
+    else v = 2.0 * sums[2 * ((k + 1) / 2 - 1)] * inv_s - mu1;
+    mom[k] = v;
+  }
+  for (int j = threadIdx.x; j < K; j += blockDim.x) {
+    const double e = sums[2 * j + 1] * inv_s, o = sums[2 * j];
+    if (!(e <= mu0 * (1.0 + 1e-3)) || !isfinite(o)) atomicExch(flag, 1);
+  }
+}
+
+}  // namespace tbk
+
+using namespace tbk;
+
+extern "C" int tbk_chebyshev_moments(tbk_ctx* ctx, const tbk_bsr* H, double emin, double emax,
+                                     uint64_t probe_seed, int32_t n_probes, int32_t order,
+                                     int32_t flags, double* moments) {
+  TBK_API_BEGIN
+  TBK_CHECK_ARG(ctx != nullptr, "ctx is NULL");
+  TBK_CHECK_ARG(moments != nullptr, "moments is NULL");
+  TBK_CHECK_ARG(order >= 1, "order must be >= 1");
+  TBK_CHECK_ARG(n_probes >= 4 && n_probes % 4 == 0, "n_probes must be a positive multiple of 4");
+  TBK_CHECK_ARG((flags & ~(TBK_FP64 | TBK_MOMENTS_DIRECT)) == 0, "unknown flag");
+  DeviceGuard dg(ctx);
+  const int prec = (flags & TBK_FP64) ? TBK_FP64 : TBK_MIXED;
+  const int direct = (flags & TBK_MOMENTS_DIRECT) ? 1 : 0;
+  HOp op = prepare_hop(ctx, H, emin, emax, prec, WS_HHAT);
+  const int s = n_probes;
+  const size_t esz = prec == TBK_MIXED ? 4 : 8;
+  const size_t panel = (size_t)op.n_rows * s * esz;
+  const int K = direct ? order - 1 : order / 2;   // steps: largest moment index 2K >= order - 1
+  const int nctas = step_grid_ctas(ctx, op, s);
+  double* partials = (double*)scratch(ctx, WS_PARTIALS, sizeof(double) * 2 * (size_t)std::max(1, K) * nctas);
+  double* sums = (double*)scratch(ctx, WS_MISC, sizeof(double) * 2 * (size_t)std::max(1, K) + 64);
+  int* flag = (int*)scratch(ctx, WS_FLAGS, 64);
+  TBK_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), ctx->stream));
+  void* A = K >= 1 ? scratch(ctx, WS_PANEL0, panel) : nullptr;
+  void* Bp = K >= 2 ? scratch(ctx, WS_PANEL1, panel) : nullptr;
+  void *cur = nullptr, *prev = nullptr;
+  for (int j = 1; j <= K; ++j) {
+    StepArgs a;
+    a.seed = probe_seed;
+    a.s = s;
+    a.direct = direct;
+    a.partials = partials + (size_t)(j - 1) * nctas * 2;
+    if (j == 1) {
+      a.cur_is_probe = 1;
+      a.alpha = 1.0;
+      a.yout = A;
+      cur = A;
+    } else if (j == 2) {
+      a.yin = A;
+      a.alpha = 2.0;
+      a.c_r = -1.0;
+      a.yout = Bp;
+      prev = A;
+      cur = Bp;
+    } else {
+      a.yin = cur;
+      a.yprev = prev;
+      a.yout = prev;
+      a.alpha = 2.0;
+      std::swap(cur, prev);  // y_{j} now lives where y_{j-2} was
+    }
+    launch_step(ctx, op, a);
+  }
+  if (K >= 1) {
+    reduce_partials<<<K, 256, 0, ctx->stream>>>(partials, nctas, sums);
+    post_launch(ctx, "reduce_partials");
+  }
+  finish_moments<<<1, 256, 0, ctx->stream>>>(sums, K, order, s, op.n_rows, direct, moments, flag);
+  post_launch(ctx, "finish_moments");
+  int hflag = 0;
+  TBK_CUDA(cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  sync(ctx);
+  if (hflag)
+    throw Error(TBK_ERR_SPECTRUM, "a Chebyshev panel grew beyond ||r||: the spectrum of H is not "
+                                  "inside [emin, emax]");
+  TBK_API_END
+}

@@ -1,0 +1,262 @@
+"""Parity of the CUDA path (through the C ABI) against the FP64 oracle on the same seeded inputs.
+
+Tolerances (stated per test): neighbour pattern bit-exact; FP64-mode energies within 1e-6
+eV/atom of the oracle's exact value of the same estimator, mixed mode within 1e-4 eV/atom;
+forces within 1e-3 eV/A (mixed) and 1e-6 eV/A (FP64).
+"""
+import numpy as np
+import pytest
+import torch
+
+import workloads as wl
+from oracle import chebyshev as och
+from oracle import neighbors as onb
+
+from gpu_common import (blocks_of, oracle_H, oracle_estimator, oracle_estimator_forces,
+                        small_fcc)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def api():
+    from paper_1812_05264_gb300 import build
+    build.build()
+    from paper_1812_05264_gb300 import api as A
+    return A
+
+
+@pytest.fixture(scope="module")
+def ctx(api):
+    return api.Context()
+
+
+def _dev(x):
+    return torch.as_tensor(np.ascontiguousarray(x), dtype=torch.float64, device="cuda")
+
+
+# ---- a1 neighbour list: bit-exact ---------------------------------------------------------
+
+@pytest.mark.parametrize("case", ["fcc1000", "fcc_jitter", "sc_open", "sc_periodic", "edge"])
+def test_neighbors_bit_exact(api, ctx, case):
+    box = None
+    if case == "fcc1000":
+        pos, rc = wl.fcc_sphere(1000), 4.0
+    elif case == "fcc_jitter":
+        pos, rc = wl.fcc_sphere(700, jitter=0.05, seed=3), 4.0
+    elif case == "sc_open":
+        pos, rc = wl.sc_cluster(10), 1.0
+    elif case == "sc_periodic":
+        pos, box = wl.sc_lattice(7)
+        rc = 1.5
+    else:
+        # points at exactly the cutoff, one ulp inside and outside, coincident points
+        rc = 1.0
+        pos = np.array([[0, 0, 0], [1, 0, 0], [0, 1.0000000000000002, 0], [0, 0, 0.9999999999999999],
+                        [0, 0, 0], [3, 3, 3], [3.6, 3, 3]], float)
+    rp, col = onb.neighbor_csr(pos, rc, box)
+    g = api.build_neighbors(ctx, _dev(pos), rc, box)
+    assert g.nnzb == len(col)
+    assert np.array_equal(g.row_ptr.cpu().numpy(), rp.astype(np.int32))
+    assert np.array_equal(g.col.cpu().numpy(), col)
+
+
+def test_neighbors_single_atom_and_empty(api, ctx):
+    g = api.build_neighbors(ctx, _dev(np.zeros((1, 3))), 2.0)
+    assert g.nnzb == 1 and g.col.cpu().tolist() == [0]
+    g0 = api.build_neighbors(ctx, torch.zeros((0, 3), dtype=torch.float64, device="cuda"), 2.0)
+    assert g0.nnzb == 0
+
+
+# ---- a2 assembly ----------------------------------------------------------------------------
+
+def test_assemble_sk_matches_oracle(api, ctx):
+    wk = small_fcc(60, jitter=0.08)
+    rp, col, H = oracle_H(wk)
+    s = api.Solver(wk, ctx)
+    g = api.build_neighbors(ctx, _dev(wk.positions), wk.cutoff)
+    Hg = api.assemble_H(ctx, s.model, _dev(wk.positions), g)
+    ref = blocks_of(H, rp, col, 9)
+    assert np.allclose(Hg.val.cpu().numpy(), ref, rtol=0, atol=1e-13)
+
+
+@pytest.mark.parametrize("which", ["sc1", "lattice9"])
+def test_assemble_table_matches_oracle(api, ctx, which):
+    wk = wl.sc_disorder(L=6) if which == "sc1" else wl.sc9_periodic(L=4, n_probes=8)
+    rp, col, H = oracle_H(wk)
+    s = api.Solver(wk, ctx)
+    g = api.build_neighbors(ctx, _dev(wk.positions), wk.cutoff, s.box)
+    Hg = api.assemble_H(ctx, s.model, _dev(wk.positions), g, s.box)
+    assert np.allclose(Hg.val.cpu().numpy(), blocks_of(H, rp, col, wk.n_orb), rtol=0, atol=1e-14)
+
+
+# ---- a3 bounds, a4 coefficients ------------------------------------------------------------
+
+@pytest.mark.parametrize("which", ["fcc", "sc1"])
+def test_spectral_bounds_enclose_spectrum(api, ctx, which):
+    wk = small_fcc(80) if which == "fcc" else wl.sc_disorder(L=8)
+    _, _, H = oracle_H(wk)
+    w = np.linalg.eigvalsh(H)
+    s = api.Solver(wk, ctx)
+    g = api.build_neighbors(ctx, _dev(wk.positions), wk.cutoff)
+    Hg = api.assemble_H(ctx, s.model, _dev(wk.positions), g)
+    emin, emax = api.spectral_bounds(ctx, Hg, steps=64, margin=0.01)
+    assert emin < w.min() and emax > w.max()
+    assert (emax - emin) < 1.1 * (w.max() - w.min())
+
+
+@pytest.mark.parametrize("fn", [0, 1, 2])
+@pytest.mark.parametrize("jackson", [False, True])
+def test_coefficients_match_oracle(api, ctx, fn, jackson):
+    p, emin, emax, mu, T = 300, -12.0, 25.0, 3.3, 0.2
+    c = api.chebyshev_coefficients(ctx, fn, p, emin, emax, mu, T, jackson).cpu().numpy()
+    af, aef, bg = och.fd_coefficients(p, emin, emax, mu, T)
+    ref = [af, aef, bg][fn] * och.damping(p, jackson)
+    assert np.allclose(c, ref, rtol=0, atol=1e-13 * max(1.0, np.abs(ref).max()))
+
+
+# ---- a5-a8 moments and observables ----------------------------------------------------------
+
+def _gpu_run(api, ctx, wk, p, fp64, direct=False, bounds=None):
+    s = api.Solver(wk, ctx)
+    pos = _dev(wk.positions)
+    res = s.energies(pos, order=p, fp64=fp64, bounds=bounds, direct=direct)
+    return s, pos, res
+
+
+@pytest.mark.parametrize("direct", [False, True])
+def test_moments_fp64_match_exact_estimator(api, ctx, direct):
+    wk = small_fcc(50, n_probes=16)
+    rp, col, H = oracle_H(wk)
+    s, pos, res = _gpu_run(api, ctx, wk, 151, fp64=True, direct=direct)
+    est = oracle_estimator(wk, H, res.emin, res.emax, 151)
+    n = H.shape[0]
+    assert np.allclose(res.moments.cpu().numpy(), est["moments"], rtol=0, atol=1e-11 * n)
+
+
+def test_sc_cluster_energies_fp64(api, ctx):
+    """Simple-cubic 10^3 open cluster, 1 orbital, Jackson damping, 32 probes, p = 200."""
+    wk = wl.sc_disorder(L=10)
+    rp, col, H = oracle_H(wk)
+    s, pos, res = _gpu_run(api, ctx, wk, wk.order, fp64=True)
+    est = oracle_estimator(wk, H, res.emin, res.emax, wk.order)
+    n = wk.n_atoms
+    assert np.allclose(res.moments.cpu().numpy(), est["moments"], rtol=0, atol=1e-11 * n)
+    assert abs(res.mu - est["mu"]) < 1e-9
+    for key in ("Omega", "E", "N"):
+        assert abs(getattr(res, key) - est[key]) / n < 1e-6, key
+
+
+@pytest.mark.parametrize("fp64,tol", [(True, 1e-6), (False, 1e-4)])
+def test_fcc_energies_vs_oracle(api, ctx, fp64, tol):
+    wk = small_fcc(120, kT=0.5, n_probes=32)
+    rp, col, H = oracle_H(wk)
+    s, pos, res = _gpu_run(api, ctx, wk, 220, fp64=fp64)
+    est = oracle_estimator(wk, H, res.emin, res.emax, 220)
+    n = wk.n_atoms
+    for key in ("Omega", "E", "N"):
+        assert abs(getattr(res, key) - est[key]) / n < tol, key
+    assert abs(res.mu - est["mu"]) < 100 * tol
+
+
+def test_fermi_level_from_oracle_moments(api, ctx):
+    """a8 alone: same moments in, same mu / Omega / E / N out (FP64, 1e-10 relative)."""
+    wk = small_fcc(40)
+    rp, col, H = oracle_H(wk)
+    w = np.linalg.eigvalsh(H)
+    emin, emax = w.min() - 0.5, w.max() + 0.5
+    est = oracle_estimator(wk, H, emin, emax, 180)
+    mom = _dev(est["moments"])
+    mu, Om, E, N = api.fermi_level(ctx, mom, emin, emax, wk.n_electrons, wk.kT)
+    assert mu == pytest.approx(est["mu"], abs=1e-10)
+    assert Om == pytest.approx(est["Omega"], rel=1e-10)
+    assert E == pytest.approx(est["E"], rel=1e-10)
+    assert N == pytest.approx(est["N"], rel=1e-10)
+    # fixed chemical potential
+    mu0 = est["mu"] + 0.3
+    _, Om2, E2, N2 = api.fermi_level(ctx, mom, emin, emax, None, wk.kT, mu=mu0)
+    ref = och.estimator_observables(est["moments"], emin, emax, mu0, wk.kT)
+    assert np.allclose([Om2, E2, N2], ref, rtol=1e-10)
+
+
+# ---- a9-a10 density matrix and forces -------------------------------------------------------
+
+@pytest.mark.parametrize("fp64,ftol", [(True, 1e-6), (False, 1e-3)])
+def test_density_and_forces_vs_oracle(api, ctx, fp64, ftol):
+    wk = small_fcc(30, kT=0.5, n_probes=8)
+    p = 120
+    rp, col, H = oracle_H(wk)
+    s, pos, res = _gpu_run(api, ctx, wk, p, fp64=fp64)
+    est = oracle_estimator(wk, H, res.emin, res.emax, p)
+    Gd, F = oracle_estimator_forces(wk, rp, col, est, res.emin, res.emax, p)
+    # use the oracle's mu so that G and F are compared at the same point
+    G, Fg = api.density_and_forces(ctx, res.H, s.model, pos, None, res.emin, res.emax,
+                                   wk.probe_seed, wk.n_probes, p, est["mu"], wk.kT, False, fp64)
+    Gref = blocks_of(Gd, rp, col, 9)
+    gscale = np.abs(Gref).max()
+    assert np.abs(G.cpu().numpy() - Gref).max() < (1e-9 if fp64 else 2e-4) * gscale
+    assert np.abs(Fg.cpu().numpy() - F).max() < ftol
+    assert np.abs(Fg.cpu().numpy().sum(0)).max() < 1e-9
+
+
+def test_checkpointed_adjoint_equals_stored(api, ctx):
+    """Replaying segments from checkpoints gives the same G as keeping every panel."""
+    wk = small_fcc(30, n_probes=8)
+    p = 90
+    s, pos, res = _gpu_run(api, ctx, wk, p, fp64=True)
+    args = (ctx, res.H, s.model, pos, None, res.emin, res.emax, wk.probe_seed, wk.n_probes, p,
+            res.mu, wk.kT, False, True)
+    G1, F1 = api.density_and_forces(*args)
+    panel = wk.n_atoms * 9 * wk.n_probes * 8
+    G2, F2 = api.density_and_forces(*args, max_panel_bytes=40 * panel)
+    assert torch.equal(G1, G2) and torch.equal(F1, F2)
+
+
+def test_autograd_free_energy(api, ctx):
+    wk = small_fcc(25, n_probes=8, order=100)
+    s = api.Solver(wk, ctx)
+    pos = _dev(wk.positions).requires_grad_(True)
+    A = api.FreeEnergy.apply(pos, s)
+    A.backward()
+    res = s.energies(_dev(wk.positions), order=100)
+    r2 = s.forces(_dev(wk.positions), res)
+    assert torch.allclose(pos.grad, -r2.forces)
+
+
+# ---- error paths ------------------------------------------------------------------------------
+
+def test_too_narrow_bounds_raise_spectrum_error(api, ctx):
+    from paper_1812_05264_gb300._lib import TBK_ERR_SPECTRUM, TbkError
+    wk = small_fcc(30)
+    s = api.Solver(wk, ctx)
+    pos = _dev(wk.positions)
+    g = api.build_neighbors(ctx, pos, wk.cutoff)
+    H = api.assemble_H(ctx, s.model, pos, g)
+    emin, emax = api.spectral_bounds(ctx, H)
+    mid, half = 0.5 * (emin + emax), 0.3 * (emax - emin)
+    with pytest.raises(TbkError) as e:
+        api.chebyshev_moments(ctx, H, mid - half, mid + half, 1, 8, 400, fp64=True)
+    assert e.value.code == TBK_ERR_SPECTRUM
+
+
+def test_argument_errors(api, ctx):
+    from paper_1812_05264_gb300._lib import TBK_ERR_ARG, TBK_ERR_NOCONV, TbkError
+    wk = small_fcc(20)
+    s = api.Solver(wk, ctx)
+    pos = _dev(wk.positions)
+    g = api.build_neighbors(ctx, pos, wk.cutoff)
+    H = api.assemble_H(ctx, s.model, pos, g)
+    with pytest.raises(TbkError) as e:
+        api.chebyshev_moments(ctx, H, -1.0, 1.0, 1, 6, 10)          # probes not a multiple of 4
+    assert e.value.code == TBK_ERR_ARG
+    with pytest.raises(TbkError) as e:
+        api.chebyshev_moments(ctx, H, 1.0, -1.0, 1, 8, 10)          # emax < emin
+    assert e.value.code == TBK_ERR_ARG
+    emin, emax = api.spectral_bounds(ctx, H)
+    mom = api.chebyshev_moments(ctx, H, emin, emax, 1, 8, 50, fp64=True)
+    with pytest.raises(TbkError) as e:
+        api.fermi_level(ctx, mom, emin, emax, 1e9, 0.5)               # more electrons than states
+    assert e.value.code == TBK_ERR_NOCONV
+    # the context stays usable after errors
+    mom2 = api.chebyshev_moments(ctx, H, emin, emax, 1, 8, 50, fp64=True)
+    assert torch.equal(mom, mom2)

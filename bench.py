@@ -256,6 +256,8 @@ def run_ours(args, rank, world):
                                       want_G=not solver.model.is_sk, want_forces=solver.model.is_sk)
         return p, (mu, Om, E, N), F
 
+    if args.only_moments:
+        return moments_only(args, ctx, solver, wk, pos)
     for _ in range(max(args.warmup, 0)):
         p, _, _ = step(pos)
     torch.cuda.synchronize()
@@ -347,6 +349,28 @@ def run_ours(args, rank, world):
     return 0
 
 
+def moments_only(args, ctx, solver, wk, pos):
+    """Profiling aid: just the fused recurrence (moments) with a fixed small order."""
+    import torch
+    from paper_1812_05264_gb300 import api
+    g = api.build_neighbors(ctx, pos, wk.cutoff, solver.box)
+    H = api.assemble_H(ctx, solver.model, pos, g, solver.box)
+    emin, emax = api.spectral_bounds(ctx, H)
+    p = args.order
+    for _ in range(args.warmup):
+        api.chebyshev_moments(ctx, H, emin, emax, wk.probe_seed, wk.n_probes, p, not wk.mixed)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(ctx.stream)
+    for _ in range(args.steps):
+        api.chebyshev_moments(ctx, H, emin, emax, wk.probe_seed, wk.n_probes, p, not wk.mixed)
+    e1.record(ctx.stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    print(json.dumps({"only": "moments", "workload": wk.name, "order": p, "ms": ms,
+                      "ms_per_launch": ms / (p // 2)}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -355,6 +379,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="fcc10k")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--only-moments", action="store_true", help="profiling aid: recurrence only")
+    ap.add_argument("--order", type=int, default=64, help="order for --only-moments")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

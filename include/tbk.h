@@ -48,6 +48,7 @@ typedef enum {
 #define TBK_MIXED 0            /* FP32 panels and FP32 mapped H, FP64 moment sums (default) */
 #define TBK_FP64 1             /* FP64 panels and FP64 mapped H throughout */
 #define TBK_MOMENTS_DIRECT 2   /* mu_k = <r, y_k> for every k instead of the doubling identity */
+#define TBK_PLAIN_KERNEL 4     /* use the plain load/FMA step kernel instead of the TMA-fed one */
 
 /* Damping of the Chebyshev series. */
 #define TBK_DAMP_NONE 0
@@ -154,8 +155,10 @@ int tbk_chebyshev_coefficients(tbk_ctx* ctx, int32_t fn, int32_t order, double e
    H^ = (2H - (emax + emin) I)/(emax - emin) and s = n_probes Rademacher probes r_i whose entry
    (row, j) is the sign of the top bit of SplitMix64 output number (row 2^32 + j + 1) of a stream
    seeded with probe_seed.  The probes are regenerated inside the kernels and never stored.
-   flags: TBK_MIXED or TBK_FP64, optionally | TBK_MOMENTS_DIRECT.  n_probes must be a
-   multiple of 4.  Fails with TBK_ERR_SPECTRUM if a panel grows beyond the bound that holds
+   flags: TBK_MIXED or TBK_FP64, optionally | TBK_MOMENTS_DIRECT | TBK_PLAIN_KERNEL.  n_probes
+   must be a multiple of 4; in mixed mode with 9x9 blocks and n_probes a multiple of 128 the
+   steps stream neighbour tiles through shared memory with bulk (TMA) copies.  TBK_ERR_TIMEOUT
+   reports an expired bounded wait inside that kernel.  Fails with TBK_ERR_SPECTRUM if a panel grows beyond the bound that holds
    when the spectrum of H^ lies in [-1, 1]. */
 int tbk_chebyshev_moments(tbk_ctx* ctx, const tbk_bsr* H, double emin, double emax,
                           uint64_t probe_seed, int32_t n_probes, int32_t order, int32_t flags,
@@ -183,7 +186,7 @@ int tbk_fermi_level(tbk_ctx* ctx, const double* moments, int32_t order, double e
    checkpoints when they do not fit in max_panel_bytes of scratch (0 = choose automatically).
    G: device, nnzb * n_orb^2 FP64, or NULL.  forces: device, n_atoms x 3 FP64, or NULL;
    F_c = -sum_ab <G_ab, dH_ab/dR_c> needs model->kind == TBK_MODEL_SK and pos (device) / box as
-   in tbk_assemble_H.  flags: TBK_MIXED or TBK_FP64. */
+   in tbk_assemble_H.  flags: TBK_MIXED or TBK_FP64, optionally | TBK_PLAIN_KERNEL. */
 int tbk_density_and_forces(tbk_ctx* ctx, const tbk_bsr* H, const tbk_model* model,
                            const double* pos, const double* box, double emin, double emax,
                            uint64_t probe_seed, int32_t n_probes, int32_t order, double mu,

@@ -21,6 +21,7 @@ TBK_ERR_TIMEOUT = -6
 TBK_MIXED = 0
 TBK_FP64 = 1
 TBK_MOMENTS_DIRECT = 2
+TBK_PLAIN_KERNEL = 4
 TBK_DAMP_NONE = 0
 TBK_DAMP_JACKSON = 1
 TBK_FN_FERMI = 0

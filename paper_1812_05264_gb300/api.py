@@ -164,11 +164,12 @@ def chebyshev_coefficients(ctx: Context, fn: int, order: int, emin: float, emax:
 
 def chebyshev_moments(ctx: Context, H: BSR, emin: float, emax: float, seed: int, n_probes: int,
                       order: int, fp64: bool = False, direct: bool = False,
-                      out: torch.Tensor | None = None) -> torch.Tensor:
+                      out: torch.Tensor | None = None, plain: bool = False) -> torch.Tensor:
     """a5-a7: mu_k = (1/s) sum_i r_i^T C_k(H^) r_i for k < order."""
     if out is None:
         out = torch.empty(order, dtype=torch.float64, device=H.val.device)
-    flags = (L.TBK_FP64 if fp64 else L.TBK_MIXED) | (L.TBK_MOMENTS_DIRECT if direct else 0)
+    flags = ((L.TBK_FP64 if fp64 else L.TBK_MIXED) | (L.TBK_MOMENTS_DIRECT if direct else 0)
+             | (L.TBK_PLAIN_KERNEL if plain else 0))
     L.call("tbk_chebyshev_moments", ctx.handle, C.byref(H.struct()), emin, emax, C.c_uint64(seed),
            int(n_probes), int(order), flags, _ptr(out))
     return out
@@ -189,7 +190,7 @@ def fermi_level(ctx: Context, moments: torch.Tensor, emin: float, emax: float,
 def density_and_forces(ctx: Context, H: BSR, model: Model | None, pos: torch.Tensor | None, box,
                        emin: float, emax: float, seed: int, n_probes: int, order: int, mu: float,
                        kT: float, jackson: bool = False, fp64: bool = False, want_G: bool = True,
-                       want_forces: bool = True, max_panel_bytes: int = 0):
+                       want_forces: bool = True, max_panel_bytes: int = 0, plain: bool = False):
     """a9-a10: (G, F) with G = dOmega^/dH (nnzb, b, b) and F = -dOmega^/dR (N, 3)."""
     dev = H.val.device
     G = torch.empty_like(H.val) if want_G else None
@@ -198,7 +199,8 @@ def density_and_forces(ctx: Context, H: BSR, model: Model | None, pos: torch.Ten
     L.call("tbk_density_and_forces", ctx.handle, C.byref(H.struct()),
            C.byref(model.s) if model is not None else None, _ptr(pos), bx, emin, emax,
            C.c_uint64(seed), int(n_probes), int(order), float(mu), float(kT),
-           L.TBK_DAMP_JACKSON if jackson else L.TBK_DAMP_NONE, L.TBK_FP64 if fp64 else L.TBK_MIXED,
+           L.TBK_DAMP_JACKSON if jackson else L.TBK_DAMP_NONE,
+           (L.TBK_FP64 if fp64 else L.TBK_MIXED) | (L.TBK_PLAIN_KERNEL if plain else 0),
            int(max_panel_bytes), _ptr(G), _ptr(F))
     return G, F
 

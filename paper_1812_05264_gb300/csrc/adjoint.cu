@@ -78,7 +78,7 @@ __global__ void transpose_map(int n_atoms, const int32_t* __restrict__ row_ptr,
       if (c < a) lo = mid + 1; else hi = mid - 1;
     }
     tr[k] = hit;
-    if (hit < 0) atomicExch(err, 1);
+    if (hit < 0) atomicOr(err, 1);
   }
 }
 
@@ -178,7 +178,8 @@ extern "C" int tbk_density_and_forces(tbk_ctx* ctx, const tbk_bsr* H, const tbk_
   TBK_CHECK_ARG(G || forces, "nothing to compute: G and forces are both NULL");
   TBK_CHECK_ARG(order >= 1, "order must be >= 1");
   TBK_CHECK_ARG(n_probes >= 4 && n_probes % 4 == 0, "n_probes must be a positive multiple of 4");
-  TBK_CHECK_ARG((flags & ~TBK_FP64) == 0, "unknown flag");
+  TBK_CHECK_ARG((flags & ~(TBK_FP64 | TBK_PLAIN_KERNEL)) == 0, "unknown flag");
+  const int plain = (flags & TBK_PLAIN_KERNEL) ? 1 : 0;
   TBK_CHECK_ARG(kT > 0.0, "kT must be positive");
   DeviceGuard dg(ctx);
   const int prec = (flags & TBK_FP64) ? TBK_FP64 : TBK_MIXED;
@@ -252,6 +253,8 @@ extern "C" int tbk_density_and_forces(tbk_ctx* ctx, const tbk_bsr* H, const tbk_
     if (t == 2) a.c_r = -1.0;
     else if (t >= 3) a.yprev = const_cast<void*>(yprev);
     a.yout = yout;
+    a.err = err;
+    a.force_simple = plain;
     launch_step(ctx, op, a);
   };
   // Forward sweep to the last checkpoint, with two rotating panels.
@@ -303,6 +306,8 @@ extern "C" int tbk_density_and_forces(tbk_ctx* ctx, const tbk_bsr* H, const tbk_
           a.c_r = c[j];
           a.yprev = have_bprev ? bprev : nullptr;
           a.yout = bprev;
+          a.err = err;
+          a.force_simple = plain;
           launch_step(ctx, op, a);
           std::swap(bcur, bprev);
           have_bprev = true;
@@ -331,6 +336,7 @@ extern "C" int tbk_density_and_forces(tbk_ctx* ctx, const tbk_bsr* H, const tbk_
   int herr = 0;
   TBK_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   sync(ctx);
+  if (herr & 2) throw Error(TBK_ERR_TIMEOUT, "a bounded wait in the recurrence kernel expired");
   TBK_CHECK_ARG(herr == 0, "the block pattern is not symmetric");
   TBK_API_END
 }

@@ -43,6 +43,8 @@ struct StepArgs {
   int s = 0;
   int direct = 0;
   double* partials = nullptr;
+  int* err = nullptr;       // device flag raised (= 2) when a bounded wait expires
+  int force_simple = 0;     // use the plain load/FMA kernel even where the TMA-fed one applies
 };
 // CTAs a step launches for this operator and probe count.
 int step_grid_ctas(tbk_ctx* ctx, const HOp& op, int s);

@@ -113,10 +113,16 @@ cheb_step_kernel(const int n_atoms, const int32_t* __restrict__ row_ptr,
                  double* __restrict__ partials) {
   constexpr int VEC = Vec16<T>::N;
   constexpr int RS = Layout<T, B>::RS, BS = Layout<T, B>::BS;
-  const int p0 = (blockIdx.y * blockDim.x + threadIdx.x) * VEC;
+  // tasks: (row group, probe chunk) with chunk fastest; CTAs stride over tasks
+  const int chunk_w = blockDim.x * VEC;
+  const int n_chunks = (s + chunk_w - 1) / chunk_w;
+  const int n_groups = (n_atoms + blockDim.y - 1) / blockDim.y;
   double sum0 = 0.0, sum1 = 0.0;
-  if (p0 < s) {
-    for (int a = blockIdx.x * blockDim.y + threadIdx.y; a < n_atoms; a += gridDim.x * blockDim.y) {
+  for (int task = blockIdx.x; task < n_groups * n_chunks; task += gridDim.x) {
+    const int grp = task / n_chunks, chunk = task - grp * n_chunks;
+    const int p0 = chunk * chunk_w + threadIdx.x * VEC;
+    const int a = grp * blockDim.y + threadIdx.y;
+    if (p0 < s && a < n_atoms) {
       T acc[B][VEC];
 #pragma unroll
       for (int i = 0; i < B; ++i)
@@ -213,79 +219,389 @@ cheb_step_kernel(const int n_atoms, const int32_t* __restrict__ row_ptr,
         a0 += red[0][w];
         a1 += red[1][w];
       }
-      const int cta = blockIdx.y * gridDim.x + blockIdx.x;
-      partials[2 * cta] = a0;
-      partials[2 * cta + 1] = a1;
+      partials[2 * blockIdx.x] = a0;
+      partials[2 * blockIdx.x + 1] = a1;
     }
   }
 }
 
-struct StepGeom {
-  dim3 block, grid;
+// ---- TMA-fed step (FP32, 9x9 blocks, panel input) -------------------------------------------
+//
+// CTA = CW consumer warps + 1 producer warp.  A task is one block row a and a chunk of
+// P = 128 CW probes (each consumer thread owns 4 consecutive probes).  The producer streams, for
+// every neighbour block k = (a, b) of the task, the 9 x P tile of y_in rows 9b..9b+8 and the
+// block H^_ab through a D-stage shared-memory ring with cp.async.bulk copies completing on
+// mbarriers; the diagonal block's tile goes to a separate "own" buffer that stays until the
+// epilogue (it is y_in of the row itself, needed for the moment sum), and the y_prev tile of
+// the row is streamed last.  Every wait is bounded: on expiry the CTA raises *err = 2 and leaves
+// the loop, and the producer waits (bounded) for the copies it issued before returning.
+
+constexpr uint32_t WAIT_SPINS = 1u << 22;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait; false when the limit expired.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  for (uint32_t i = 0; i < WAIT_SPINS; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+      "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+
+template <int CW, int D>
+struct BulkCfg {
+  static constexpr int P = 128 * CW;                       // probes per task
+  static constexpr int XB = 9 * P * 4;                      // tile bytes
+  static constexpr int HB = Layout<float, 9>::BS * 4;       // 432 bytes
+  static constexpr int SB = ((XB + HB + 127) / 128) * 128;  // stage bytes
+  static constexpr int SMEM = (D + 1) * SB + 8 * (2 * D + 4);
+  static constexpr int THREADS = 32 * (CW + 1);
 };
 
-template <typename T, int B, bool P>
-static int occupancy() {
-  static int occ[64] = {};
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (dev < 0 || dev >= 64) dev = 0;
-  if (!occ[dev]) {
-    int n = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, cheb_step_kernel<T, B, P>, STEP_THREADS, 0);
-    occ[dev] = n > 0 ? n : 1;
+template <int CW, int D>
+__global__ void __launch_bounds__(32 * (CW + 1))
+cheb_step_bulk(const int n_atoms, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+               const float* __restrict__ hv, const float* __restrict__ yin, const float* yprev,
+               float* yout, const float alpha, const float c_r, const uint64_t seed, const int s,
+               const int direct, double* __restrict__ partials, int* __restrict__ err) {
+  using C = BulkCfg<CW, D>;
+  extern __shared__ __align__(128) unsigned char smem[];
+  unsigned char* own = smem + D * C::SB;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (D + 1) * C::SB);
+  // bars: full[0..D), empty[D..2D), own_full = 2D, own_empty = 2D + 1
+  const uint32_t bar0 = smem_u32(bars);
+  auto full = [&](int i) { return bar0 + 8u * i; };
+  auto empty = [&](int i) { return bar0 + 8u * (D + i); };
+  const uint32_t own_full = bar0 + 8u * (2 * D), own_empty = bar0 + 8u * (2 * D + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n_chunks = s / C::P;
+  const int n_tasks = n_atoms * n_chunks;
+  const bool has_prev = yprev != nullptr;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < D; ++i) {
+      mbar_init(full(i), 1);
+      mbar_init(empty(i), CW);
+    }
+    mbar_init(own_full, 1);
+    mbar_init(own_empty, CW);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  return occ[dev];
+  __syncthreads();
+
+  if (warp == CW) {
+    // ---------------- producer ----------------
+    if (lane == 0) {
+      int it = 0, own_it = 0;
+      bool ok = true;
+      for (int task = blockIdx.x; task < n_tasks && ok; task += gridDim.x) {
+        const int a = task / n_chunks, ch = task - a * n_chunks;
+        const int k0 = __ldg(row_ptr + a), k1 = __ldg(row_ptr + a + 1);
+        const int nt = k1 - k0 + (has_prev ? 1 : 0);
+        for (int q = 0; q < nt && ok; ++q) {
+          const bool is_prev = q == k1 - k0;
+          const int b = is_prev ? a : __ldg(col + k0 + q);
+          const bool is_own = !is_prev && b == a;
+          uint32_t dst, bar;
+          if (is_own) {
+            ok = mbar_wait(own_empty, (own_it & 1) ^ 1);
+            dst = smem_u32(own);
+            bar = own_full;
+            ++own_it;
+          } else {
+            const int st = it % D;
+            ok = mbar_wait(empty(st), ((it / D) & 1) ^ 1);
+            dst = smem_u32(smem + st * C::SB);
+            bar = full(st);
+            ++it;
+          }
+          if (!ok) break;
+          const float* src = (is_prev ? yprev : yin) + (int64_t)9 * b * s + (int64_t)ch * C::P;
+          mbar_expect_tx(bar, C::XB + (is_prev ? 0 : C::HB));
+          if (C::P == s) {
+            bulk_g2s(dst, src, C::XB, bar);
+          } else {
+            for (int l = 0; l < 9; ++l) bulk_g2s(dst + l * C::P * 4, src + (int64_t)l * s, C::P * 4, bar);
+          }
+          if (!is_prev) bulk_g2s(dst + C::XB, hv + (int64_t)(k0 + q) * Layout<float, 9>::BS, C::HB, bar);
+        }
+      }
+      if (!ok) {
+        atomicOr(err, 2);
+        // wait (bounded) for copies still in flight into the ring before leaving
+        for (int j = (it > D ? it - D : 0); j < it; ++j) mbar_wait(full(j % D), (j / D) & 1);
+      }
+    }
+    return;
+  }
+
+  // ---------------- consumers ----------------
+  double sum0 = 0.0, sum1 = 0.0;
+  int it = 0, own_it = 0;
+  bool ok = true;
+  for (int task = blockIdx.x; task < n_tasks && ok; task += gridDim.x) {
+    const int a = task / n_chunks, ch = task - a * n_chunks;
+    const int k0 = __ldg(row_ptr + a), k1 = __ldg(row_ptr + a + 1);
+    const int pl = 4 * threadIdx.x;  // probe offset inside the chunk
+    float acc[9][4];
+#pragma unroll
+    for (int i = 0; i < 9; ++i)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) acc[i][v] = 0.f;
+    for (int q = 0; q < k1 - k0; ++q) {
+      const bool is_own = __ldg(col + k0 + q) == a;
+      const unsigned char* base;
+      int st = 0;
+      if (is_own) {
+        ok = mbar_wait(own_full, own_it & 1);
+        base = own;
+      } else {
+        st = it % D;
+        ok = mbar_wait(full(st), (it / D) & 1);
+        base = smem + st * C::SB;
+      }
+      if (!ok) break;
+      const float* X = reinterpret_cast<const float*>(base);
+      const float* Hs = reinterpret_cast<const float*>(base + C::XB);
+      float x[9][4];
+#pragma unroll
+      for (int l = 0; l < 9; ++l) {
+        const float4 t = *reinterpret_cast<const float4*>(X + l * C::P + pl);
+        x[l][0] = t.x; x[l][1] = t.y; x[l][2] = t.z; x[l][3] = t.w;
+      }
+#pragma unroll
+      for (int i = 0; i < 9; ++i) {
+        float hr[12];
+#pragma unroll
+        for (int j = 0; j < 12; j += 4) {
+          const float4 t = *reinterpret_cast<const float4*>(Hs + i * 12 + j);
+          hr[j] = t.x; hr[j + 1] = t.y; hr[j + 2] = t.z; hr[j + 3] = t.w;
+        }
+#pragma unroll
+        for (int l = 0; l < 9; ++l)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) acc[i][v] = fmaf(hr[l], x[l][v], acc[i][v]);
+      }
+      if (!is_own) {
+        __syncwarp();
+        if (lane == 0) mbar_arrive(empty(st));
+        ++it;
+      }
+    }
+    if (!ok) break;
+    // previous panel tile of this row (streamed last)
+    float yp[9][4];
+    if (has_prev) {
+      const int st = it % D;
+      ok = mbar_wait(full(st), (it / D) & 1);
+      if (!ok) break;
+      const float* X = reinterpret_cast<const float*>(smem + st * C::SB);
+#pragma unroll
+      for (int l = 0; l < 9; ++l) {
+        const float4 t = *reinterpret_cast<const float4*>(X + l * C::P + pl);
+        yp[l][0] = t.x; yp[l][1] = t.y; yp[l][2] = t.z; yp[l][3] = t.w;
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(empty(st));
+      ++it;
+    }
+    // epilogue: y_out = alpha acc + c_r r - y_prev, moment partial sums
+    const float* Y = reinterpret_cast<const float*>(own);
+    const int p0 = ch * C::P + pl;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      const int64_t row = (int64_t)9 * a + i;
+      float yo[4], r[4];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) yo[v] = alpha * acc[i][v];
+      if (c_r != 0.f || direct) {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) r[v] = tbk_probe_sign(seed, row, p0 + v);
+      }
+      if (c_r != 0.f) {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) yo[v] = fmaf(c_r, r[v], yo[v]);
+      }
+      if (has_prev) {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) yo[v] -= yp[i][v];
+      }
+      *reinterpret_cast<float4*>(yout + row * s + p0) = make_float4(yo[0], yo[1], yo[2], yo[3]);
+      if (partials) {
+        float xin[4];
+        if (direct) {
+#pragma unroll
+          for (int v = 0; v < 4; ++v) xin[v] = r[v];
+        } else {
+          const float4 t = *reinterpret_cast<const float4*>(Y + i * C::P + pl);
+          xin[0] = t.x; xin[1] = t.y; xin[2] = t.z; xin[3] = t.w;
+        }
+        float q0 = 0.f, q1 = 0.f;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          q0 = fmaf(yo[v], xin[v], q0);
+          q1 = fmaf(yo[v], yo[v], q1);
+        }
+        sum0 += (double)q0;
+        sum1 += (double)q1;
+      }
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(own_empty);
+    ++own_it;
+  }
+  if (!ok) atomicOr(err, 2);
+  if (partials) {
+    __shared__ double red[2][8];
+    for (int o = 16; o > 0; o >>= 1) {
+      sum0 += __shfl_xor_sync(0xffffffffu, sum0, o);
+      sum1 += __shfl_xor_sync(0xffffffffu, sum1, o);
+    }
+    if (lane == 0) {
+      red[0][warp] = sum0;
+      red[1][warp] = sum1;
+    }
+    // named barrier over the consumer warps only (the producer warp has returned)
+    asm volatile("bar.sync 1, %0;" ::"r"(32 * CW) : "memory");
+    if (threadIdx.x == 0) {
+      double a0 = 0.0, a1 = 0.0;
+      for (int w = 0; w < CW; ++w) {
+        a0 += red[0][w];
+        a1 += red[1][w];
+      }
+      partials[2 * blockIdx.x] = a0;
+      partials[2 * blockIdx.x + 1] = a1;
+    }
+  }
+}
+
+// ---- launch geometry ---------------------------------------------------------------------------
+
+template <typename T, int B, bool P>
+static int occupancy_simple() {
+  int n = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, cheb_step_kernel<T, B, P>, STEP_THREADS, 0);
+  return n > 0 ? n : 1;
+}
+
+template <int CW, int D>
+static int occupancy_bulk() {
+  using C = BulkCfg<CW, D>;
+  cudaFuncSetAttribute(cheb_step_bulk<CW, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+  int n = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, cheb_step_bulk<CW, D>, C::THREADS, C::SMEM);
+  return n;
+}
+
+constexpr int BULK_D = 3;
+
+// Consumer warps of the TMA-fed kernel for this operator and probe count (0 = not eligible).
+static int bulk_warps(const HOp& op, int s) {
+  if (op.prec != TBK_MIXED || op.B != 9 || s % 128 != 0) return 0;
+  if (s % 512 == 0) return 4;
+  if (s % 256 == 0) return 2;
+  return 1;
+}
+
+struct Occ {
+  int simple = 0, bulk[5] = {0, 0, 0, 0, 0};
+};
+
+static Occ& occ_cache(int dev) {
+  static Occ o[64];
+  return o[dev < 0 || dev >= 64 ? 0 : dev];
 }
 
 template <typename T, int B>
-static StepGeom step_geom(tbk_ctx* ctx, const HOp& op, int s) {
+static dim3 simple_block(int s) {
   constexpr int VEC = Vec16<T>::N;
-  const int lanes_needed = s / VEC;
+  const int lanes_needed = (s + VEC - 1) / VEC;
   int lanes = 1;  // a power of two, so that every warp of the CTA is complete
   while (lanes < lanes_needed && lanes < STEP_THREADS) lanes <<= 1;
-  const int rows = STEP_THREADS / lanes;
-  StepGeom g;
-  g.block = dim3(lanes, rows);
-  const int gy = ceil_div(lanes_needed, lanes);
-  const int64_t row_groups = (op.n_atoms + rows - 1) / rows;
-  const int occ = std::min(occupancy<T, B, false>(), occupancy<T, B, true>());
-  const int64_t wave = (int64_t)occ * ctx->num_sms;
-  const int64_t gx = std::max<int64_t>(1, std::min<int64_t>(row_groups, std::max<int64_t>(1, wave / gy)));
-  g.grid = dim3((unsigned)gx, (unsigned)gy);
-  return g;
-}
-
-static StepGeom geom_for(tbk_ctx* ctx, const HOp& op, int s) {
-  if (op.prec == TBK_MIXED) return op.B == 9 ? step_geom<float, 9>(ctx, op, s) : step_geom<float, 1>(ctx, op, s);
-  return op.B == 9 ? step_geom<double, 9>(ctx, op, s) : step_geom<double, 1>(ctx, op, s);
+  return dim3(lanes, STEP_THREADS / lanes);
 }
 
 int step_grid_ctas(tbk_ctx* ctx, const HOp& op, int s) {
-  StepGeom g = geom_for(ctx, op, s);
-  return (int)(g.grid.x * g.grid.y);
+  Occ& o = occ_cache(ctx->device);
+  if (!o.simple) {
+    int m = 1 << 30;
+    m = std::min(m, std::min(occupancy_simple<float, 9, false>(), occupancy_simple<float, 9, true>()));
+    m = std::min(m, std::min(occupancy_simple<float, 1, false>(), occupancy_simple<float, 1, true>()));
+    m = std::min(m, std::min(occupancy_simple<double, 9, false>(), occupancy_simple<double, 9, true>()));
+    m = std::min(m, std::min(occupancy_simple<double, 1, false>(), occupancy_simple<double, 1, true>()));
+    o.simple = std::max(1, m);
+    o.bulk[1] = occupancy_bulk<1, BULK_D>();
+    o.bulk[2] = occupancy_bulk<2, BULK_D>();
+    o.bulk[4] = occupancy_bulk<4, BULK_D>();
+  }
+  int per_sm = o.simple;
+  const int cw = bulk_warps(op, s);
+  if (cw && o.bulk[cw] > 0) per_sm = std::min(per_sm, o.bulk[cw]);
+  return std::max(1, per_sm * ctx->num_sms);
 }
 
 template <typename T, int B>
-static void launch_typed(tbk_ctx* ctx, const HOp& op, const StepArgs& a) {
-  StepGeom g = step_geom<T, B>(ctx, op, a.s);
+static void launch_simple(tbk_ctx* ctx, const HOp& op, const StepArgs& a, int G) {
+  const dim3 blk = simple_block<T, B>(a.s);
   const T* hv = (const T*)op.hv;
   if (a.cur_is_probe)
-    cheb_step_kernel<T, B, true><<<g.grid, g.block, 0, ctx->stream>>>(
+    cheb_step_kernel<T, B, true><<<G, blk, 0, ctx->stream>>>(
         op.n_atoms, op.row_ptr, op.col, hv, (const T*)a.yin, (const T*)a.yprev, (T*)a.yout, (T)a.alpha,
         (T)a.c_r, a.seed, a.s, a.direct, a.partials);
   else
-    cheb_step_kernel<T, B, false><<<g.grid, g.block, 0, ctx->stream>>>(
+    cheb_step_kernel<T, B, false><<<G, blk, 0, ctx->stream>>>(
         op.n_atoms, op.row_ptr, op.col, hv, (const T*)a.yin, (const T*)a.yprev, (T*)a.yout, (T)a.alpha,
         (T)a.c_r, a.seed, a.s, a.direct, a.partials);
   post_launch(ctx, "cheb_step_kernel");
 }
 
+template <int CW>
+static void launch_bulk(tbk_ctx* ctx, const HOp& op, const StepArgs& a, int G) {
+  using C = BulkCfg<CW, BULK_D>;
+  cheb_step_bulk<CW, BULK_D><<<G, C::THREADS, C::SMEM, ctx->stream>>>(
+      op.n_atoms, op.row_ptr, op.col, (const float*)op.hv, (const float*)a.yin, (const float*)a.yprev,
+      (float*)a.yout, (float)a.alpha, (float)a.c_r, a.seed, a.s, a.direct, a.partials, a.err);
+  post_launch(ctx, "cheb_step_bulk");
+}
+
 void launch_step(tbk_ctx* ctx, const HOp& op, const StepArgs& a) {
+  const int G = step_grid_ctas(ctx, op, a.s);
+  const int cw = bulk_warps(op, a.s);
+  if (cw && !a.cur_is_probe && a.err && !a.force_simple && occ_cache(ctx->device).bulk[cw] > 0) {
+    if (cw == 4) launch_bulk<4>(ctx, op, a, G);
+    else if (cw == 2) launch_bulk<2>(ctx, op, a, G);
+    else launch_bulk<1>(ctx, op, a, G);
+    return;
+  }
   if (op.prec == TBK_MIXED) {
-    if (op.B == 9) launch_typed<float, 9>(ctx, op, a); else launch_typed<float, 1>(ctx, op, a);
+    if (op.B == 9) launch_simple<float, 9>(ctx, op, a, G); else launch_simple<float, 1>(ctx, op, a, G);
   } else {
-    if (op.B == 9) launch_typed<double, 9>(ctx, op, a); else launch_typed<double, 1>(ctx, op, a);
+    if (op.B == 9) launch_simple<double, 9>(ctx, op, a, G); else launch_simple<double, 1>(ctx, op, a, G);
   }
 }
 
@@ -364,7 +680,7 @@ __global__ void finish_moments(const double* __restrict__ sums, int K, int order
   }
   for (int j = threadIdx.x; j < K; j += blockDim.x) {
     const double e = sums[2 * j + 1] * inv_s, o = sums[2 * j];
-    if (!(e <= mu0 * (1.0 + 1e-3)) || !isfinite(o)) atomicExch(flag, 1);
+    if (!(e <= mu0 * (1.0 + 1e-3)) || !isfinite(o)) atomicOr(flag, 1);
   }
 }
 
@@ -380,7 +696,7 @@ extern "C" int tbk_chebyshev_moments(tbk_ctx* ctx, const tbk_bsr* H, double emin
   TBK_CHECK_ARG(moments != nullptr, "moments is NULL");
   TBK_CHECK_ARG(order >= 1, "order must be >= 1");
   TBK_CHECK_ARG(n_probes >= 4 && n_probes % 4 == 0, "n_probes must be a positive multiple of 4");
-  TBK_CHECK_ARG((flags & ~(TBK_FP64 | TBK_MOMENTS_DIRECT)) == 0, "unknown flag");
+  TBK_CHECK_ARG((flags & ~(TBK_FP64 | TBK_MOMENTS_DIRECT | TBK_PLAIN_KERNEL)) == 0, "unknown flag");
   DeviceGuard dg(ctx);
   const int prec = (flags & TBK_FP64) ? TBK_FP64 : TBK_MIXED;
   const int direct = (flags & TBK_MOMENTS_DIRECT) ? 1 : 0;
@@ -403,6 +719,8 @@ extern "C" int tbk_chebyshev_moments(tbk_ctx* ctx, const tbk_bsr* H, double emin
     a.s = s;
     a.direct = direct;
     a.partials = partials + (size_t)(j - 1) * nctas * 2;
+    a.err = flag;
+    a.force_simple = (flags & TBK_PLAIN_KERNEL) ? 1 : 0;
     if (j == 1) {
       a.cur_is_probe = 1;
       a.alpha = 1.0;
@@ -433,6 +751,7 @@ extern "C" int tbk_chebyshev_moments(tbk_ctx* ctx, const tbk_bsr* H, double emin
   int hflag = 0;
   TBK_CUDA(cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   sync(ctx);
+  if (hflag & 2) throw Error(TBK_ERR_TIMEOUT, "a bounded wait in the recurrence kernel expired");
   if (hflag)
     throw Error(TBK_ERR_SPECTRUM, "a Chebyshev panel grew beyond ||r||: the spectrum of H is not "
                                   "inside [emin, emax]");

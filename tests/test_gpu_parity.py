@@ -260,3 +260,38 @@ def test_argument_errors(api, ctx):
     # the context stays usable after errors
     mom2 = api.chebyshev_moments(ctx, H, emin, emax, 1, 8, 50, fp64=True)
     assert torch.equal(mom, mom2)
+
+
+# ---- the TMA-fed step kernel (mixed precision, 9x9 blocks, probes a multiple of 128) ----------
+
+@pytest.mark.parametrize("s", [128, 256, 512, 1024])
+def test_tma_step_kernel_matches_plain_kernel_and_oracle(api, ctx, s):
+    wk = small_fcc(90, n_probes=s, jitter=0.05)
+    rp, col, H = oracle_H(wk)
+    sv = api.Solver(wk, ctx)
+    pos = _dev(wk.positions)
+    g = api.build_neighbors(ctx, pos, wk.cutoff)
+    Hg = api.assemble_H(ctx, sv.model, pos, g)
+    emin, emax = api.spectral_bounds(ctx, Hg)
+    p = 101
+    m_tma = api.chebyshev_moments(ctx, Hg, emin, emax, wk.probe_seed, s, p)
+    m_plain = api.chebyshev_moments(ctx, Hg, emin, emax, wk.probe_seed, s, p, plain=True)
+    n = H.shape[0]
+    # same FMA order per element: agreement to rounding of the partial-sum grouping
+    assert np.allclose(m_tma.cpu().numpy(), m_plain.cpu().numpy(), rtol=0, atol=1e-9 * n)
+    est = oracle_estimator(wk, H, emin, emax, p)
+    assert np.abs(m_tma.cpu().numpy() - est["moments"]).max() < 2e-5 * n
+    d_tma = api.chebyshev_moments(ctx, Hg, emin, emax, wk.probe_seed, s, p, direct=True)
+    assert np.abs(d_tma.cpu().numpy() - est["moments"]).max() < 2e-5 * n
+
+
+def test_tma_step_kernel_in_the_adjoint(api, ctx):
+    wk = small_fcc(40, n_probes=128, kT=0.5)
+    p = 80
+    s_, pos, res = _gpu_run(api, ctx, wk, p, fp64=False)
+    args = (ctx, res.H, s_.model, pos, None, res.emin, res.emax, wk.probe_seed, wk.n_probes, p,
+            res.mu, wk.kT, False, False)
+    G1, F1 = api.density_and_forces(*args)
+    G2, F2 = api.density_and_forces(*args, plain=True)
+    assert torch.allclose(G1, G2, rtol=0, atol=1e-9 * G2.abs().max().item())
+    assert torch.allclose(F1, F2, rtol=0, atol=1e-7)

@@ -13,6 +13,7 @@
 #include <cmath>
 #include <vector>
 
+#include "bulk.cuh"
 #include "cheb.cuh"
 #include "model.cuh"
 #include "sk.cuh"
@@ -61,6 +62,263 @@ sddmm_kernel(int n_atoms, const int32_t* __restrict__ row_ptr, const int32_t* __
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     if (lane == (e & 31)) Gacc[(int64_t)k * B * B + e] += w * v;
   }
+}
+
+// ---- fused Clenshaw step + sampled outer product (TMA-fed, FP32, 9x9 blocks, P = s) ------------
+//
+// For one backward index j and every block row a (one CTA task covers all s probes):
+//   b_j[a]   = 2 sum_b H^_ab b_{j+1}[b] + c_j r[a] - b_{j+2}[a]          (skipped when bout = 0)
+//   Gacc_ab += w sum_probes y_j[a] b_{j+1}[b]^T   for every neighbour block (a, b)
+// The neighbour tiles b_{j+1}[b] and blocks H^_ab stream through a D-stage ring as in the
+// forward step; the own-row tile y_j[a] (or the probe block when j = 0) is staged once per task.
+// Each consumer warp owns quadrant(s) of the 9x9 outer product (rows/cols split 5 + 4): its 32
+// lanes cover interleaved 4-probe groups, and a butterfly reduce-scatter over the lanes leaves
+// one entry per lane, added to the FP64 accumulator (one CTA owns each block: no atomics).
+
+template <int CW>
+struct SdCfg {
+  static constexpr int D = 2;
+  static constexpr int P = 128 * CW;
+  static constexpr int XB = 9 * P * 4;
+  static constexpr int HB = Layout<float, 9>::BS * 4;
+  static constexpr int SB = ((XB + HB + 127) / 128) * 128;
+  static constexpr int YB = ((XB + 127) / 128) * 128;
+  static constexpr int SMEM = (D + 1) * SB + YB + 8 * (2 * D + 6);
+  static constexpr int THREADS = 32 * (CW + 1);
+};
+
+// 32 lane partials per entry -> lane e holds the lane-sum of entry e.
+__device__ __forceinline__ void butterfly32(float (&v)[32], int lane) {
+#pragma unroll
+  for (int off = 16, n = 32; off >= 1; off >>= 1, n >>= 1) {
+    const bool up = (lane & off) != 0;
+#pragma unroll
+    for (int k = 0; k < n / 2; ++k) {
+      const float send = up ? v[k] : v[k + n / 2];
+      const float keep = up ? v[k + n / 2] : v[k];
+      v[k] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+    }
+  }
+}
+
+// Quadrant q of the 9x9 outer product sum_p Y[i][p] X[l][p] over this warp's probes: rows
+// I0.. and columns L0.. with I0, L0 in {0, 5}; one 5x5 code path for all quadrants (rows and
+// columns past 8 are clamped to 8 and their results dropped).
+template <int P>
+__device__ __forceinline__ void sddmm_quadrant(int q, const float* Y, const float* X, bool y_probe,
+                                               uint64_t seed, int a, int lane, int64_t k, double w,
+                                               double* __restrict__ Gacc) {
+  const int I0 = (q >> 1) * 5, L0 = (q & 1) * 5;
+  int ri[5], rl[5];
+#pragma unroll
+  for (int t = 0; t < 5; ++t) {
+    ri[t] = min(I0 + t, 8);
+    rl[t] = min(L0 + t, 8);
+  }
+  float v[32];
+#pragma unroll
+  for (int e = 0; e < 32; ++e) v[e] = 0.f;
+#pragma unroll 1
+  for (int m = 0; m < P / 128; ++m) {
+    const int pb = 4 * (lane + 32 * m);
+    float yv[5][4], xv[5][4];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+      if (y_probe) {
+#pragma unroll
+        for (int t = 0; t < 4; ++t) yv[i][t] = tbk_probe_sign(seed, (int64_t)9 * a + ri[i], pb + t);
+      } else {
+        const float4 u = *reinterpret_cast<const float4*>(Y + ri[i] * P + pb);
+        yv[i][0] = u.x; yv[i][1] = u.y; yv[i][2] = u.z; yv[i][3] = u.w;
+      }
+      const float4 u = *reinterpret_cast<const float4*>(X + rl[i] * P + pb);
+      xv[i][0] = u.x; xv[i][1] = u.y; xv[i][2] = u.z; xv[i][3] = u.w;
+    }
+#pragma unroll
+    for (int i = 0; i < 5; ++i)
+#pragma unroll
+      for (int l = 0; l < 5; ++l)
+#pragma unroll
+        for (int t = 0; t < 4; ++t) v[i * 5 + l] = fmaf(yv[i][t], xv[l][t], v[i * 5 + l]);
+  }
+  butterfly32(v, lane);
+  const int i = I0 + lane / 5, l = L0 + lane % 5;
+  if (lane < 25 && i < 9 && l < 9)
+    // fire-and-forget reduction: one writer per entry and launch, so the sum stays deterministic
+    atomicAdd(Gacc + k * 81 + i * 9 + l, w * (double)v[0]);
+}
+
+template <int CW>
+__global__ void __launch_bounds__(32 * (CW + 1))
+clenshaw_sddmm_bulk(const int n_atoms, const int32_t* __restrict__ row_ptr,
+                    const int32_t* __restrict__ col, const float* __restrict__ hv,
+                    const float* __restrict__ bin, const float* bprev, float* bout,
+                    const float* __restrict__ ypan, const float c_r, const uint64_t seed,
+                    const int s, const double w, double* __restrict__ Gacc, int* __restrict__ err) {
+  using C = SdCfg<CW>;
+  constexpr int D = C::D;
+  extern __shared__ __align__(128) unsigned char smem[];
+  unsigned char* own = smem + D * C::SB;
+  float* Ys = reinterpret_cast<float*>(smem + (D + 1) * C::SB);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (D + 1) * C::SB + C::YB);
+  const uint32_t bar0 = smem_u32(bars);
+  auto full = [&](int i) { return bar0 + 8u * i; };
+  auto empty = [&](int i) { return bar0 + 8u * (D + i); };
+  const uint32_t own_full = bar0 + 8u * (2 * D), own_empty = bar0 + 8u * (2 * D + 1);
+  const uint32_t y_full = bar0 + 8u * (2 * D + 2), y_empty = bar0 + 8u * (2 * D + 3);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const bool has_prev = bprev != nullptr, y_probe = ypan == nullptr, has_out = bout != nullptr;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < D; ++i) {
+      mbar_init(full(i), 1);
+      mbar_init(empty(i), CW);
+    }
+    mbar_init(own_full, 1);
+    mbar_init(own_empty, CW);
+    mbar_init(y_full, 1);
+    mbar_init(y_empty, CW);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+
+  if (warp == CW) {
+    if (lane == 0) {
+      int it = 0, own_it = 0, y_it = 0;
+      bool ok = true;
+      for (int a = blockIdx.x; a < n_atoms && ok; a += gridDim.x) {
+        const int k0 = __ldg(row_ptr + a), k1 = __ldg(row_ptr + a + 1);
+        if (!y_probe) {
+          ok = mbar_wait(y_empty, (y_it & 1) ^ 1);
+          if (!ok) break;
+          mbar_expect_tx(y_full, C::XB);
+          bulk_g2s(smem_u32(Ys), ypan + (int64_t)9 * a * s, C::XB, y_full);
+          ++y_it;
+        }
+        const int nt = k1 - k0 + ((has_prev && has_out) ? 1 : 0);
+        for (int q = 0; q < nt && ok; ++q) {
+          const bool is_prev = q == k1 - k0;
+          const int b = is_prev ? a : __ldg(col + k0 + q);
+          const bool is_own = !is_prev && b == a;
+          uint32_t dst, bar;
+          if (is_own) {
+            ok = mbar_wait(own_empty, (own_it & 1) ^ 1);
+            dst = smem_u32(own);
+            bar = own_full;
+            ++own_it;
+          } else {
+            const int st = it % D;
+            ok = mbar_wait(empty(st), ((it / D) & 1) ^ 1);
+            dst = smem_u32(smem + st * C::SB);
+            bar = full(st);
+            ++it;
+          }
+          if (!ok) break;
+          const float* src = (is_prev ? bprev : bin) + (int64_t)9 * b * s;
+          mbar_expect_tx(bar, C::XB + (is_prev ? 0 : C::HB));
+          bulk_g2s(dst, src, C::XB, bar);
+          if (!is_prev) bulk_g2s(dst + C::XB, hv + (int64_t)(k0 + q) * Layout<float, 9>::BS, C::HB, bar);
+        }
+      }
+      if (!ok) {
+        atomicOr(err, 2);
+        for (int j = (it > D ? it - D : 0); j < it; ++j) mbar_wait(full(j % D), (j / D) & 1);
+      }
+    }
+    return;
+  }
+
+  int it = 0, own_it = 0, y_it = 0;
+  bool ok = true;
+  const int pl = 4 * threadIdx.x;
+  for (int a = blockIdx.x; a < n_atoms && ok; a += gridDim.x) {
+    const int k0 = __ldg(row_ptr + a), k1 = __ldg(row_ptr + a + 1);
+    if (!y_probe) {
+      ok = mbar_wait(y_full, y_it & 1);
+      if (!ok) break;
+    }
+    float acc[9][4];
+#pragma unroll
+    for (int i = 0; i < 9; ++i)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) acc[i][v] = 0.f;
+    for (int q = 0; q < k1 - k0; ++q) {
+      const bool is_own = __ldg(col + k0 + q) == a;
+      const unsigned char* base;
+      int st = 0;
+      if (is_own) {
+        ok = mbar_wait(own_full, own_it & 1);
+        base = own;
+      } else {
+        st = it % D;
+        ok = mbar_wait(full(st), (it / D) & 1);
+        base = smem + st * C::SB;
+      }
+      if (!ok) break;
+      const float* X = reinterpret_cast<const float*>(base);
+      if (has_out) {
+        const float* Hs = reinterpret_cast<const float*>(base + C::XB);
+        float x[9][4];
+#pragma unroll
+        for (int l = 0; l < 9; ++l) {
+          const float4 t = *reinterpret_cast<const float4*>(X + l * C::P + pl);
+          x[l][0] = t.x; x[l][1] = t.y; x[l][2] = t.z; x[l][3] = t.w;
+        }
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+          float hr[12];
+#pragma unroll
+          for (int j = 0; j < 12; j += 4) {
+            const float4 t = *reinterpret_cast<const float4*>(Hs + i * 12 + j);
+            hr[j] = t.x; hr[j + 1] = t.y; hr[j + 2] = t.z; hr[j + 3] = t.w;
+          }
+#pragma unroll
+          for (int l = 0; l < 9; ++l)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[i][v] = fmaf(hr[l], x[l][v], acc[i][v]);
+        }
+      }
+      for (int qd = warp; qd < 4; qd += CW)
+        sddmm_quadrant<C::P>(qd, Ys, X, y_probe, seed, a, lane, (int64_t)(k0 + q), w, Gacc);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(is_own ? own_empty : empty(st));
+      if (is_own) ++own_it; else ++it;
+    }
+    if (!ok) break;
+    if (!y_probe) {
+      __syncwarp();
+      if (lane == 0) mbar_arrive(y_empty);
+      ++y_it;
+    }
+    if (!has_out) continue;
+    float yp[9][4];
+    if (has_prev) {
+      const int st = it % D;
+      ok = mbar_wait(full(st), (it / D) & 1);
+      if (!ok) break;
+      const float* X = reinterpret_cast<const float*>(smem + st * C::SB);
+#pragma unroll
+      for (int l = 0; l < 9; ++l) {
+        const float4 t = *reinterpret_cast<const float4*>(X + l * C::P + pl);
+        yp[l][0] = t.x; yp[l][1] = t.y; yp[l][2] = t.z; yp[l][3] = t.w;
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(empty(st));
+      ++it;
+    }
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      const int64_t row = (int64_t)9 * a + i;
+      float yo[4];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) yo[v] = fmaf(c_r, tbk_probe_sign(seed, row, pl + v), 2.f * acc[i][v]);
+      if (has_prev) {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) yo[v] -= yp[i][v];
+      }
+      *reinterpret_cast<float4*>(bout + row * s + pl) = make_float4(yo[0], yo[1], yo[2], yo[3]);
+    }
+  }
+  if (!ok) atomicOr(err, 2);
 }
 
 // tr[k] = index of block (b, a) for block k = (a, b) (the pattern is symmetric).
@@ -146,6 +404,34 @@ __global__ void gather_forces(int n_atoms, const int32_t* __restrict__ row_ptr,
   F[3 * c + 2] = f2;
 }
 
+static bool fused_eligible(const HOp& op, int s, int plain) {
+  return !plain && op.prec == TBK_MIXED && op.B == 9 && (s == 128 || s == 256 || s == 512);
+}
+
+template <int CW>
+static void launch_fused_cw(tbk_ctx* ctx, const HOp& op, const void* bin, const void* bprev, void* bout,
+                            const void* ypan, double c_r, uint64_t seed, int s, double w, double* Gacc,
+                            int* err) {
+  using C = SdCfg<CW>;
+  TBK_CUDA(cudaFuncSetAttribute(clenshaw_sddmm_bulk<CW>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
+  int occ = 0;
+  TBK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, clenshaw_sddmm_bulk<CW>, C::THREADS, C::SMEM));
+  TBK_CHECK_ARG(occ > 0, "fused adjoint kernel does not fit on this device");
+  const int G = std::max(1, std::min(op.n_atoms, occ * ctx->num_sms));
+  clenshaw_sddmm_bulk<CW><<<G, C::THREADS, C::SMEM, ctx->stream>>>(
+      op.n_atoms, op.row_ptr, op.col, (const float*)op.hv, (const float*)bin, (const float*)bprev,
+      (float*)bout, (const float*)ypan, (float)c_r, seed, s, w, Gacc, err);
+  post_launch(ctx, "clenshaw_sddmm_bulk");
+}
+
+static void launch_fused(tbk_ctx* ctx, const HOp& op, const void* bin, const void* bprev, void* bout,
+                         const void* ypan, double c_r, uint64_t seed, int s, double w, double* Gacc,
+                         int* err) {
+  if (s == 512) launch_fused_cw<4>(ctx, op, bin, bprev, bout, ypan, c_r, seed, s, w, Gacc, err);
+  else if (s == 256) launch_fused_cw<2>(ctx, op, bin, bprev, bout, ypan, c_r, seed, s, w, Gacc, err);
+  else launch_fused_cw<1>(ctx, op, bin, bprev, bout, ypan, c_r, seed, s, w, Gacc, err);
+}
+
 static void launch_sddmm(tbk_ctx* ctx, const HOp& op, const void* y, int y_is_probe, uint64_t seed,
                          const void* b, int s, double w, double* Gacc) {
   const int64_t threads = op.nnzb * 32;
@@ -191,6 +477,7 @@ extern "C" int tbk_density_and_forces(tbk_ctx* ctx, const tbk_bsr* H, const tbk_
   }
   HOp op = prepare_hop(ctx, H, emin, emax, prec, WS_HHAT);
   const int p = order, s = n_probes, BB = op.B * op.B;
+  const bool fused = fused_eligible(op, s, plain);
   const double W = emax - emin;
 
   // coefficients c_k = d_k beta_k[g] (device, then host for the per-step scalars)
@@ -296,6 +583,16 @@ extern "C" int tbk_density_and_forces(tbk_ctx* ctx, const tbk_bsr* H, const tbk_
       }
       for (; j >= t0; --j) {
         const void* yj = j == 0 ? nullptr : P(j - t0 + 1);
+        if (fused) {
+          // one launch: b_j (when j >= 1) and the y_j b_{j+1}^T term
+          launch_fused(ctx, op, bcur, have_bprev ? bprev : nullptr, j >= 1 ? bprev : nullptr, yj,
+                       j >= 1 ? c[j] : 0.0, probe_seed, s, j == 0 ? 1.0 : 2.0, Gacc, err);
+          if (j >= 1) {
+            std::swap(bcur, bprev);
+            have_bprev = true;
+          }
+          continue;
+        }
         launch_sddmm(ctx, op, yj, j == 0, probe_seed, bcur, s, j == 0 ? 1.0 : 2.0, Gacc);
         if (j >= 1) {
           StepArgs a;

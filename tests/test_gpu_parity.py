@@ -285,13 +285,21 @@ def test_tma_step_kernel_matches_plain_kernel_and_oracle(api, ctx, s):
     assert np.abs(d_tma.cpu().numpy() - est["moments"]).max() < 2e-5 * n
 
 
-def test_tma_step_kernel_in_the_adjoint(api, ctx):
-    wk = small_fcc(40, n_probes=128, kT=0.5)
+@pytest.mark.parametrize("s", [128, 256, 512])
+def test_fused_clenshaw_outer_product_kernel(api, ctx, s):
+    """The TMA-fed backward step with the fused y_j b_{j+1}^T term vs the plain kernels and the
+    oracle's estimator forces (mixed precision: 1e-3 eV/A)."""
+    wk = small_fcc(40, n_probes=s, kT=0.5)
     p = 80
+    rp, col, H = oracle_H(wk)
     s_, pos, res = _gpu_run(api, ctx, wk, p, fp64=False)
+    est = oracle_estimator(wk, H, res.emin, res.emax, p)
     args = (ctx, res.H, s_.model, pos, None, res.emin, res.emax, wk.probe_seed, wk.n_probes, p,
-            res.mu, wk.kT, False, False)
+            est["mu"], wk.kT, False, False)
     G1, F1 = api.density_and_forces(*args)
     G2, F2 = api.density_and_forces(*args, plain=True)
-    assert torch.allclose(G1, G2, rtol=0, atol=1e-9 * G2.abs().max().item())
-    assert torch.allclose(F1, F2, rtol=0, atol=1e-7)
+    gmax = G2.abs().max().item()
+    assert torch.allclose(G1, G2, rtol=0, atol=2e-5 * gmax)
+    assert torch.allclose(F1, F2, rtol=0, atol=1e-4)
+    _, F = oracle_estimator_forces(wk, rp, col, est, res.emin, res.emax, p)
+    assert np.abs(F1.cpu().numpy() - F).max() < 1e-3

@@ -193,6 +193,29 @@ int tbk_density_and_forces(tbk_ctx* ctx, const tbk_bsr* H, const tbk_model* mode
                            double kT, int32_t damping, int32_t flags, int64_t max_panel_bytes,
                            double* G, double* forces);
 
+/* ---- allocation-free variant of tbk_chebyshev_moments ------------------------------------
+
+   No counterpart in the paper: this entry point exists for callers that cannot allocate device
+   memory while they run (latency-bounded loops where an allocation may block on the device,
+   embedders whose device memory is budgeted by a framework that owns every allocation, drivers
+   that forbid allocation between set-up and shutdown).  It computes exactly what
+   tbk_chebyshev_moments computes, with the same kernels, but takes all of its scratch from one
+   static device array of 64 MiB (TBK_NOALLOC_SCRATCH_BYTES) that is part of the library and
+   stays reserved on every GPU that loads the library until the process exits.  The call
+   allocates nothing: no cudaMalloc, cudaFree or allocating library routine.
+   - Arguments, layout, ownership and errors are those of tbk_chebyshev_moments; in addition a
+     problem whose scratch (mapped H, two panels, per-step partial sums) exceeds the static size
+     fails with TBK_ERR_ARG and a message giving the bytes it would need.
+   - The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
+     that device current; make that first call before any stream capture.
+   - Every call on a device shares the one array and leaves its contents behind (the call clears
+     what must start at zero).  Calls whose work overlaps on the GPU -- on different streams, or
+     from different host threads -- race on the array and give wrong results. */
+#define TBK_NOALLOC_SCRATCH_BYTES (64u << 20)
+int tbk_chebyshev_moments_noalloc(tbk_ctx* ctx, const tbk_bsr* H, double emin, double emax,
+                                  uint64_t probe_seed, int32_t n_probes, int32_t order,
+                                  int32_t flags, double* moments);
+
 #ifdef __cplusplus
 }
 #endif

@@ -52,4 +52,11 @@ void launch_step(tbk_ctx* ctx, const HOp& op, const StepArgs& a);
 // panel = c * r (probe block) for all rows.
 void launch_scaled_probe(tbk_ctx* ctx, const HOp& op, void* panel, double c, uint64_t seed, int s);
 
+// Allocation-free building blocks: bytes of the mapped operator, building it into caller
+// memory, and the per-step partial-sum reduction into moments (flag bit 1 = spectrum error).
+size_t mapped_h_bytes(const tbk_bsr* H, int prec);
+HOp prepare_hop_into(tbk_ctx* ctx, const tbk_bsr* H, double emin, double emax, int prec, void* dst);
+void launch_moment_reduction(tbk_ctx* ctx, const double* partials, int nctas, int K, int order, int s,
+                             int64_t n_rows, int direct, double* sums, double* moments, int* flag);
+
 }  // namespace tbk

@@ -647,6 +647,58 @@ __global__ void finish_moments(const double* __restrict__ sums, int K, int order
   }
 }
 
+// ---- building blocks that allocate nothing (for the static-scratch entry point) --------------
+
+size_t mapped_h_bytes(const tbk_bsr* H, int prec) {
+  const int bs = H->n_orb == 9 ? (prec == TBK_MIXED ? Layout<float, 9>::BS : Layout<double, 9>::BS) : 1;
+  return (size_t)H->nnzb * bs * (prec == TBK_MIXED ? 4 : 8);
+}
+
+HOp prepare_hop_into(tbk_ctx* ctx, const tbk_bsr* H, double emin, double emax, int prec, void* dst) {
+  TBK_CHECK_ARG(H != nullptr, "H is NULL");
+  TBK_CHECK_ARG(H->n_orb == 1 || H->n_orb == 9, "n_orb must be 1 or 9");
+  TBK_CHECK_ARG(H->n_atoms >= 1 && H->nnzb >= H->n_atoms, "empty or inconsistent matrix");
+  TBK_CHECK_ARG(H->row_ptr && H->col && H->val, "NULL matrix array");
+  TBK_CHECK_ARG(H->nnzb < INT32_MAX, "nnzb must be below 2^31");
+  TBK_CHECK_ARG(std::isfinite(emin) && std::isfinite(emax) && emax > emin, "need emax > emin");
+  TBK_CHECK_ARG(prec == TBK_MIXED || prec == TBK_FP64, "unknown precision");
+  HOp op;
+  op.n_atoms = H->n_atoms;
+  op.B = H->n_orb;
+  op.prec = prec;
+  op.nnzb = H->nnzb;
+  op.n_rows = (int64_t)H->n_atoms * H->n_orb;
+  op.row_ptr = H->row_ptr;
+  op.col = H->col;
+  op.hv = dst;
+  const double shift = 0.5 * (emax + emin), inv = 2.0 / (emax - emin);
+  const dim3 blk(8, 16);
+  const int grid = ceil_div(op.n_atoms, 16);
+  if (prec == TBK_MIXED) {
+    if (op.B == 9)
+      map_h_kernel<float, 9><<<grid, blk, 0, ctx->stream>>>(op.n_atoms, op.row_ptr, op.col, H->val, shift, inv, (float*)dst);
+    else
+      map_h_kernel<float, 1><<<grid, blk, 0, ctx->stream>>>(op.n_atoms, op.row_ptr, op.col, H->val, shift, inv, (float*)dst);
+  } else {
+    if (op.B == 9)
+      map_h_kernel<double, 9><<<grid, blk, 0, ctx->stream>>>(op.n_atoms, op.row_ptr, op.col, H->val, shift, inv, (double*)dst);
+    else
+      map_h_kernel<double, 1><<<grid, blk, 0, ctx->stream>>>(op.n_atoms, op.row_ptr, op.col, H->val, shift, inv, (double*)dst);
+  }
+  post_launch(ctx, "map_h_kernel");
+  return op;
+}
+
+void launch_moment_reduction(tbk_ctx* ctx, const double* partials, int nctas, int K, int order, int s,
+                             int64_t n_rows, int direct, double* sums, double* moments, int* flag) {
+  if (K >= 1) {
+    reduce_partials<<<K, 256, 0, ctx->stream>>>(partials, nctas, sums);
+    post_launch(ctx, "reduce_partials");
+  }
+  finish_moments<<<1, 256, 0, ctx->stream>>>(sums, K, order, s, n_rows, direct, moments, flag);
+  post_launch(ctx, "finish_moments");
+}
+
 }  // namespace tbk
 
 using namespace tbk;

@@ -115,9 +115,9 @@ __device__ __forceinline__ void sddmm_quadrant(int q, const float* Y, const floa
     ri[t] = min(I0 + t, 8);
     rl[t] = min(L0 + t, 8);
   }
-  float v[32];
+  float2 v2[25];  // (even probe, odd probe) partial sums of entry i * 5 + l
 #pragma unroll
-  for (int e = 0; e < 32; ++e) v[e] = 0.f;
+  for (int e = 0; e < 25; ++e) v2[e] = make_float2(0.f, 0.f);
 #pragma unroll 1
   for (int m = 0; m < P / 128; ++m) {
     const int pb = 4 * (lane + 32 * m);
@@ -139,8 +139,13 @@ __device__ __forceinline__ void sddmm_quadrant(int q, const float* Y, const floa
 #pragma unroll
       for (int l = 0; l < 5; ++l)
 #pragma unroll
-        for (int t = 0; t < 4; ++t) v[i * 5 + l] = fmaf(yv[i][t], xv[l][t], v[i * 5 + l]);
+        for (int t = 0; t < 4; t += 2)
+          v2[i * 5 + l] = __ffma2_rn(make_float2(yv[i][t], yv[i][t + 1]),
+                                     make_float2(xv[l][t], xv[l][t + 1]), v2[i * 5 + l]);
   }
+  float v[32];
+#pragma unroll
+  for (int e = 0; e < 32; ++e) v[e] = e < 25 ? v2[e].x + v2[e].y : 0.f;
   butterfly32(v, lane);
   const int i = I0 + lane / 5, l = L0 + lane % 5;
   if (lane < 25 && i < 9 && l < 9)
@@ -236,11 +241,11 @@ clenshaw_sddmm_bulk(const int n_atoms, const int32_t* __restrict__ row_ptr,
       ok = mbar_wait(y_full, y_it & 1);
       if (!ok) break;
     }
-    float acc[9][4];
+    float2 acc[5][4];  // rows (2 ip, 2 ip + 1) x probe v
 #pragma unroll
-    for (int i = 0; i < 9; ++i)
+    for (int i = 0; i < 5; ++i)
 #pragma unroll
-      for (int v = 0; v < 4; ++v) acc[i][v] = 0.f;
+      for (int v = 0; v < 4; ++v) acc[i][v] = make_float2(0.f, 0.f);
     for (int q = 0; q < k1 - k0; ++q) {
       const bool is_own = __ldg(col + k0 + q) == a;
       const unsigned char* base;
@@ -255,28 +260,7 @@ clenshaw_sddmm_bulk(const int n_atoms, const int32_t* __restrict__ row_ptr,
       }
       if (!ok) break;
       const float* X = reinterpret_cast<const float*>(base);
-      if (has_out) {
-        const float* Hs = reinterpret_cast<const float*>(base + C::XB);
-        float x[9][4];
-#pragma unroll
-        for (int l = 0; l < 9; ++l) {
-          const float4 t = *reinterpret_cast<const float4*>(X + l * C::P + pl);
-          x[l][0] = t.x; x[l][1] = t.y; x[l][2] = t.z; x[l][3] = t.w;
-        }
-#pragma unroll
-        for (int i = 0; i < 9; ++i) {
-          float hr[12];
-#pragma unroll
-          for (int j = 0; j < 12; j += 4) {
-            const float4 t = *reinterpret_cast<const float4*>(Hs + i * 12 + j);
-            hr[j] = t.x; hr[j + 1] = t.y; hr[j + 2] = t.z; hr[j + 3] = t.w;
-          }
-#pragma unroll
-          for (int l = 0; l < 9; ++l)
-#pragma unroll
-            for (int v = 0; v < 4; ++v) acc[i][v] = fmaf(hr[l], x[l][v], acc[i][v]);
-        }
-      }
+      if (has_out) spmm_tile_f2(X, reinterpret_cast<const float*>(base + C::XB), C::P, pl, acc);
       for (int qd = warp; qd < 4; qd += CW)
         sddmm_quadrant<C::P>(qd, Ys, X, y_probe, seed, a, lane, (int64_t)(k0 + q), w, Gacc);
       __syncwarp();
@@ -310,7 +294,9 @@ clenshaw_sddmm_bulk(const int n_atoms, const int32_t* __restrict__ row_ptr,
       const int64_t row = (int64_t)9 * a + i;
       float yo[4];
 #pragma unroll
-      for (int v = 0; v < 4; ++v) yo[v] = fmaf(c_r, tbk_probe_sign(seed, row, pl + v), 2.f * acc[i][v]);
+      for (int v = 0; v < 4; ++v)
+        yo[v] = fmaf(c_r, tbk_probe_sign(seed, row, pl + v),
+                     2.f * ((i & 1) ? acc[i >> 1][v].y : acc[i >> 1][v].x));
       if (has_prev) {
 #pragma unroll
         for (int v = 0; v < 4; ++v) yo[v] -= yp[i][v];

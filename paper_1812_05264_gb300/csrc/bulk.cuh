@@ -44,4 +44,29 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
 }
 
 
+// One neighbour tile of the FP32 block product with packed f32x2 FMAs:
+//   acc[ip][v] += (H^[2ip][l], H^[2ip+1][l]) * x[l][v]   for l = 0..8,
+// X: 9 x P tile in shared memory, Hs: column-major block (columns padded to 12 floats), pl: the
+// thread's first probe.  Every accumulator sums l = 0..8 in order (same rounding as scalar FMAs).
+__device__ __forceinline__ void spmm_tile_f2(const float* X, const float* Hs, int P, int pl,
+                                             float2 (&acc)[5][4]) {
+#pragma unroll
+  for (int l = 0; l < 9; ++l) {
+    const float4 t = *reinterpret_cast<const float4*>(X + l * P + pl);
+    const float xv[4] = {t.x, t.y, t.z, t.w};
+    float hc[12];
+#pragma unroll
+    for (int j = 0; j < 12; j += 4) {
+      const float4 u = *reinterpret_cast<const float4*>(Hs + l * 12 + j);
+      hc[j] = u.x; hc[j + 1] = u.y; hc[j + 2] = u.z; hc[j + 3] = u.w;
+    }
+#pragma unroll
+    for (int ip = 0; ip < 5; ++ip) {
+      const float2 h2 = make_float2(hc[2 * ip], hc[2 * ip + 1]);
+#pragma unroll
+      for (int v = 0; v < 4; ++v) acc[ip][v] = __ffma2_rn(h2, make_float2(xv[v], xv[v]), acc[ip][v]);
+    }
+  }
+}
+
 }  // namespace tbk

@@ -6,12 +6,15 @@
 
 namespace tbk {
 
-// Row stride (elements) of one block row inside a stored block: rows are padded so that every
-// row starts on a 16-byte boundary and can be read with 128-bit loads.
+// Stored block of the mapped operator.  FP32 9x9 blocks are column-major: column l holds
+// H^[0..8][l] padded to 12 floats, so a column is three 16-byte vectors and adjacent rows (i, i+1)
+// form the float pairs of the packed f32x2 FMAs.  FP64 9x9 blocks are row-major with rows padded
+// to 10 doubles.  RS is the padded stride of the leading index, BS the elements per block.
 template <typename T, int B>
 struct Layout {
+  static constexpr bool COLMAJOR = B == 9 && sizeof(T) == 4;
   static constexpr int RS = B == 1 ? 1 : (sizeof(T) == 4 ? 12 : 10);
-  static constexpr int BS = B * RS;  // elements per stored block
+  static constexpr int BS = B * RS;
 };
 
 struct HOp {

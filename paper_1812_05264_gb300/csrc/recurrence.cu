@@ -54,10 +54,12 @@ __global__ void map_h_kernel(int n_atoms, const int32_t* __restrict__ row_ptr,
     const bool diag = col[k] == a;
     for (int i = 0; i < B; ++i)
       for (int j = 0; j < RS; ++j) {
+        // stored element (major index i, minor index j): H^[i][j] row-major, H^[j][i] column-major
+        const int r = Layout<T, B>::COLMAJOR ? j : i, c = Layout<T, B>::COLMAJOR ? i : j;
         double v = 0.0;
         if (j < B) {
-          v = H[(int64_t)k * B * B + i * B + j];
-          if (diag && i == j) v -= shift;
+          v = H[(int64_t)k * B * B + r * B + c];
+          if (diag && r == c) v -= shift;
           v *= inv_half_w;
         }
         out[(int64_t)k * BS + i * RS + j] = (T)v;
@@ -144,19 +146,33 @@ cheb_step_kernel(const int n_atoms, const int32_t* __restrict__ row_ptr,
           }
         }
         const T* h = hv + (int64_t)k * BS;
+        if constexpr (Layout<T, B>::COLMAJOR) {
+          // column l of the block against row l of the tile; each acc[i] still sums l = 0..8
 #pragma unroll
-        for (int i = 0; i < B; ++i) {
-          T hr[RS];
-          if constexpr (B == 1) {
-            hr[0] = __ldg(h);
-          } else {
+          for (int l = 0; l < B; ++l) {
+            T hc[RS];
 #pragma unroll
-            for (int j = 0; j < RS; j += VEC) ldg16(h + i * RS + j, hr + j);
+            for (int j = 0; j < RS; j += VEC) ldg16(h + l * RS + j, hc + j);
+#pragma unroll
+            for (int i = 0; i < B; ++i)
+#pragma unroll
+              for (int v = 0; v < VEC; ++v) acc[i][v] = fma(hc[i], x[l][v], acc[i][v]);
           }
+        } else {
 #pragma unroll
-          for (int l = 0; l < B; ++l)
+          for (int i = 0; i < B; ++i) {
+            T hr[RS];
+            if constexpr (B == 1) {
+              hr[0] = __ldg(h);
+            } else {
 #pragma unroll
-            for (int v = 0; v < VEC; ++v) acc[i][v] = fma(hr[l], x[l][v], acc[i][v]);
+              for (int j = 0; j < RS; j += VEC) ldg16(h + i * RS + j, hr + j);
+            }
+#pragma unroll
+            for (int l = 0; l < B; ++l)
+#pragma unroll
+              for (int v = 0; v < VEC; ++v) acc[i][v] = fma(hr[l], x[l][v], acc[i][v]);
+          }
         }
       }
 #pragma unroll
@@ -331,11 +347,11 @@ cheb_step_bulk(const int n_atoms, const int32_t* __restrict__ row_ptr, const int
     const int a = task / n_chunks, ch = task - a * n_chunks;
     const int k0 = __ldg(row_ptr + a), k1 = __ldg(row_ptr + a + 1);
     const int pl = 4 * threadIdx.x;  // probe offset inside the chunk
-    float acc[9][4];
+    float2 acc[5][4];  // acc[ip][v] = rows (2 ip, 2 ip + 1) for probe v; row 9 is padding
 #pragma unroll
-    for (int i = 0; i < 9; ++i)
+    for (int i = 0; i < 5; ++i)
 #pragma unroll
-      for (int v = 0; v < 4; ++v) acc[i][v] = 0.f;
+      for (int v = 0; v < 4; ++v) acc[i][v] = make_float2(0.f, 0.f);
     for (int q = 0; q < k1 - k0; ++q) {
       const bool is_own = __ldg(col + k0 + q) == a;
       const unsigned char* base;
@@ -351,25 +367,7 @@ cheb_step_bulk(const int n_atoms, const int32_t* __restrict__ row_ptr, const int
       if (!ok) break;
       const float* X = reinterpret_cast<const float*>(base);
       const float* Hs = reinterpret_cast<const float*>(base + C::XB);
-      float x[9][4];
-#pragma unroll
-      for (int l = 0; l < 9; ++l) {
-        const float4 t = *reinterpret_cast<const float4*>(X + l * C::P + pl);
-        x[l][0] = t.x; x[l][1] = t.y; x[l][2] = t.z; x[l][3] = t.w;
-      }
-#pragma unroll
-      for (int i = 0; i < 9; ++i) {
-        float hr[12];
-#pragma unroll
-        for (int j = 0; j < 12; j += 4) {
-          const float4 t = *reinterpret_cast<const float4*>(Hs + i * 12 + j);
-          hr[j] = t.x; hr[j + 1] = t.y; hr[j + 2] = t.z; hr[j + 3] = t.w;
-        }
-#pragma unroll
-        for (int l = 0; l < 9; ++l)
-#pragma unroll
-          for (int v = 0; v < 4; ++v) acc[i][v] = fmaf(hr[l], x[l][v], acc[i][v]);
-      }
+      spmm_tile_f2(X, Hs, C::P, pl, acc);
       if (!is_own) {
         __syncwarp();
         if (lane == 0) mbar_arrive(empty(st));
@@ -401,7 +399,7 @@ cheb_step_bulk(const int n_atoms, const int32_t* __restrict__ row_ptr, const int
       const int64_t row = (int64_t)9 * a + i;
       float yo[4], r[4];
 #pragma unroll
-      for (int v = 0; v < 4; ++v) yo[v] = alpha * acc[i][v];
+      for (int v = 0; v < 4; ++v) yo[v] = alpha * ((i & 1) ? acc[i >> 1][v].y : acc[i >> 1][v].x);
       if (c_r != 0.f || direct) {
 #pragma unroll
         for (int v = 0; v < 4; ++v) r[v] = tbk_probe_sign(seed, row, p0 + v);

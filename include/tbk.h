@@ -49,6 +49,7 @@ typedef enum {
 #define TBK_FP64 1             /* FP64 panels and FP64 mapped H throughout */
 #define TBK_MOMENTS_DIRECT 2   /* mu_k = <r, y_k> for every k instead of the doubling identity */
 #define TBK_PLAIN_KERNEL 4     /* use the plain load/FMA step kernel instead of the TMA-fed one */
+#define TBK_NO_GRAPH 8         /* batched calls: enqueue the kernels directly, no CUDA graph */
 
 /* Damping of the Chebyshev series. */
 #define TBK_DAMP_NONE 0
@@ -192,6 +193,30 @@ int tbk_density_and_forces(tbk_ctx* ctx, const tbk_bsr* H, const tbk_model* mode
                            uint64_t probe_seed, int32_t n_probes, int32_t order, double mu,
                            double kT, int32_t damping, int32_t flags, int64_t max_panel_bytes,
                            double* G, double* forces);
+
+/* ---- a11: batches of clusters ------------------------------------------------------------
+
+   tbk_batched_moments: the moments of n_clusters independent clusters (each with its own H,
+   spectral interval, probe seed and order) in one launch per recurrence step.  The clusters'
+   mapped operators are merged block-diagonally, sorted by step count so that the clusters still
+   running form a prefix of the rows; each cluster keeps its own probe stream, so its moments
+   equal those of tbk_chebyshev_moments on it alone (mixed precision).  H: host array of
+   n_clusters descriptors (9x9 blocks).  emin, emax, seeds, orders: host arrays.  moments:
+   device, sum(orders) doubles, cluster c at offset sum_{c' < c} orders[c'].  n_probes: a
+   multiple of 128.  flags: 0 or TBK_MOMENTS_DIRECT, optionally | TBK_NO_GRAPH.  The step
+   sequence is captured into a CUDA graph on the first call and replayed while the arguments
+   stay the same.  Synchronises the stream. */
+int tbk_batched_moments(tbk_ctx* ctx, int32_t n_clusters, const tbk_bsr* H, const double* emin,
+                        const double* emax, const uint64_t* seeds, int32_t n_probes,
+                        const int32_t* orders, int32_t flags, double* moments);
+
+/* tbk_batched_fermi_level: tbk_fermi_level for every cluster of a batch (moments laid out as
+   tbk_batched_moments writes them); host arrays orders, emin, emax, n_electrons, kT; out: host,
+   4 doubles {mu, Omega, E, N} per cluster.  Synchronises the stream once. */
+int tbk_batched_fermi_level(tbk_ctx* ctx, int32_t n_clusters, const double* moments,
+                            const int32_t* orders, const double* emin, const double* emax,
+                            const double* n_electrons, const double* kT, int32_t damping,
+                            double* out);
 
 /* ---- allocation-free variant of tbk_chebyshev_moments ------------------------------------
 

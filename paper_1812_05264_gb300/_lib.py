@@ -22,6 +22,7 @@ TBK_MIXED = 0
 TBK_FP64 = 1
 TBK_MOMENTS_DIRECT = 2
 TBK_PLAIN_KERNEL = 4
+TBK_NO_GRAPH = 8
 TBK_DAMP_NONE = 0
 TBK_DAMP_JACKSON = 1
 TBK_FN_FERMI = 0
@@ -69,6 +70,10 @@ SIGNATURES = {
     "tbk_chebyshev_coefficients": [_P, _I, _I, _D, _D, _D, _D, _I, _P],
     "tbk_chebyshev_moments": [_P, C.POINTER(tbk_bsr), _D, _D, _U, _I, _I, _I, _P],
     "tbk_chebyshev_moments_noalloc": [_P, C.POINTER(tbk_bsr), _D, _D, _U, _I, _I, _I, _P],
+    "tbk_batched_moments": [_P, _I, C.POINTER(tbk_bsr), C.POINTER(_D), C.POINTER(_D), C.POINTER(_U),
+                            _I, C.POINTER(_I), _I, _P],
+    "tbk_batched_fermi_level": [_P, _I, _P, C.POINTER(_I), C.POINTER(_D), C.POINTER(_D),
+                                C.POINTER(_D), C.POINTER(_D), _I, C.POINTER(_D)],
     "tbk_fermi_level": [_P, _P, _I, _D, _D, _D, _D, _D, _I, C.POINTER(_D)],
     "tbk_density_and_forces": [_P, C.POINTER(tbk_bsr), C.POINTER(tbk_model), _P, _P, _D, _D, _U,
                                _I, _I, _D, _D, _I, _I, _L, _P, _P],

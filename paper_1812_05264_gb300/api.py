@@ -205,6 +205,35 @@ def density_and_forces(ctx: Context, H: BSR, model: Model | None, pos: torch.Ten
     return G, F
 
 
+def batched_moments(ctx: Context, Hs: list, emins, emaxs, seeds, n_probes: int, orders,
+                    direct: bool = False, graph: bool = True) -> list:
+    """a11: moments of many clusters in one launch per recurrence step (list of tensors)."""
+    n = len(Hs)
+    structs = (L.tbk_bsr * n)(*[h.struct() for h in Hs])
+    e0 = (C.c_double * n)(*map(float, emins))
+    e1 = (C.c_double * n)(*map(float, emaxs))
+    sd = (C.c_uint64 * n)(*map(int, seeds))
+    od = (C.c_int32 * n)(*map(int, orders))
+    out = torch.empty(int(sum(orders)), dtype=torch.float64, device=Hs[0].val.device)
+    flags = (L.TBK_MOMENTS_DIRECT if direct else 0) | (0 if graph else L.TBK_NO_GRAPH)
+    L.call("tbk_batched_moments", ctx.handle, n, structs, e0, e1, sd, int(n_probes), od, flags,
+           _ptr(out))
+    return list(torch.split(out, [int(p) for p in orders]))
+
+
+def batched_fermi_level(ctx: Context, moments: list, emins, emaxs, n_electrons, kTs,
+                        jackson: bool = False) -> np.ndarray:
+    """a8 for every cluster of a batch: rows (mu, Omega, E, N)."""
+    n = len(moments)
+    cat = torch.cat(moments).contiguous()
+    od = (C.c_int32 * n)(*[m.numel() for m in moments])
+    arr = lambda v: (C.c_double * n)(*map(float, v))
+    out = (C.c_double * (4 * n))()
+    L.call("tbk_batched_fermi_level", ctx.handle, n, _ptr(cat), od, arr(emins), arr(emaxs),
+           arr(n_electrons), arr(kTs), L.TBK_DAMP_JACKSON if jackson else L.TBK_DAMP_NONE, out)
+    return np.array(out[:], dtype=np.float64).reshape(n, 4)
+
+
 def order_for(W: float, kT: float, eps: float = 1e-7, p_min: int = 64) -> int:
     """Chebyshev terms from the paper's error model eps_poly ~ exp(-6.4 p kT / W) (Sec. II.B.1)."""
     return max(p_min, int(math.ceil((W / kT) * math.log(1.0 / eps) / 6.4)))

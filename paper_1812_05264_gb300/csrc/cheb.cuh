@@ -35,6 +35,14 @@ HOp prepare_hop(tbk_ctx* ctx, const tbk_bsr* H, double emin, double emax, int pr
 // update: each element is read and then written by the same thread).
 // With `partials` not NULL the CTA writes two FP64 partial sums at partials + 2 * cta:
 //   [0] = sum y_out . y_in   (or sum y_out . r when `direct`),   [1] = sum y_out . y_out.
+// Batched operators (many clusters merged block-diagonally): per-atom cluster index, per-cluster
+// probe seed and first atom, so that each cluster's probes are those of a standalone run.
+struct BatchRows {
+  const int32_t* atom_cl = nullptr;
+  const uint64_t* seed = nullptr;
+  const int32_t* atom0 = nullptr;
+};
+
 struct StepArgs {
   const void* yin = nullptr;
   void* yprev = nullptr;
@@ -48,7 +56,13 @@ struct StepArgs {
   double* partials = nullptr;
   int* err = nullptr;       // device flag raised (= 2) when a bounded wait expires
   int force_simple = 0;     // use the plain load/FMA kernel even where the TMA-fed one applies
+  // TMA-fed kernel only: per-cluster probes, and partial sums per (atom, consumer warp) at
+  // partials + 2 (a * CW + warp) instead of per CTA (CW = consumer warps, bulk_consumer_warps).
+  BatchRows batch;
+  int per_task = 0;
 };
+// Consumer warps of the TMA-fed step kernel for this operator and probe count (0 = not used).
+int bulk_consumer_warps(const HOp& op, int s);
 // CTAs a step launches for this operator and probe count.
 int step_grid_ctas(tbk_ctx* ctx, const HOp& op, int s);
 void launch_step(tbk_ctx* ctx, const HOp& op, const StepArgs& a);

@@ -159,6 +159,23 @@ void coefficients(tbk_ctx* ctx, int fn, int p, double emin, double emax, double 
   post_launch(ctx, "coeff_kernel");
 }
 
+// Enqueue the chemical-potential solve for one moment vector without synchronising: tab (4M
+// doubles), rho (M doubles) and res (5 doubles: mu, Omega, E, N, status) are device buffers.
+void fermi_enqueue(tbk_ctx* ctx, const double* moments, int order, double emin, double emax,
+                   double n_electrons, double mu_fixed, double kT, int damping, double* tab,
+                   double* rho, double* res) {
+  TBK_CHECK_ARG(order >= 1 && order <= (1 << 22), "order out of range");
+  TBK_CHECK_ARG(kT > 0.0 && std::isfinite(kT), "kT must be positive");
+  TBK_CHECK_ARG(emax > emin, "need emax > emin");
+  const int M = quad_nodes(order);
+  cos_table<<<ceil_div(4 * (int64_t)M, 256), 256, 0, ctx->stream>>>(M, tab);
+  post_launch(ctx, "cos_table");
+  rho_kernel<<<ceil_div(M, 128), 128, 0, ctx->stream>>>(moments, order, M, damping, tab, rho);
+  post_launch(ctx, "rho_kernel");
+  fermi_kernel<<<1, 1024, 0, ctx->stream>>>(rho, M, emin, emax, n_electrons, mu_fixed, kT, res);
+  post_launch(ctx, "fermi_kernel");
+}
+
 }  // namespace tbk
 
 using namespace tbk;

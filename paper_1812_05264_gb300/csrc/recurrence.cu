@@ -268,7 +268,8 @@ __global__ void __launch_bounds__(32 * (CW + 1))
 cheb_step_bulk(const int n_atoms, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
                const float* __restrict__ hv, const float* __restrict__ yin, const float* yprev,
                float* yout, const float alpha, const float c_r, const uint64_t seed, const int s,
-               const int direct, double* __restrict__ partials, int* __restrict__ err) {
+               const int direct, double* __restrict__ partials, int* __restrict__ err,
+               const BatchRows batch, const int per_task) {
   using C = BulkCfg<CW, D>;
   extern __shared__ __align__(128) unsigned char smem[];
   unsigned char* own = smem + D * C::SB;
@@ -394,6 +395,13 @@ cheb_step_bulk(const int n_atoms, const int32_t* __restrict__ row_ptr, const int
     // epilogue: y_out = alpha acc + c_r r - y_prev, moment partial sums
     const float* Y = reinterpret_cast<const float*>(own);
     const int p0 = ch * C::P + pl;
+    uint64_t sd = seed;          // probe stream and row index within the cluster
+    int64_t rloc = (int64_t)9 * a;
+    if (batch.atom_cl) {
+      const int cl = __ldg(batch.atom_cl + a);
+      sd = __ldg(batch.seed + cl);
+      rloc = (int64_t)9 * (a - __ldg(batch.atom0 + cl));
+    }
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
       const int64_t row = (int64_t)9 * a + i;
@@ -402,7 +410,7 @@ cheb_step_bulk(const int n_atoms, const int32_t* __restrict__ row_ptr, const int
       for (int v = 0; v < 4; ++v) yo[v] = alpha * ((i & 1) ? acc[i >> 1][v].y : acc[i >> 1][v].x);
       if (c_r != 0.f || direct) {
 #pragma unroll
-        for (int v = 0; v < 4; ++v) r[v] = tbk_probe_sign(seed, row, p0 + v);
+        for (int v = 0; v < 4; ++v) r[v] = tbk_probe_sign(sd, rloc + i, p0 + v);
       }
       if (c_r != 0.f) {
 #pragma unroll
@@ -435,9 +443,21 @@ cheb_step_bulk(const int n_atoms, const int32_t* __restrict__ row_ptr, const int
     __syncwarp();
     if (lane == 0) mbar_arrive(own_empty);
     ++own_it;
+    if (per_task && partials) {
+      // per (atom, warp) partial sums: no barrier between warps is needed
+      for (int o = 16; o > 0; o >>= 1) {
+        sum0 += __shfl_xor_sync(0xffffffffu, sum0, o);
+        sum1 += __shfl_xor_sync(0xffffffffu, sum1, o);
+      }
+      if (lane == 0) {
+        partials[2 * ((int64_t)a * CW + warp)] = sum0;
+        partials[2 * ((int64_t)a * CW + warp) + 1] = sum1;
+      }
+      sum0 = sum1 = 0.0;
+    }
   }
   if (!ok) atomicOr(err, 2);
-  if (partials) {
+  if (partials && !per_task) {
     __shared__ double red[2][8];
     for (int o = 16; o > 0; o >>= 1) {
       sum0 += __shfl_xor_sync(0xffffffffu, sum0, o);
@@ -481,6 +501,7 @@ static int occupancy_bulk() {
 
 constexpr int BULK_D = 3;
 
+int bulk_consumer_warps(const HOp& op, int s);
 // Consumer warps of the TMA-fed kernel for this operator and probe count (0 = not eligible).
 static int bulk_warps(const HOp& op, int s) {
   if (op.prec != TBK_MIXED || op.B != 9 || s % 128 != 0) return 0;
@@ -488,6 +509,8 @@ static int bulk_warps(const HOp& op, int s) {
   if (s % 256 == 0) return 2;
   return 1;
 }
+
+int bulk_consumer_warps(const HOp& op, int s) { return bulk_warps(op, s); }
 
 struct Occ {
   int simple = 0, bulk[5] = {0, 0, 0, 0, 0};
@@ -546,7 +569,8 @@ static void launch_bulk(tbk_ctx* ctx, const HOp& op, const StepArgs& a, int G) {
   using C = BulkCfg<CW, BULK_D>;
   cheb_step_bulk<CW, BULK_D><<<G, C::THREADS, C::SMEM, ctx->stream>>>(
       op.n_atoms, op.row_ptr, op.col, (const float*)op.hv, (const float*)a.yin, (const float*)a.yprev,
-      (float*)a.yout, (float)a.alpha, (float)a.c_r, a.seed, a.s, a.direct, a.partials, a.err);
+      (float*)a.yout, (float)a.alpha, (float)a.c_r, a.seed, a.s, a.direct, a.partials, a.err,
+      a.batch, a.per_task);
   post_launch(ctx, "cheb_step_bulk");
 }
 

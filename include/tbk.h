@@ -218,6 +218,21 @@ int tbk_batched_fermi_level(tbk_ctx* ctx, int32_t n_clusters, const double* mome
                             const double* n_electrons, const double* kT, int32_t damping,
                             double* out);
 
+/* tbk_batched_density_and_forces: tbk_density_and_forces for every cluster of a batch, with
+   the backward sweep of all clusters in one launch per step (merged operator as in
+   tbk_batched_moments; each cluster joins the sweep at its own order).  Host arrays: H, pos
+   (device pointers, n_atoms x 3 each; open clusters), emin, emax, seeds, orders, mu, kT, G and
+   forces (device pointers or NULL entries; either array may be NULL).  n_probes 128, 256 or 512
+   for the one-launch path; other shapes run the clusters one after another.  flags: 0 (mixed).
+   Synchronises the stream. */
+int tbk_batched_density_and_forces(tbk_ctx* ctx, int32_t n_clusters, const tbk_bsr* H,
+                                   const tbk_model* model, const double* const* pos,
+                                   const double* emin, const double* emax, const uint64_t* seeds,
+                                   int32_t n_probes, const int32_t* orders, const double* mu,
+                                   const double* kT, int32_t damping, int32_t flags,
+                                   int64_t max_panel_bytes, double* const* G,
+                                   double* const* forces);
+
 /* ---- allocation-free variant of tbk_chebyshev_moments ------------------------------------
 
    No counterpart in the paper: this entry point exists for callers that cannot allocate device

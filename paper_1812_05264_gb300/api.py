@@ -234,6 +234,26 @@ def batched_fermi_level(ctx: Context, moments: list, emins, emaxs, n_electrons, 
     return np.array(out[:], dtype=np.float64).reshape(n, 4)
 
 
+def batched_density_and_forces(ctx: Context, Hs: list, model: Model, positions: list, emins,
+                               emaxs, seeds, n_probes: int, orders, mus, kTs,
+                               jackson: bool = False, want_G: bool = False,
+                               max_panel_bytes: int = 0):
+    """a9-a11: (G list or None, forces list) of a batch, backward sweeps in one launch per step."""
+    n = len(Hs)
+    structs = (L.tbk_bsr * n)(*[h.struct() for h in Hs])
+    arr = lambda v: (C.c_double * n)(*map(float, v))
+    Fs = [torch.empty((h.graph.n_atoms, 3), dtype=torch.float64, device=h.val.device) for h in Hs]
+    Gs = [torch.empty_like(h.val) for h in Hs] if want_G else None
+    pp = (C.c_void_p * n)(*[p.data_ptr() for p in positions])
+    fp = (C.c_void_p * n)(*[f.data_ptr() for f in Fs])
+    gp = (C.c_void_p * n)(*[g.data_ptr() for g in Gs]) if want_G else None
+    L.call("tbk_batched_density_and_forces", ctx.handle, n, structs, C.byref(model.s), pp,
+           arr(emins), arr(emaxs), (C.c_uint64 * n)(*map(int, seeds)), int(n_probes),
+           (C.c_int32 * n)(*map(int, orders)), arr(mus), arr(kTs),
+           L.TBK_DAMP_JACKSON if jackson else L.TBK_DAMP_NONE, 0, int(max_panel_bytes), gp, fp)
+    return Gs, Fs
+
+
 def order_for(W: float, kT: float, eps: float = 1e-7, p_min: int = 64) -> int:
     """Chebyshev terms from the paper's error model eps_poly ~ exp(-6.4 p kT / W) (Sec. II.B.1)."""
     return max(p_min, int(math.ceil((W / kT) * math.log(1.0 / eps) / 6.4)))

@@ -106,8 +106,8 @@ __device__ __forceinline__ void butterfly32(float (&v)[32], int lane) {
 // columns past 8 are clamped to 8 and their results dropped).
 template <int P>
 __device__ __forceinline__ void sddmm_quadrant(int q, const float* Y, const float* X, bool y_probe,
-                                               uint64_t seed, int a, int lane, int64_t k, double w,
-                                               double* __restrict__ Gacc) {
+                                               uint64_t seed, int64_t rloc, int lane, int64_t k,
+                                               double w, double* __restrict__ Gacc) {
   const int I0 = (q >> 1) * 5, L0 = (q & 1) * 5;
   int ri[5], rl[5];
 #pragma unroll
@@ -126,7 +126,7 @@ __device__ __forceinline__ void sddmm_quadrant(int q, const float* Y, const floa
     for (int i = 0; i < 5; ++i) {
       if (y_probe) {
 #pragma unroll
-        for (int t = 0; t < 4; ++t) yv[i][t] = tbk_probe_sign(seed, (int64_t)9 * a + ri[i], pb + t);
+        for (int t = 0; t < 4; ++t) yv[i][t] = tbk_probe_sign(seed, rloc + ri[i], pb + t);
       } else {
         const float4 u = *reinterpret_cast<const float4*>(Y + ri[i] * P + pb);
         yv[i][0] = u.x; yv[i][1] = u.y; yv[i][2] = u.z; yv[i][3] = u.w;
@@ -159,7 +159,8 @@ clenshaw_sddmm_bulk(const int n_atoms, const int32_t* __restrict__ row_ptr,
                     const int32_t* __restrict__ col, const float* __restrict__ hv,
                     const float* __restrict__ bin, const float* bprev, float* bout,
                     const float* __restrict__ ypan, const float c_r, const uint64_t seed,
-                    const int s, const double w, double* __restrict__ Gacc, int* __restrict__ err) {
+                    const int s, const double w, double* __restrict__ Gacc, int* __restrict__ err,
+                    const BatchRows batch, const float* __restrict__ c_cl) {
   using C = SdCfg<CW>;
   constexpr int D = C::D;
   extern __shared__ __align__(128) unsigned char smem[];
@@ -237,6 +238,16 @@ clenshaw_sddmm_bulk(const int n_atoms, const int32_t* __restrict__ row_ptr,
   const int pl = 4 * threadIdx.x;
   for (int a = blockIdx.x; a < n_atoms && ok; a += gridDim.x) {
     const int k0 = __ldg(row_ptr + a), k1 = __ldg(row_ptr + a + 1);
+    // probe stream and cluster-local row of this atom; per-cluster coefficient in batches
+    uint64_t sd = seed;
+    int64_t rloc = (int64_t)9 * a;
+    float cr = c_r;
+    if (batch.atom_cl) {
+      const int cl = __ldg(batch.atom_cl + a);
+      sd = __ldg(batch.seed + cl);
+      rloc = (int64_t)9 * (a - __ldg(batch.atom0 + cl));
+      if (c_cl) cr = __ldg(c_cl + cl);
+    }
     if (!y_probe) {
       ok = mbar_wait(y_full, y_it & 1);
       if (!ok) break;
@@ -262,7 +273,7 @@ clenshaw_sddmm_bulk(const int n_atoms, const int32_t* __restrict__ row_ptr,
       const float* X = reinterpret_cast<const float*>(base);
       if (has_out) spmm_tile_f2(X, reinterpret_cast<const float*>(base + C::XB), C::P, pl, acc);
       for (int qd = warp; qd < 4; qd += CW)
-        sddmm_quadrant<C::P>(qd, Ys, X, y_probe, seed, a, lane, (int64_t)(k0 + q), w, Gacc);
+        sddmm_quadrant<C::P>(qd, Ys, X, y_probe, sd, rloc, lane, (int64_t)(k0 + q), w, Gacc);
       __syncwarp();
       if (lane == 0) mbar_arrive(is_own ? own_empty : empty(st));
       if (is_own) ++own_it; else ++it;
@@ -295,7 +306,7 @@ clenshaw_sddmm_bulk(const int n_atoms, const int32_t* __restrict__ row_ptr,
       float yo[4];
 #pragma unroll
       for (int v = 0; v < 4; ++v)
-        yo[v] = fmaf(c_r, tbk_probe_sign(seed, row, pl + v),
+        yo[v] = fmaf(cr, tbk_probe_sign(sd, rloc + i, pl + v),
                      2.f * ((i & 1) ? acc[i >> 1][v].y : acc[i >> 1][v].x));
       if (has_prev) {
 #pragma unroll
@@ -390,14 +401,14 @@ __global__ void gather_forces(int n_atoms, const int32_t* __restrict__ row_ptr,
   F[3 * c + 2] = f2;
 }
 
-static bool fused_eligible(const HOp& op, int s, int plain) {
+bool fused_eligible(const HOp& op, int s, int plain) {
   return !plain && op.prec == TBK_MIXED && op.B == 9 && (s == 128 || s == 256 || s == 512);
 }
 
 template <int CW>
 static void launch_fused_cw(tbk_ctx* ctx, const HOp& op, const void* bin, const void* bprev, void* bout,
                             const void* ypan, double c_r, uint64_t seed, int s, double w, double* Gacc,
-                            int* err) {
+                            int* err, const BatchRows& batch, const float* c_cl) {
   using C = SdCfg<CW>;
   TBK_CUDA(cudaFuncSetAttribute(clenshaw_sddmm_bulk<CW>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
   int occ = 0;
@@ -406,16 +417,16 @@ static void launch_fused_cw(tbk_ctx* ctx, const HOp& op, const void* bin, const 
   const int G = std::max(1, std::min(op.n_atoms, occ * ctx->num_sms));
   clenshaw_sddmm_bulk<CW><<<G, C::THREADS, C::SMEM, ctx->stream>>>(
       op.n_atoms, op.row_ptr, op.col, (const float*)op.hv, (const float*)bin, (const float*)bprev,
-      (float*)bout, (const float*)ypan, (float)c_r, seed, s, w, Gacc, err);
+      (float*)bout, (const float*)ypan, (float)c_r, seed, s, w, Gacc, err, batch, c_cl);
   post_launch(ctx, "clenshaw_sddmm_bulk");
 }
 
-static void launch_fused(tbk_ctx* ctx, const HOp& op, const void* bin, const void* bprev, void* bout,
-                         const void* ypan, double c_r, uint64_t seed, int s, double w, double* Gacc,
-                         int* err) {
-  if (s == 512) launch_fused_cw<4>(ctx, op, bin, bprev, bout, ypan, c_r, seed, s, w, Gacc, err);
-  else if (s == 256) launch_fused_cw<2>(ctx, op, bin, bprev, bout, ypan, c_r, seed, s, w, Gacc, err);
-  else launch_fused_cw<1>(ctx, op, bin, bprev, bout, ypan, c_r, seed, s, w, Gacc, err);
+void launch_fused(tbk_ctx* ctx, const HOp& op, const void* bin, const void* bprev, void* bout,
+                  const void* ypan, double c_r, uint64_t seed, int s, double w, double* Gacc,
+                  int* err, const BatchRows& batch, const float* c_cl) {
+  if (s == 512) launch_fused_cw<4>(ctx, op, bin, bprev, bout, ypan, c_r, seed, s, w, Gacc, err, batch, c_cl);
+  else if (s == 256) launch_fused_cw<2>(ctx, op, bin, bprev, bout, ypan, c_r, seed, s, w, Gacc, err, batch, c_cl);
+  else launch_fused_cw<1>(ctx, op, bin, bprev, bout, ypan, c_r, seed, s, w, Gacc, err, batch, c_cl);
 }
 
 static void launch_sddmm(tbk_ctx* ctx, const HOp& op, const void* y, int y_is_probe, uint64_t seed,
@@ -433,6 +444,46 @@ static void launch_sddmm(tbk_ctx* ctx, const HOp& op, const void* y, int y_is_pr
   }
 #undef TBK_SD
   post_launch(ctx, "sddmm_kernel");
+}
+
+// ---- pieces shared with the batched driver -------------------------------------------------
+
+void launch_transpose_map(tbk_ctx* ctx, int n_atoms, const int32_t* row_ptr, const int32_t* col,
+                          int32_t* tr, int* err) {
+  transpose_map<<<ceil_div(n_atoms, 16), dim3(8, 16), 0, ctx->stream>>>(n_atoms, row_ptr, col, tr, err);
+  post_launch(ctx, "transpose_map");
+}
+
+// G[k] = scale(cluster of row a) (Gacc[k] + Gacc[tr[k]]^T) / 2 for a merged batch.
+__global__ void symmetrize_batched(int n_atoms, const int32_t* __restrict__ row_ptr,
+                                   const int32_t* __restrict__ tr, const int32_t* __restrict__ atom_cl,
+                                   const double* __restrict__ scale_cl, const double* __restrict__ Gacc,
+                                   double* __restrict__ G) {
+  const int a = blockIdx.x * blockDim.y + threadIdx.y;
+  if (a >= n_atoms) return;
+  const double sc = scale_cl[atom_cl[a]];
+  for (int k = row_ptr[a]; k < row_ptr[a + 1]; ++k)
+    for (int e = threadIdx.x; e < 81; e += blockDim.x) {
+      const int i = e / 9, l = e - 9 * i;
+      const int64_t kt = tr[k];
+      G[(int64_t)k * 81 + e] = kt < 0 ? 0.0 : 0.5 * sc * (Gacc[(int64_t)k * 81 + e] + Gacc[kt * 81 + l * 9 + i]);
+    }
+}
+
+void launch_symmetrize_batched(tbk_ctx* ctx, int n_atoms, const int32_t* row_ptr, const int32_t* tr,
+                               const int32_t* atom_cl, const double* scale_cl, const double* Gacc,
+                               double* G) {
+  symmetrize_batched<<<ceil_div(n_atoms, 8), dim3(32, 8), 0, ctx->stream>>>(n_atoms, row_ptr, tr, atom_cl,
+                                                                             scale_cl, Gacc, G);
+  post_launch(ctx, "symmetrize_batched");
+}
+
+void launch_forces(tbk_ctx* ctx, const DevModel& M, const double* pos, int n_atoms, const int32_t* row_ptr,
+                   const int32_t* col, const int32_t* tr, const double* G, double* tq, double* F) {
+  bond_terms<<<ceil_div(n_atoms, 8), dim3(4, 8), 0, ctx->stream>>>(M, pos, n_atoms, row_ptr, col, G, tq);
+  post_launch(ctx, "bond_terms");
+  gather_forces<<<ceil_div(n_atoms, 128), 128, 0, ctx->stream>>>(n_atoms, row_ptr, col, tr, tq, F);
+  post_launch(ctx, "gather_forces");
 }
 
 }  // namespace tbk
@@ -572,7 +623,8 @@ extern "C" int tbk_density_and_forces(tbk_ctx* ctx, const tbk_bsr* H, const tbk_
         if (fused) {
           // one launch: b_j (when j >= 1) and the y_j b_{j+1}^T term
           launch_fused(ctx, op, bcur, have_bprev ? bprev : nullptr, j >= 1 ? bprev : nullptr, yj,
-                       j >= 1 ? c[j] : 0.0, probe_seed, s, j == 0 ? 1.0 : 2.0, Gacc, err);
+                       j >= 1 ? c[j] : 0.0, probe_seed, s, j == 0 ? 1.0 : 2.0, Gacc, err, BatchRows(),
+                       nullptr);
           if (j >= 1) {
             std::swap(bcur, bprev);
             have_bprev = true;

@@ -72,3 +72,46 @@ def test_batched_energies_vs_oracle(api, ctx):
         assert abs(o[1] - est["Omega"]) / n < 1e-4
         assert abs(o[2] - est["E"]) / n < 1e-4
         assert abs(o[3] - est["N"]) / n < 1e-4
+
+
+def test_batched_forces_equal_single_cluster_forces(api, ctx):
+    sizes, kTs = [37, 70, 13, 52], [0.5, 0.1, 0.5, 0.5]
+    b = _batch(api, ctx, sizes, kTs)
+    b = [(wk, H, e0, e1, min(p, 90 + 17 * i)) for i, (wk, H, e0, e1, p) in enumerate(b)]
+    model = api.Solver(b[0][0], ctx).model
+    mus = []
+    for wk, H, e0, e1, p in b:
+        m = api.chebyshev_moments(ctx, H, e0, e1, wk.probe_seed, 128, p)
+        mus.append(api.fermi_level(ctx, m, e0, e1, wk.n_electrons, wk.kT)[0])
+    pos = [torch.as_tensor(x[0].positions, dtype=torch.float64, device="cuda") for x in b]
+    Gs, Fs = api.batched_density_and_forces(
+        ctx, [x[1] for x in b], model, pos, [x[2] for x in b], [x[3] for x in b],
+        [x[0].probe_seed for x in b], 128, [x[4] for x in b], mus, kTs, want_G=True)
+    for (wk, H, e0, e1, p), mu, G, F, ps in zip(b, mus, Gs, Fs, pos):
+        G1, F1 = api.density_and_forces(ctx, H, model, ps, None, e0, e1, wk.probe_seed, 128, p, mu,
+                                        wk.kT, False, False, want_G=True)
+        gmax = G1.abs().max().item()
+        assert torch.allclose(G, G1, rtol=0, atol=2e-5 * gmax)
+        assert torch.allclose(F, F1, rtol=0, atol=1e-4)
+        assert F.sum(0).abs().max().item() < 1e-9
+
+
+def test_batched_forces_vs_oracle(api, ctx):
+    from gpu_common import oracle_estimator_forces
+    sizes, kTs = [19, 28], [0.5, 0.5]
+    b = _batch(api, ctx, sizes, kTs)
+    b = [(wk, H, e0, e1, 80) for (wk, H, e0, e1, p) in b]
+    model = api.Solver(b[0][0], ctx).model
+    ests, mus = [], []
+    for wk, H, e0, e1, p in b:
+        rp, col, Hd = oracle_H(wk)
+        est = oracle_estimator(wk, Hd, e0, e1, p)
+        ests.append((rp, col, est))
+        mus.append(est["mu"])
+    pos = [torch.as_tensor(x[0].positions, dtype=torch.float64, device="cuda") for x in b]
+    _, Fs = api.batched_density_and_forces(ctx, [x[1] for x in b], model, pos, [x[2] for x in b],
+                                           [x[3] for x in b], [x[0].probe_seed for x in b], 128,
+                                           [x[4] for x in b], mus, kTs)
+    for (wk, H, e0, e1, p), (rp, col, est), F in zip(b, ests, Fs):
+        _, Fo = oracle_estimator_forces(wk, rp, col, est, e0, e1, p)
+        assert np.abs(F.cpu().numpy() - Fo).max() < 1e-3

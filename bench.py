@@ -50,6 +50,9 @@ def make_workload(name: str, rank: int = 0):
         return wl.sc_disorder(L=10, probe_seed=18120 + rank)
     if name == "sc9-48":
         return wl.sc9_periodic(L=48, probe_seed=48480 + rank)
+    if name == "batched64":
+        # a representative member of the batch (mean size, middle temperature): the oracle sample
+        return wl.fcc_cu(1253, kT=0.1, n_probes=128, seed=5264, probe_seed=64000 + rank)
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -66,12 +69,15 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, device: int):
+    def __init__(self, device: int, enabled: bool = True):
         self.device = device
+        self.enabled = enabled
         self.proc = None
         self.lines: list[str] = []
 
     def start(self):
+        if not self.enabled:
+            return
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
@@ -88,7 +94,8 @@ class ClockSampler:
 
     def stop(self) -> dict:
         if self.proc is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+            why = "not sampled (--no-clocks)" if not self.enabled else "nvidia-smi unavailable"
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [why]}
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
@@ -258,11 +265,13 @@ def run_ours(args, rank, world):
 
     if args.only_moments:
         return moments_only(args, ctx, solver, wk, pos)
+    if args.only_adjoint:
+        return adjoint_only(args, ctx, solver, wk, pos)
     for _ in range(max(args.warmup, 0)):
         p, _, _ = step(pos)
     torch.cuda.synchronize()
     barrier()
-    clocks = ClockSampler(local)
+    clocks = ClockSampler(local, enabled=not args.no_clocks)
     clocks.start()
     launches0 = ctx.launches
     t0 = torch.cuda.Event(enable_timing=True)
@@ -371,6 +380,141 @@ def moments_only(args, ctx, solver, wk, pos):
     return 0
 
 
+def adjoint_only(args, ctx, solver, wk, pos):
+    """Profiling aid: just the adjoint (density matrix and forces) with a fixed small order."""
+    import torch
+    from paper_1812_05264_gb300 import api
+    g = api.build_neighbors(ctx, pos, wk.cutoff, solver.box)
+    H = api.assemble_H(ctx, solver.model, pos, g, solver.box)
+    emin, emax = api.spectral_bounds(ctx, H)
+    p = args.order
+    mom = api.chebyshev_moments(ctx, H, emin, emax, wk.probe_seed, wk.n_probes, p, not wk.mixed)
+    mu = api.fermi_level(ctx, mom, emin, emax, wk.n_electrons, wk.kT)[0]
+    args_ = (ctx, H, solver.model, pos, solver.box, emin, emax, wk.probe_seed, wk.n_probes, p, mu,
+             wk.kT, wk.jackson, not wk.mixed)
+    for _ in range(args.warmup):
+        api.density_and_forces(*args_)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(ctx.stream)
+    for _ in range(args.steps):
+        api.density_and_forces(*args_)
+    e1.record(ctx.stream)
+    torch.cuda.synchronize()
+    print(json.dumps({"only": "adjoint", "workload": wk.name, "order": p,
+                      "ms": e0.elapsed_time(e1) / args.steps}))
+    return 0
+
+
+def run_batched(args, rank, world):
+    """Many fcc clusters (sizes log-uniform in [100, 5000], kT in {0.025, 0.1, 0.5} eV, N(0, 0.05 A)
+    jitter, 128 probes each): energies and forces of the whole batch per step, the recurrence of
+    all clusters in one launch per step (CUDA-graph replay) and the backward sweeps likewise."""
+    import torch
+    from paper_1812_05264_gb300 import build as _build
+    _build.build()
+    from paper_1812_05264_gb300 import api
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = world > 1
+    if dist:
+        import torch.distributed as td
+        td.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    spec = wl.batched_clusters(64, 100, 5000, (0.025, 0.1, 0.5), seed=6464 + rank)
+    s = 128
+    wks = []
+    for i, (n, kT) in enumerate(zip(spec.sizes, spec.kTs)):
+        wk = wl.fcc_cu(int(n), kT=float(kT), n_probes=s, seed=5264, probe_seed=64000 + 97 * rank + i)
+        wk.positions = spec.positions[i]
+        wks.append(wk)
+    ctx = api.Context()
+    model = api.Solver(wks[0], ctx).model
+    hosts = [torch.from_numpy(np.ascontiguousarray(w.positions)).pin_memory() for w in wks]
+    devs = [h.to(f"cuda:{local}") for h in hosts]
+    mom_ev = []
+
+    def step(pos, record=False):
+        Hs, e0, e1, ps = [], [], [], []
+        for w, p_ in zip(wks, pos):
+            g = api.build_neighbors(ctx, p_, w.cutoff)
+            H = api.assemble_H(ctx, model, p_, g)
+            lo, hi = api.spectral_bounds(ctx, H)
+            Hs.append(H); e0.append(lo); e1.append(hi); ps.append(order_rule(hi - lo, w.kT))
+        seeds = [w.probe_seed for w in wks]
+        if record:
+            a = torch.cuda.Event(enable_timing=True); b = torch.cuda.Event(enable_timing=True)
+            a.record(ctx.stream)
+        mom = api.batched_moments(ctx, Hs, e0, e1, seeds, s, ps)
+        if record:
+            b.record(ctx.stream)
+            mom_ev.append((a, b, Hs, ps))
+        obs = api.batched_fermi_level(ctx, mom, e0, e1, [w.n_electrons for w in wks], [w.kT for w in wks])
+        _, Fs = api.batched_density_and_forces(ctx, Hs, model, pos, e0, e1, seeds, s, ps, obs[:, 0],
+                                               [w.kT for w in wks])
+        return ps, obs, Fs
+
+    for _ in range(args.warmup):
+        step(devs)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local, enabled=not args.no_clocks)
+    clocks.start()
+    l0 = ctx.launches
+    t0 = torch.cuda.Event(enable_timing=True); t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(ctx.stream)
+    for _ in range(args.steps):
+        ps, obs, Fs = step(devs, record=True)
+    t1.record(ctx.stream)
+    torch.cuda.synchronize()
+    launches = ctx.launches - l0
+    ms = t0.elapsed_time(t1) / args.steps
+    e_ms = []
+    for _ in range(max(1, min(args.steps, 2))):
+        a = torch.cuda.Event(enable_timing=True); b = torch.cuda.Event(enable_timing=True)
+        a.record(ctx.stream)
+        pe = [h.to(f"cuda:{local}", non_blocking=True) for h in hosts]
+        _, obs_e, Fe = step(pe)
+        outs = [f.cpu() for f in Fe]
+        b.record(ctx.stream)
+        torch.cuda.synchronize()
+        e_ms.append(a.elapsed_time(b))
+    clk = clocks.stop()
+    units = sum(w.n_atoms * s * p for w, p in zip(wks, ps))
+    # algorithmic bytes of the batched recurrence: active clusters per step
+    mom_ms = sum(a.elapsed_time(b) for a, b, _, _ in mom_ev)
+    _, _, Hs, ps_ = mom_ev[-1]
+    K = [p // 2 for p in ps_]
+    tot_bytes = 0
+    for j in range(1, max(K) + 1):
+        for H, k in zip(Hs, K):
+            if k >= j:
+                tot_bytes += 3 * H.graph.n_atoms * 9 * s * 4 + H.graph.nnzb * 81 * 4
+    tot_bytes *= len(mom_ev)
+    achieved = tot_bytes / (mom_ms / 1e3) / 1e9
+    peak = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", 6800.0)) \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6800.0
+    h2d = sum(h.numel() * 8 for h in hosts)
+    d2h = sum(w.n_atoms * 3 * 8 for w in wks)
+    line = {"metric": METRIC, "value": units * world / (ms / 1e3), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "batched64-fcc-sk9", "clusters": len(wks),
+                       "atoms": int(sum(w.n_atoms for w in wks)), "probes": s,
+                       "orders_p": [int(p) for p in ps], "kT": [float(w.kT) for w in wks],
+                       "l2": "merged panels (%.0f MB each) larger than L2" % (sum(w.n_atoms for w in wks) * 9 * s * 4 / 1e6),
+                       "parallelism": f"replicas x{world}"},
+            "e2e": {"value": units * world / (statistics.median(e_ms) / 1e3), "unit": UNIT,
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "kernel": "cheb_step_bulk (batched)",
+                         "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"},
+            "clocks": clk}
+    if rank == 0:
+        print(json.dumps(line))
+    if dist:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -380,12 +524,19 @@ def main():
     ap.add_argument("--workload", default="fcc10k")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only-moments", action="store_true", help="profiling aid: recurrence only")
-    ap.add_argument("--order", type=int, default=64, help="order for --only-moments")
+    ap.add_argument("--only-adjoint", action="store_true", help="profiling aid: adjoint only")
+    ap.add_argument("--no-clocks", action="store_true",
+                    help="do not run the nvidia-smi clock sampler (for runs under a profiler)")
+    ap.add_argument("--order-atoms", default="radius", choices=["radius", "morton"],
+                    help="atom order of the fcc workloads: by radius, or Morton order of 4 A cells")
+    ap.add_argument("--order", type=int, default=64, help="order for --only-moments / --only-adjoint")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.workload == "batched64":
+        return run_batched(args, rank, world)
     return run_ours(args, rank, world)
 
 

@@ -267,6 +267,8 @@ def run_ours(args, rank, world):
         return moments_only(args, ctx, solver, wk, pos)
     if args.only_adjoint:
         return adjoint_only(args, ctx, solver, wk, pos)
+    if args.compare_fp64:
+        return precision_compare(args, ctx, solver, wk, pos)
     for _ in range(max(args.warmup, 0)):
         p, _, _ = step(pos)
     torch.cuda.synchronize()
@@ -335,7 +337,7 @@ def run_ours(args, rank, world):
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": traffic_from_profile("cheb_step_fcc10000.md"),
+                     "frac": achieved / peak, "traffic": traffic_from_profile("cheb_step_bulk_fcc10000.md"),
                      "kernel": "cheb_step_kernel", "algorithmic_bytes_per_launch": bytes_per_launch,
                      "avg_launch_ms": mom_ms / launches_k, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"},
         "clocks": clk,
@@ -377,6 +379,34 @@ def moments_only(args, ctx, solver, wk, pos):
     ms = e0.elapsed_time(e1) / args.steps
     print(json.dumps({"only": "moments", "workload": wk.name, "order": p, "ms": ms,
                       "ms_per_launch": ms / (p // 2)}))
+    return 0
+
+
+def precision_compare(args, ctx, solver, wk, pos):
+    """Mixed (FP32 recurrence, FP64 moments) against the plain FP64 GPU path on the same
+    workload, probes and order: time per recurrence step and the energy difference per site."""
+    import torch
+    from paper_1812_05264_gb300 import api
+    g = api.build_neighbors(ctx, pos, wk.cutoff, solver.box)
+    H = api.assemble_H(ctx, solver.model, pos, g, solver.box)
+    emin, emax = api.spectral_bounds(ctx, H)
+    p = wk.order or order_rule(emax - emin, wk.kT)
+    out = {}
+    for name, fp64 in (("mixed", False), ("fp64", True)):
+        api.chebyshev_moments(ctx, H, emin, emax, wk.probe_seed, wk.n_probes, 8, fp64)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(ctx.stream)
+        mom = api.chebyshev_moments(ctx, H, emin, emax, wk.probe_seed, wk.n_probes, p, fp64)
+        e1.record(ctx.stream)
+        torch.cuda.synchronize()
+        mu, Om, E, N = api.fermi_level(ctx, mom, emin, emax, wk.n_electrons, wk.kT, wk.jackson)
+        out[name] = {"ms": e0.elapsed_time(e1), "ms_per_step": e0.elapsed_time(e1) / (p // 2),
+                     "Omega_per_site": Om / wk.n_atoms, "E_per_site": E / wk.n_atoms, "mu": mu}
+    out["speedup_mixed_over_fp64"] = out["fp64"]["ms"] / out["mixed"]["ms"]
+    out["energy_diff_per_site"] = abs(out["mixed"]["E_per_site"] - out["fp64"]["E_per_site"])
+    out["omega_diff_per_site"] = abs(out["mixed"]["Omega_per_site"] - out["fp64"]["Omega_per_site"])
+    print(json.dumps({"compare": "mixed_vs_fp64", "workload": wk.name, "order": p,
+                      "probes": wk.n_probes, "sites": wk.n_atoms, **out}))
     return 0
 
 
@@ -525,10 +555,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only-moments", action="store_true", help="profiling aid: recurrence only")
     ap.add_argument("--only-adjoint", action="store_true", help="profiling aid: adjoint only")
+    ap.add_argument("--compare-fp64", action="store_true",
+                    help="time the mixed path against the plain FP64 GPU path (same p, probes)")
     ap.add_argument("--no-clocks", action="store_true",
                     help="do not run the nvidia-smi clock sampler (for runs under a profiler)")
-    ap.add_argument("--order-atoms", default="radius", choices=["radius", "morton"],
-                    help="atom order of the fcc workloads: by radius, or Morton order of 4 A cells")
     ap.add_argument("--order", type=int, default=64, help="order for --only-moments / --only-adjoint")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))

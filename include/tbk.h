@@ -50,6 +50,7 @@ typedef enum {
 #define TBK_MOMENTS_DIRECT 2   /* mu_k = <r, y_k> for every k instead of the doubling identity */
 #define TBK_PLAIN_KERNEL 4     /* use the plain load/FMA step kernel instead of the TMA-fed one */
 #define TBK_NO_GRAPH 8         /* batched calls: enqueue the kernels directly, no CUDA graph */
+#define TBK_TENSOR_CORES 16    /* mixed mode: recurrence steps on the tensor cores (tcgen05, TF32 x3) */
 
 /* Damping of the Chebyshev series. */
 #define TBK_DAMP_NONE 0
@@ -156,10 +157,12 @@ int tbk_chebyshev_coefficients(tbk_ctx* ctx, int32_t fn, int32_t order, double e
    H^ = (2H - (emax + emin) I)/(emax - emin) and s = n_probes Rademacher probes r_i whose entry
    (row, j) is the sign of the top bit of SplitMix64 output number (row 2^32 + j + 1) of a stream
    seeded with probe_seed.  The probes are regenerated inside the kernels and never stored.
-   flags: TBK_MIXED or TBK_FP64, optionally | TBK_MOMENTS_DIRECT | TBK_PLAIN_KERNEL.  n_probes
-   must be a multiple of 4; in mixed mode with 9x9 blocks and n_probes a multiple of 128 the
-   steps stream neighbour tiles through shared memory with bulk (TMA) copies.  TBK_ERR_TIMEOUT
-   reports an expired bounded wait inside that kernel.  Fails with TBK_ERR_SPECTRUM if a panel grows beyond the bound that holds
+   flags: TBK_MIXED or TBK_FP64, optionally | TBK_MOMENTS_DIRECT | TBK_PLAIN_KERNEL |
+   TBK_TENSOR_CORES.  n_probes must be a multiple of 4; in mixed mode with 9x9 blocks and
+   n_probes a multiple of 128 the steps stream neighbour tiles through shared memory with bulk
+   (TMA) copies, and with TBK_TENSOR_CORES the block products run as tcgen05 TF32 MMAs with a
+   three-way split (head x head + head x rest + rest x head, FP32 accuracy).  TBK_ERR_TIMEOUT
+   reports an expired bounded wait inside those kernels.  Fails with TBK_ERR_SPECTRUM if a panel grows beyond the bound that holds
    when the spectrum of H^ lies in [-1, 1]. */
 int tbk_chebyshev_moments(tbk_ctx* ctx, const tbk_bsr* H, double emin, double emax,
                           uint64_t probe_seed, int32_t n_probes, int32_t order, int32_t flags,

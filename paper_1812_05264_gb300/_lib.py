@@ -23,6 +23,7 @@ TBK_FP64 = 1
 TBK_MOMENTS_DIRECT = 2
 TBK_PLAIN_KERNEL = 4
 TBK_NO_GRAPH = 8
+TBK_TENSOR_CORES = 16
 TBK_DAMP_NONE = 0
 TBK_DAMP_JACKSON = 1
 TBK_FN_FERMI = 0

@@ -164,12 +164,13 @@ def chebyshev_coefficients(ctx: Context, fn: int, order: int, emin: float, emax:
 
 def chebyshev_moments(ctx: Context, H: BSR, emin: float, emax: float, seed: int, n_probes: int,
                       order: int, fp64: bool = False, direct: bool = False,
-                      out: torch.Tensor | None = None, plain: bool = False) -> torch.Tensor:
+                      out: torch.Tensor | None = None, plain: bool = False,
+                      tensor_cores: bool = False) -> torch.Tensor:
     """a5-a7: mu_k = (1/s) sum_i r_i^T C_k(H^) r_i for k < order."""
     if out is None:
         out = torch.empty(order, dtype=torch.float64, device=H.val.device)
     flags = ((L.TBK_FP64 if fp64 else L.TBK_MIXED) | (L.TBK_MOMENTS_DIRECT if direct else 0)
-             | (L.TBK_PLAIN_KERNEL if plain else 0))
+             | (L.TBK_PLAIN_KERNEL if plain else 0) | (L.TBK_TENSOR_CORES if tensor_cores else 0))
     L.call("tbk_chebyshev_moments", ctx.handle, C.byref(H.struct()), emin, emax, C.c_uint64(seed),
            int(n_probes), int(order), flags, _ptr(out))
     return out

@@ -60,6 +60,7 @@ struct StepArgs {
   // partials + 2 (a * CW + warp) instead of per CTA (CW = consumer warps, bulk_consumer_warps).
   BatchRows batch;
   int per_task = 0;
+  int use_tc = 0;           // tensor-core (tcgen05) step where it applies
 };
 // Consumer warps of the TMA-fed step kernel for this operator and probe count (0 = not used).
 int bulk_consumer_warps(const HOp& op, int s);

@@ -530,6 +530,10 @@ static dim3 simple_block(int s) {
   return dim3(lanes, STEP_THREADS / lanes);
 }
 
+bool tc_eligible(const HOp& op, int s);
+int tc_grid(tbk_ctx* ctx);
+void launch_step_tc(tbk_ctx* ctx, const HOp& op, const StepArgs& a, int G);
+
 int step_grid_ctas(tbk_ctx* ctx, const HOp& op, int s) {
   Occ& o = occ_cache(ctx->device);
   if (!o.simple) {
@@ -546,7 +550,9 @@ int step_grid_ctas(tbk_ctx* ctx, const HOp& op, int s) {
   int per_sm = o.simple;
   const int cw = bulk_warps(op, s);
   if (cw && o.bulk[cw] > 0) per_sm = std::min(per_sm, o.bulk[cw]);
-  return std::max(1, per_sm * ctx->num_sms);
+  int G = std::max(1, per_sm * ctx->num_sms);
+  if (tc_eligible(op, s)) G = std::min(G, tc_grid(ctx));
+  return G;
 }
 
 template <typename T, int B>
@@ -576,6 +582,11 @@ static void launch_bulk(tbk_ctx* ctx, const HOp& op, const StepArgs& a, int G) {
 
 void launch_step(tbk_ctx* ctx, const HOp& op, const StepArgs& a) {
   const int G = step_grid_ctas(ctx, op, a.s);
+  if (a.use_tc && !a.cur_is_probe && a.err && !a.force_simple && !a.batch.atom_cl && !a.per_task &&
+      tc_eligible(op, a.s)) {
+    launch_step_tc(ctx, op, a, G);
+    return;
+  }
   const int cw = bulk_warps(op, a.s);
   if (cw && !a.cur_is_probe && a.err && !a.force_simple && occ_cache(ctx->device).bulk[cw] > 0) {
     if (cw == 4) launch_bulk<4>(ctx, op, a, G);
@@ -733,7 +744,8 @@ extern "C" int tbk_chebyshev_moments(tbk_ctx* ctx, const tbk_bsr* H, double emin
   TBK_CHECK_ARG(moments != nullptr, "moments is NULL");
   TBK_CHECK_ARG(order >= 1, "order must be >= 1");
   TBK_CHECK_ARG(n_probes >= 4 && n_probes % 4 == 0, "n_probes must be a positive multiple of 4");
-  TBK_CHECK_ARG((flags & ~(TBK_FP64 | TBK_MOMENTS_DIRECT | TBK_PLAIN_KERNEL)) == 0, "unknown flag");
+  TBK_CHECK_ARG((flags & ~(TBK_FP64 | TBK_MOMENTS_DIRECT | TBK_PLAIN_KERNEL | TBK_TENSOR_CORES)) == 0,
+                "unknown flag");
   DeviceGuard dg(ctx);
   const int prec = (flags & TBK_FP64) ? TBK_FP64 : TBK_MIXED;
   const int direct = (flags & TBK_MOMENTS_DIRECT) ? 1 : 0;
@@ -758,6 +770,7 @@ extern "C" int tbk_chebyshev_moments(tbk_ctx* ctx, const tbk_bsr* H, double emin
     a.partials = partials + (size_t)(j - 1) * nctas * 2;
     a.err = flag;
     a.force_simple = (flags & TBK_PLAIN_KERNEL) ? 1 : 0;
+    a.use_tc = (flags & TBK_TENSOR_CORES) ? 1 : 0;
     if (j == 1) {
       a.cur_is_probe = 1;
       a.alpha = 1.0;

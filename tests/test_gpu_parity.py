@@ -303,3 +303,26 @@ def test_fused_clenshaw_outer_product_kernel(api, ctx, s):
     assert torch.allclose(F1, F2, rtol=0, atol=1e-4)
     _, F = oracle_estimator_forces(wk, rp, col, est, res.emin, res.emax, p)
     assert np.abs(F1.cpu().numpy() - F).max() < 1e-3
+
+
+# ---- the tensor-core step (tcgen05, TF32 split three ways) ------------------------------------
+
+@pytest.mark.parametrize("s", [128, 256, 512])
+def test_tensor_core_step_matches_fp32_kernels_and_oracle(api, ctx, s):
+    wk = small_fcc(90, n_probes=s, jitter=0.05)
+    rp, col, H = oracle_H(wk)
+    sv = api.Solver(wk, ctx)
+    pos = _dev(wk.positions)
+    g = api.build_neighbors(ctx, pos, wk.cutoff)
+    Hg = api.assemble_H(ctx, sv.model, pos, g)
+    emin, emax = api.spectral_bounds(ctx, Hg)
+    p = 101
+    m_tc = api.chebyshev_moments(ctx, Hg, emin, emax, wk.probe_seed, s, p, tensor_cores=True)
+    m_fp32 = api.chebyshev_moments(ctx, Hg, emin, emax, wk.probe_seed, s, p)
+    n = H.shape[0]
+    est = oracle_estimator(wk, H, emin, emax, p)
+    assert np.abs(m_tc.cpu().numpy() - est["moments"]).max() < 2e-5 * n
+    assert np.abs(m_tc.cpu().numpy() - m_fp32.cpu().numpy()).max() < 2e-5 * n
+    mu, Om, E, N = api.fermi_level(ctx, m_tc, emin, emax, wk.n_electrons, wk.kT)
+    assert abs(Om - est["Omega"]) / wk.n_atoms < 1e-4
+    assert abs(E - est["E"]) / wk.n_atoms < 1e-4

@@ -158,9 +158,10 @@ __global__ void __launch_bounds__(32 * (CW + 1))
 clenshaw_sddmm_bulk(const int n_atoms, const int32_t* __restrict__ row_ptr,
                     const int32_t* __restrict__ col, const float* __restrict__ hv,
                     const float* __restrict__ bin, const float* bprev, float* bout,
-                    const float* __restrict__ ypan, const float c_r, const uint64_t seed,
+                    const float* __restrict__ ypan, const float4 cf, const uint64_t seed,
                     const int s, const double w, double* __restrict__ Gacc, int* __restrict__ err,
-                    const BatchRows batch, const float* __restrict__ c_cl) {
+                    const BatchRows batch, const float4* __restrict__ cf_cl,
+                    const float* __restrict__ ym1, const float* __restrict__ yp1) {
   using C = SdCfg<CW>;
   constexpr int D = C::D;
   extern __shared__ __align__(128) unsigned char smem[];
@@ -187,6 +188,16 @@ clenshaw_sddmm_bulk(const int n_atoms, const int32_t* __restrict__ row_ptr,
   }
   __syncthreads();
 
+  // own-row tiles streamed after the neighbour tiles, with their coefficients:
+  // b_prev (-1), y_{k-1} (cf.z), y_{k+1} (cf.w)
+  const float* extra_src[3];
+  float extra_cf[3];
+  int n_extra = 0;
+  if (has_out) {
+    if (has_prev) { extra_src[n_extra] = bprev; extra_cf[n_extra++] = -1.f; }
+    if (ym1 && cf.z != 0.f) { extra_src[n_extra] = ym1; extra_cf[n_extra++] = cf.z; }
+    if (yp1 && cf.w != 0.f) { extra_src[n_extra] = yp1; extra_cf[n_extra++] = cf.w; }
+  }
   if (warp == CW) {
     if (lane == 0) {
       int it = 0, own_it = 0, y_it = 0;
@@ -200,9 +211,12 @@ clenshaw_sddmm_bulk(const int n_atoms, const int32_t* __restrict__ row_ptr,
           bulk_g2s(smem_u32(Ys), ypan + (int64_t)9 * a * s, C::XB, y_full);
           ++y_it;
         }
-        const int nt = k1 - k0 + ((has_prev && has_out) ? 1 : 0);
+        // after the neighbour tiles: the own-row tiles of b_prev, y_{k-1} and y_{k+1} (when used)
+        const int nb = k1 - k0;
+        const int nt = nb + n_extra;
         for (int q = 0; q < nt && ok; ++q) {
-          const bool is_prev = q == k1 - k0;
+          const bool is_prev = q >= nb;
+          const float* extra = is_prev ? extra_src[q - nb] : nullptr;
           const int b = is_prev ? a : __ldg(col + k0 + q);
           const bool is_own = !is_prev && b == a;
           uint32_t dst, bar;
@@ -219,7 +233,7 @@ clenshaw_sddmm_bulk(const int n_atoms, const int32_t* __restrict__ row_ptr,
             ++it;
           }
           if (!ok) break;
-          const float* src = (is_prev ? bprev : bin) + (int64_t)9 * b * s;
+          const float* src = (is_prev ? extra : bin) + (int64_t)9 * b * s;
           mbar_expect_tx(bar, C::XB + (is_prev ? 0 : C::HB));
           bulk_g2s(dst, src, C::XB, bar);
           if (!is_prev) bulk_g2s(dst + C::XB, hv + (int64_t)(k0 + q) * Layout<float, 9>::BS, C::HB, bar);
@@ -241,12 +255,12 @@ clenshaw_sddmm_bulk(const int n_atoms, const int32_t* __restrict__ row_ptr,
     // probe stream and cluster-local row of this atom; per-cluster coefficient in batches
     uint64_t sd = seed;
     int64_t rloc = (int64_t)9 * a;
-    float cr = c_r;
+    float4 cfa = cf;  // (probe, own y, y_{k-1}, y_{k+1}) coefficients of the source term
     if (batch.atom_cl) {
       const int cl = __ldg(batch.atom_cl + a);
       sd = __ldg(batch.seed + cl);
       rloc = (int64_t)9 * (a - __ldg(batch.atom0 + cl));
-      if (c_cl) cr = __ldg(c_cl + cl);
+      if (cf_cl) cfa = cf_cl[cl];
     }
     if (!y_probe) {
       ok = mbar_wait(y_full, y_it & 1);
@@ -279,40 +293,60 @@ clenshaw_sddmm_bulk(const int n_atoms, const int32_t* __restrict__ row_ptr,
       if (is_own) ++own_it; else ++it;
     }
     if (!ok) break;
-    if (!y_probe) {
-      __syncwarp();
-      if (lane == 0) mbar_arrive(y_empty);
-      ++y_it;
+    if (!has_out) {
+      if (!y_probe) {
+        __syncwarp();
+        if (lane == 0) mbar_arrive(y_empty);
+        ++y_it;
+      }
+      continue;
     }
-    if (!has_out) continue;
-    float yp[9][4];
-    if (has_prev) {
+    // y_out = 2 H^ b_in + cf.x r + cf.y y_own + (own-row tiles: -b_prev + cf.z y_{k-1} + cf.w y_{k+1})
+    float yo[9][4];
+#pragma unroll
+    for (int i = 0; i < 9; ++i)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) yo[i][v] = 2.f * ((i & 1) ? acc[i >> 1][v].y : acc[i >> 1][v].x);
+    if (cfa.x != 0.f) {
+#pragma unroll
+      for (int i = 0; i < 9; ++i)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) yo[i][v] = fmaf(cfa.x, tbk_probe_sign(sd, rloc + i, pl + v), yo[i][v]);
+    }
+    if (cfa.y != 0.f && !y_probe) {
+#pragma unroll
+      for (int i = 0; i < 9; ++i) {
+        const float4 t = *reinterpret_cast<const float4*>(Ys + i * C::P + pl);
+        yo[i][0] = fmaf(cfa.y, t.x, yo[i][0]); yo[i][1] = fmaf(cfa.y, t.y, yo[i][1]);
+        yo[i][2] = fmaf(cfa.y, t.z, yo[i][2]); yo[i][3] = fmaf(cfa.y, t.w, yo[i][3]);
+      }
+    }
+    for (int e = 0; e < n_extra; ++e) {
       const int st = it % D;
       ok = mbar_wait(full(st), (it / D) & 1);
       if (!ok) break;
       const float* X = reinterpret_cast<const float*>(smem + st * C::SB);
+      const float ce = extra_cf[e];
 #pragma unroll
-      for (int l = 0; l < 9; ++l) {
-        const float4 t = *reinterpret_cast<const float4*>(X + l * C::P + pl);
-        yp[l][0] = t.x; yp[l][1] = t.y; yp[l][2] = t.z; yp[l][3] = t.w;
+      for (int i = 0; i < 9; ++i) {
+        const float4 t = *reinterpret_cast<const float4*>(X + i * C::P + pl);
+        yo[i][0] = fmaf(ce, t.x, yo[i][0]); yo[i][1] = fmaf(ce, t.y, yo[i][1]);
+        yo[i][2] = fmaf(ce, t.z, yo[i][2]); yo[i][3] = fmaf(ce, t.w, yo[i][3]);
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(empty(st));
       ++it;
     }
+    if (!ok) break;
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
       const int64_t row = (int64_t)9 * a + i;
-      float yo[4];
-#pragma unroll
-      for (int v = 0; v < 4; ++v)
-        yo[v] = fmaf(cr, tbk_probe_sign(sd, rloc + i, pl + v),
-                     2.f * ((i & 1) ? acc[i >> 1][v].y : acc[i >> 1][v].x));
-      if (has_prev) {
-#pragma unroll
-        for (int v = 0; v < 4; ++v) yo[v] -= yp[i][v];
-      }
-      *reinterpret_cast<float4*>(bout + row * s + pl) = make_float4(yo[0], yo[1], yo[2], yo[3]);
+      *reinterpret_cast<float4*>(bout + row * s + pl) = make_float4(yo[i][0], yo[i][1], yo[i][2], yo[i][3]);
+    }
+    if (!y_probe) {
+      __syncwarp();
+      if (lane == 0) mbar_arrive(y_empty);
+      ++y_it;
     }
   }
   if (!ok) atomicOr(err, 2);
@@ -407,8 +441,9 @@ bool fused_eligible(const HOp& op, int s, int plain) {
 
 template <int CW>
 static void launch_fused_cw(tbk_ctx* ctx, const HOp& op, const void* bin, const void* bprev, void* bout,
-                            const void* ypan, double c_r, uint64_t seed, int s, double w, double* Gacc,
-                            int* err, const BatchRows& batch, const float* c_cl) {
+                            const void* ypan, float4 cf, uint64_t seed, int s, double w, double* Gacc,
+                            int* err, const BatchRows& batch, const float4* cf_cl, const void* ym1,
+                            const void* yp1) {
   using C = SdCfg<CW>;
   TBK_CUDA(cudaFuncSetAttribute(clenshaw_sddmm_bulk<CW>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
   int occ = 0;
@@ -417,16 +452,21 @@ static void launch_fused_cw(tbk_ctx* ctx, const HOp& op, const void* bin, const 
   const int G = std::max(1, std::min(op.n_atoms, occ * ctx->num_sms));
   clenshaw_sddmm_bulk<CW><<<G, C::THREADS, C::SMEM, ctx->stream>>>(
       op.n_atoms, op.row_ptr, op.col, (const float*)op.hv, (const float*)bin, (const float*)bprev,
-      (float*)bout, (const float*)ypan, (float)c_r, seed, s, w, Gacc, err, batch, c_cl);
+      (float*)bout, (const float*)ypan, cf, seed, s, w, Gacc, err, batch, cf_cl, (const float*)ym1,
+      (const float*)yp1);
   post_launch(ctx, "clenshaw_sddmm_bulk");
 }
 
 void launch_fused(tbk_ctx* ctx, const HOp& op, const void* bin, const void* bprev, void* bout,
-                  const void* ypan, double c_r, uint64_t seed, int s, double w, double* Gacc,
-                  int* err, const BatchRows& batch, const float* c_cl) {
-  if (s == 512) launch_fused_cw<4>(ctx, op, bin, bprev, bout, ypan, c_r, seed, s, w, Gacc, err, batch, c_cl);
-  else if (s == 256) launch_fused_cw<2>(ctx, op, bin, bprev, bout, ypan, c_r, seed, s, w, Gacc, err, batch, c_cl);
-  else launch_fused_cw<1>(ctx, op, bin, bprev, bout, ypan, c_r, seed, s, w, Gacc, err, batch, c_cl);
+                  const void* ypan, float4 cf, uint64_t seed, int s, double w, double* Gacc,
+                  int* err, const BatchRows& batch, const float4* cf_cl, const void* ym1,
+                  const void* yp1) {
+  if (s == 512)
+    launch_fused_cw<4>(ctx, op, bin, bprev, bout, ypan, cf, seed, s, w, Gacc, err, batch, cf_cl, ym1, yp1);
+  else if (s == 256)
+    launch_fused_cw<2>(ctx, op, bin, bprev, bout, ypan, cf, seed, s, w, Gacc, err, batch, cf_cl, ym1, yp1);
+  else
+    launch_fused_cw<1>(ctx, op, bin, bprev, bout, ypan, cf, seed, s, w, Gacc, err, batch, cf_cl, ym1, yp1);
 }
 
 static void launch_sddmm(tbk_ctx* ctx, const HOp& op, const void* y, int y_is_probe, uint64_t seed,
@@ -486,6 +526,153 @@ void launch_forces(tbk_ctx* ctx, const DevModel& M, const double* pos, int n_ato
   post_launch(ctx, "gather_forces");
 }
 
+// ---- adjoint of the doubled moments (TMA-fed fused path) ------------------------------------
+//
+// The moments come from the doubling identities (C_m C_n = (C_{m+n} + C_{|m-n|})/2):
+//   mu_2k = 2 e_k - mu_0,  mu_2k-1 = 2 o_k - mu_1,  e_k = <y_k, y_k>/s,  o_k = <y_k, y_{k-1}>/s,
+// so Omega^ = sum_m c_m mu_m = const + sum_{k=1..K} (w_k e_k + v_k o_k),  K = floor(p/2), with
+//   w_k = 2 c_2k (2k < p),  v_1 = c_1 - sum_{k>=2} c_{2k-1},  v_k = 2 c_{2k-1} (k >= 2, 2k-1 < p).
+// Reverse-mode differentiation through y_{k+1} = 2 H^ y_k - y_{k-1} (y_1 = H^ y_0, y_0 = r):
+//   ybar_K = g_K,  ybar_k = g_k + 2 H^ ybar_{k+1} - ybar_{k+2},
+//   g_k = (2 w_k y_k + v_k y_{k-1} + v_{k+1} y_{k+1}) / s,
+//   dOmega^/dH^ = sum_{k=1}^{K-1} 2 ybar_{k+1} y_k^T + ybar_1 y_0^T.
+// This needs the y_k only up to K = p/2: half the forward, replay and backward work of the
+// Clenshaw form of Eq. polynomial_response, for the same estimator and the same gradient.
+
+__global__ void ybar_init(int64_t n, int s, float ca, const float* __restrict__ yk, float cb,
+                          const float* __restrict__ ykm1, uint64_t seed, float* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n * s) return;
+  const int64_t row = i / s;
+  const int p = (int)(i - row * s);
+  const float prev = ykm1 ? ykm1[i] : tbk_probe_sign(seed, row, p);
+  out[i] = fmaf(ca, yk[i], cb * prev);
+}
+
+void adjoint_doubling(tbk_ctx* ctx, const HOp& op, uint64_t probe_seed, int s, const std::vector<double>& c,
+                      int64_t max_panel_bytes, double* Gacc, int* err) {
+  const int p = (int)c.size();
+  const int K = p / 2;
+  if (K < 1) return;  // p = 1: the estimate does not depend on H
+  // source-term coefficients
+  std::vector<double> w(K + 2, 0.0), v(K + 2, 0.0);
+  for (int k = 1; k <= K; ++k) {
+    if (2 * k < p) w[k] = 2.0 * c[2 * k];
+    if (k >= 2 && 2 * k - 1 < p) v[k] = 2.0 * c[2 * k - 1];
+  }
+  v[1] = p > 1 ? c[1] : 0.0;
+  for (int k = 2; 2 * k - 1 < p; ++k) v[1] -= c[2 * k - 1];
+  auto ca = [&](int k) { return (float)(2.0 * w[k] / s); };
+  auto cb = [&](int k) { return (float)(v[k] / s); };
+  auto cc = [&](int k) { return (float)(v[k + 1] / s); };
+
+  const size_t panel = (size_t)op.n_rows * s * 4;
+  size_t budget = (size_t)std::max<int64_t>(0, max_panel_bytes);
+  if (budget == 0) {
+    size_t fr = 0, tot = 0;
+    TBK_CUDA(cudaMemGetInfo(&fr, &tot));
+    budget = (size_t)(0.6 * (double)fr);
+  }
+  const int npan = K;  // y_1 .. y_K
+  int seg = std::max(1, npan);
+  if ((size_t)(npan + 4) * panel > budget && npan > 2) {
+    seg = std::max(2, (int)std::ceil(std::sqrt(2.0 * npan)));
+    const size_t need = (size_t)(2 * ((npan + seg - 1) / seg) + seg + 4) * panel;
+    if (need > budget)
+      throw Error(TBK_ERR_OOM, "panel scratch budget of " + std::to_string(budget) +
+                                   " bytes is below the checkpoint plan's " + std::to_string(need));
+  }
+  const int nseg = (npan + seg - 1) / seg;
+  const bool all_stored = nseg <= 1;
+  // P(0 .. seg): segment panels (P(i) = y_{t0 - 1 + i}); checkpoints (y_{t0-2}, y_{t0-1}); E = y_{t1+1};
+  // two ybar panels
+  const size_t n_seg_pan = (size_t)seg + 1, n_ckpt = all_stored ? 0 : 2 * (size_t)nseg;
+  char* base = (char*)scratch(ctx, WS_CHECKPOINTS, panel * (n_seg_pan + n_ckpt + 3));
+  auto P = [&](size_t i) { return (void*)(base + i * panel); };
+  auto CK = [&](int sg, int which) { return P(n_seg_pan + 2 * (size_t)sg + which); };
+  void* E = P(n_seg_pan + n_ckpt);
+  void* bcur = P(n_seg_pan + n_ckpt + 1);
+  void* bprev = P(n_seg_pan + n_ckpt + 2);
+  auto forward_step = [&](int t, const void* yin, const void* yprev, void* yout) {
+    StepArgs a;
+    a.seed = probe_seed;
+    a.s = s;
+    a.yin = yin;
+    a.cur_is_probe = t == 1;
+    a.alpha = t == 1 ? 1.0 : 2.0;
+    if (t == 2) a.c_r = -1.0;
+    else if (t >= 3) a.yprev = const_cast<void*>(yprev);
+    a.yout = yout;
+    a.err = err;
+    launch_step(ctx, op, a);
+  };
+  if (!all_stored) {
+    void *cur = nullptr, *prv = nullptr;
+    const int last = seg * (nseg - 1);
+    for (int t = 1; t <= last; ++t) {
+      void* out = t == 1 ? P(0) : (t == 2 ? P(1) : prv);
+      forward_step(t, cur, prv, out);
+      prv = cur;
+      cur = out;
+      if (t % seg == 0) {
+        const int sg = t / seg;
+        TBK_CUDA(cudaMemcpyAsync(CK(sg, 0), prv, panel, cudaMemcpyDeviceToDevice, ctx->stream));
+        TBK_CUDA(cudaMemcpyAsync(CK(sg, 1), cur, panel, cudaMemcpyDeviceToDevice, ctx->stream));
+      }
+    }
+  }
+  int k = K;
+  bool have_bprev = false;
+  for (int sg = nseg - 1; sg >= -1 && k >= 0; --sg) {
+    const int t0 = sg >= 0 ? 1 + seg * sg : 0;
+    const int t1 = sg >= 0 ? std::min(npan, t0 + seg - 1) : 0;
+    if (sg >= 0) {
+      if (sg < nseg - 1) {
+        // y_{t1+1} is the first panel of the segment just finished
+        TBK_CUDA(cudaMemcpyAsync(E, P(1), panel, cudaMemcpyDeviceToDevice, ctx->stream));
+      }
+      int t = t0;
+      if (sg > 0) {
+        TBK_CUDA(cudaMemcpyAsync(P(0), CK(sg, 1), panel, cudaMemcpyDeviceToDevice, ctx->stream));
+        forward_step(t0, P(0), CK(sg, 0), P(1));
+        ++t;
+      }
+      for (; t <= t1; ++t) {
+        const int i = t - t0 + 1;
+        forward_step(t, t == 1 ? nullptr : P(i - 1), t >= 3 ? P(i - 2) : nullptr, P(i));
+      }
+    }
+    // y_j for j in [t0 - 1, t1 + 1] (nullptr = the probe block r = y_0)
+    auto Y = [&](int j) -> const void* {
+      if (j == 0) return nullptr;
+      if (j == t1 + 1) return E;
+      return P(j - t0 + 1);
+    };
+    for (; k >= t0; --k) {
+      if (k == K) {
+        // ybar_K = g_K (y_{K+1} does not enter)
+        const int64_t n = op.n_rows * s;
+        ybar_init<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(
+            op.n_rows, s, ca(K), (const float*)Y(K), cb(K), (const float*)Y(K - 1), probe_seed, (float*)bcur);
+        post_launch(ctx, "ybar_init");
+        continue;
+      }
+      if (k >= 1) {
+        // ybar_k = g_k + 2 H^ ybar_{k+1} - ybar_{k+2}, and G += 2 y_k ybar_{k+1}^T on the pattern
+        const float4 cf = make_float4(k == 1 ? cb(1) : 0.f, ca(k), k == 1 ? 0.f : cb(k), cc(k));
+        launch_fused(ctx, op, bcur, have_bprev ? bprev : nullptr, bprev, Y(k), cf, probe_seed, s, 2.0, Gacc,
+                     err, BatchRows(), nullptr, k >= 2 ? Y(k - 1) : nullptr, Y(k + 1));
+        std::swap(bcur, bprev);
+        have_bprev = true;
+      } else {
+        // G += y_0 ybar_1^T
+        launch_fused(ctx, op, bcur, nullptr, nullptr, nullptr, make_float4(0.f, 0.f, 0.f, 0.f), probe_seed, s,
+                     1.0, Gacc, err, BatchRows(), nullptr, nullptr, nullptr);
+      }
+    }
+  }
+}
+
 }  // namespace tbk
 
 using namespace tbk;
@@ -536,124 +723,118 @@ extern "C" int tbk_density_and_forces(tbk_ctx* ctx, const tbk_bsr* H, const tbk_
 
   const size_t esz = prec == TBK_MIXED ? 4 : 8;
   const size_t panel = (size_t)op.n_rows * s * esz;
-  // Panels y_1 .. y_{p-2} are needed in reverse order: all of them are kept when they fit the
-  // budget, else segments of ~sqrt(2p) steps are replayed from checkpoints.
-  const int npan = std::max(0, p - 2);  // y_1 .. y_{p-2}
-  size_t budget = (size_t)std::max<int64_t>(0, max_panel_bytes);
-  if (budget == 0) {
-    size_t fr = 0, tot = 0;
-    TBK_CUDA(cudaMemGetInfo(&fr, &tot));
-    budget = (size_t)(0.6 * (double)fr);
-  }
-  int seg = std::max(1, npan);
-  if ((size_t)(npan + 3) * panel > budget && npan > 2) {
-    seg = std::max(2, (int)std::ceil(std::sqrt(2.0 * npan)));
-    const size_t need = (size_t)(2 * ((npan + seg - 1) / seg) + seg + 3) * panel;
-    if (need > budget)
-      throw Error(TBK_ERR_OOM, "panel scratch budget of " + std::to_string(budget) +
-                                   " bytes is below the checkpoint plan's " + std::to_string(need));
-  }
-  const int nseg = npan > 0 ? (npan + seg - 1) / seg : 0;
-  const bool all_stored = nseg <= 1;
-  // Scratch layout: P(0 .. seg) segment panels, P(seg+1 ..) checkpoints, then two b panels.
-  // Segment sg covers y_j for j in [t0, t1], t0 = 1 + seg sg, t1 = min(p - 2, t0 + seg - 1),
-  // and holds y_{t0 - 1 + i} at P(i).  Checkpoint sg (sg >= 1) is (y_{t0-2}, y_{t0-1}).
-  const size_t n_seg_pan = (size_t)seg + 1;
-  const size_t n_ckpt = all_stored ? 0 : 2 * (size_t)nseg;
-  char* base = (char*)scratch(ctx, WS_CHECKPOINTS, panel * (n_seg_pan + n_ckpt + 2));
-  auto P = [&](size_t i) { return (void*)(base + i * panel); };
-  auto CK = [&](int sg, int which) { return P(n_seg_pan + 2 * (size_t)sg + which); };
-  void* bcur = P(n_seg_pan + n_ckpt);
-  void* bprev = P(n_seg_pan + n_ckpt + 1);
+  double scale = 2.0 / (W * s);
+  if (fused) {
+    adjoint_doubling(ctx, op, probe_seed, s, c, max_panel_bytes, Gacc, err);
+    scale = 2.0 / W;  // the 1/s of the moments is inside the source terms
+  } else {
+    // Panels y_1 .. y_{p-2} are needed in reverse order: all of them are kept when they fit the
+    // budget, else segments of ~sqrt(2p) steps are replayed from checkpoints.
+    const int npan = std::max(0, p - 2);  // y_1 .. y_{p-2}
+    size_t budget = (size_t)std::max<int64_t>(0, max_panel_bytes);
+    if (budget == 0) {
+      size_t fr = 0, tot = 0;
+      TBK_CUDA(cudaMemGetInfo(&fr, &tot));
+      budget = (size_t)(0.6 * (double)fr);
+    }
+    int seg = std::max(1, npan);
+    if ((size_t)(npan + 3) * panel > budget && npan > 2) {
+      seg = std::max(2, (int)std::ceil(std::sqrt(2.0 * npan)));
+      const size_t need = (size_t)(2 * ((npan + seg - 1) / seg) + seg + 3) * panel;
+      if (need > budget)
+        throw Error(TBK_ERR_OOM, "panel scratch budget of " + std::to_string(budget) +
+                                     " bytes is below the checkpoint plan's " + std::to_string(need));
+    }
+    const int nseg = npan > 0 ? (npan + seg - 1) / seg : 0;
+    const bool all_stored = nseg <= 1;
+    // Scratch layout: P(0 .. seg) segment panels, P(seg+1 ..) checkpoints, then two b panels.
+    // Segment sg covers y_j for j in [t0, t1], t0 = 1 + seg sg, t1 = min(p - 2, t0 + seg - 1),
+    // and holds y_{t0 - 1 + i} at P(i).  Checkpoint sg (sg >= 1) is (y_{t0-2}, y_{t0-1}).
+    const size_t n_seg_pan = (size_t)seg + 1;
+    const size_t n_ckpt = all_stored ? 0 : 2 * (size_t)nseg;
+    char* base = (char*)scratch(ctx, WS_CHECKPOINTS, panel * (n_seg_pan + n_ckpt + 2));
+    auto P = [&](size_t i) { return (void*)(base + i * panel); };
+    auto CK = [&](int sg, int which) { return P(n_seg_pan + 2 * (size_t)sg + which); };
+    void* bcur = P(n_seg_pan + n_ckpt);
+    void* bprev = P(n_seg_pan + n_ckpt + 1);
 
-  // y_t from y_{t-1} (yin; the probe block when t == 1) and y_{t-2} (the probe when t == 2).
-  auto forward_step = [&](int t, const void* yin, const void* yprev, void* yout) {
-    StepArgs a;
-    a.seed = probe_seed;
-    a.s = s;
-    a.yin = yin;
-    a.cur_is_probe = t == 1;
-    a.alpha = t == 1 ? 1.0 : 2.0;
-    if (t == 2) a.c_r = -1.0;
-    else if (t >= 3) a.yprev = const_cast<void*>(yprev);
-    a.yout = yout;
-    a.err = err;
-    a.force_simple = plain;
-    launch_step(ctx, op, a);
-  };
-  // Forward sweep to the last checkpoint, with two rotating panels.
-  if (!all_stored) {
-    void *cur = nullptr, *prv = nullptr;
-    const int last = seg * (nseg - 1);
-    for (int t = 1; t <= last; ++t) {
-      void* out = t == 1 ? P(0) : (t == 2 ? P(1) : prv);
-      forward_step(t, cur, prv, out);
-      prv = cur;
-      cur = out;
-      if (t % seg == 0) {
-        const int sg = t / seg;  // the segment starting at t0 = t + 1
-        TBK_CUDA(cudaMemcpyAsync(CK(sg, 0), prv, panel, cudaMemcpyDeviceToDevice, ctx->stream));
-        TBK_CUDA(cudaMemcpyAsync(CK(sg, 1), cur, panel, cudaMemcpyDeviceToDevice, ctx->stream));
+    // y_t from y_{t-1} (yin; the probe block when t == 1) and y_{t-2} (the probe when t == 2).
+    auto forward_step = [&](int t, const void* yin, const void* yprev, void* yout) {
+      StepArgs a;
+      a.seed = probe_seed;
+      a.s = s;
+      a.yin = yin;
+      a.cur_is_probe = t == 1;
+      a.alpha = t == 1 ? 1.0 : 2.0;
+      if (t == 2) a.c_r = -1.0;
+      else if (t >= 3) a.yprev = const_cast<void*>(yprev);
+      a.yout = yout;
+      a.err = err;
+      a.force_simple = plain;
+      launch_step(ctx, op, a);
+    };
+    // Forward sweep to the last checkpoint, with two rotating panels.
+    if (!all_stored) {
+      void *cur = nullptr, *prv = nullptr;
+      const int last = seg * (nseg - 1);
+      for (int t = 1; t <= last; ++t) {
+        void* out = t == 1 ? P(0) : (t == 2 ? P(1) : prv);
+        forward_step(t, cur, prv, out);
+        prv = cur;
+        cur = out;
+        if (t % seg == 0) {
+          const int sg = t / seg;  // the segment starting at t0 = t + 1
+          TBK_CUDA(cudaMemcpyAsync(CK(sg, 0), prv, panel, cudaMemcpyDeviceToDevice, ctx->stream));
+          TBK_CUDA(cudaMemcpyAsync(CK(sg, 1), cur, panel, cudaMemcpyDeviceToDevice, ctx->stream));
+        }
       }
     }
-  }
-  // Backward sweep: b_{p-1} = c_{p-1} r, then for j = p-2 .. 0 add the y_j b_{j+1} term and
-  // form b_j = c_j r + 2 H^ b_{j+1} - b_{j+2}.
-  if (p >= 2) {
-    launch_scaled_probe(ctx, op, bcur, c[p - 1], probe_seed, s);
-    bool have_bprev = false;
-    int j = p - 2;
-    for (int sg = nseg - 1; sg >= -1 && j >= 0; --sg) {
-      const int t0 = sg >= 0 ? 1 + seg * sg : 0;
-      const int t1 = sg >= 0 ? std::min(npan, t0 + seg - 1) : 0;
-      if (sg >= 0) {
-        int t = t0;
-        if (sg > 0) {
-          TBK_CUDA(cudaMemcpyAsync(P(0), CK(sg, 1), panel, cudaMemcpyDeviceToDevice, ctx->stream));
-          forward_step(t0, P(0), CK(sg, 0), P(1));
-          ++t;
+    // Backward sweep: b_{p-1} = c_{p-1} r, then for j = p-2 .. 0 add the y_j b_{j+1} term and
+    // form b_j = c_j r + 2 H^ b_{j+1} - b_{j+2}.
+    if (p >= 2) {
+      launch_scaled_probe(ctx, op, bcur, c[p - 1], probe_seed, s);
+      bool have_bprev = false;
+      int j = p - 2;
+      for (int sg = nseg - 1; sg >= -1 && j >= 0; --sg) {
+        const int t0 = sg >= 0 ? 1 + seg * sg : 0;
+        const int t1 = sg >= 0 ? std::min(npan, t0 + seg - 1) : 0;
+        if (sg >= 0) {
+          int t = t0;
+          if (sg > 0) {
+            TBK_CUDA(cudaMemcpyAsync(P(0), CK(sg, 1), panel, cudaMemcpyDeviceToDevice, ctx->stream));
+            forward_step(t0, P(0), CK(sg, 0), P(1));
+            ++t;
+          }
+          for (; t <= t1; ++t) {
+            const int i = t - t0 + 1;
+            forward_step(t, t == 1 ? nullptr : P(i - 1), t >= 3 ? P(i - 2) : nullptr, P(i));
+          }
         }
-        for (; t <= t1; ++t) {
-          const int i = t - t0 + 1;
-          forward_step(t, t == 1 ? nullptr : P(i - 1), t >= 3 ? P(i - 2) : nullptr, P(i));
-        }
-      }
-      for (; j >= t0; --j) {
-        const void* yj = j == 0 ? nullptr : P(j - t0 + 1);
-        if (fused) {
-          // one launch: b_j (when j >= 1) and the y_j b_{j+1}^T term
-          launch_fused(ctx, op, bcur, have_bprev ? bprev : nullptr, j >= 1 ? bprev : nullptr, yj,
-                       j >= 1 ? c[j] : 0.0, probe_seed, s, j == 0 ? 1.0 : 2.0, Gacc, err, BatchRows(),
-                       nullptr);
+        for (; j >= t0; --j) {
+          const void* yj = j == 0 ? nullptr : P(j - t0 + 1);
+          launch_sddmm(ctx, op, yj, j == 0, probe_seed, bcur, s, j == 0 ? 1.0 : 2.0, Gacc);
           if (j >= 1) {
+            StepArgs a;
+            a.seed = probe_seed;
+            a.s = s;
+            a.yin = bcur;
+            a.alpha = 2.0;
+            a.c_r = c[j];
+            a.yprev = have_bprev ? bprev : nullptr;
+            a.yout = bprev;
+            a.err = err;
+            a.force_simple = plain;
+            launch_step(ctx, op, a);
             std::swap(bcur, bprev);
             have_bprev = true;
           }
-          continue;
-        }
-        launch_sddmm(ctx, op, yj, j == 0, probe_seed, bcur, s, j == 0 ? 1.0 : 2.0, Gacc);
-        if (j >= 1) {
-          StepArgs a;
-          a.seed = probe_seed;
-          a.s = s;
-          a.yin = bcur;
-          a.alpha = 2.0;
-          a.c_r = c[j];
-          a.yprev = have_bprev ? bprev : nullptr;
-          a.yout = bprev;
-          a.err = err;
-          a.force_simple = plain;
-          launch_step(ctx, op, a);
-          std::swap(bcur, bprev);
-          have_bprev = true;
         }
       }
     }
   }
-  // symmetrise and scale: G = (2/W)(1/s) sym(Gacc)
+  // symmetrise and scale: G = scale sym(Gacc)
   double* Gout = G ? G : Gsym;
   const int64_t tot = op.nnzb * BB;
-  const double scale = 2.0 / (W * s);
   if (op.B == 9)
     symmetrize<9><<<(unsigned)((tot + 255) / 256), 256, 0, ctx->stream>>>(op.nnzb, tr, Gacc, scale, Gout);
   else

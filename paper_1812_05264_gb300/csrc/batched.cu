@@ -405,8 +405,9 @@ void coefficients(tbk_ctx* ctx, int fn, int p, double emin, double emax, double 
                   int damping, double* out);
 bool fused_eligible(const HOp& op, int s, int plain);
 void launch_fused(tbk_ctx* ctx, const HOp& op, const void* bin, const void* bprev, void* bout,
-                  const void* ypan, double c_r, uint64_t seed, int s, double w, double* Gacc,
-                  int* err, const BatchRows& batch, const float* c_cl);
+                  const void* ypan, float4 cf, uint64_t seed, int s, double w, double* Gacc,
+                  int* err, const BatchRows& batch, const float4* cf_cl, const void* ym1,
+                  const void* yp1);
 void launch_transpose_map(tbk_ctx* ctx, int n_atoms, const int32_t* row_ptr, const int32_t* col,
                           int32_t* tr, int* err);
 void launch_symmetrize_batched(tbk_ctx* ctx, int n_atoms, const int32_t* row_ptr, const int32_t* tr,
@@ -415,13 +416,14 @@ void launch_symmetrize_batched(tbk_ctx* ctx, int n_atoms, const int32_t* row_ptr
 void launch_forces(tbk_ctx* ctx, const DevModel& M, const double* pos, int n_atoms, const int32_t* row_ptr,
                    const int32_t* col, const int32_t* tr, const double* G, double* tq, double* F);
 
-// c_tab[j * ncl + ci] = coef[ci * pmax + j] (as float) for j < p_ci, else 0.
+// c_tab[j * ncl + ci] = (coef[ci * pmax + j], 0, 0, 0) for j < p_ci, else 0: the Clenshaw
+// coefficient enters the backward step as the probe source term.
 __global__ void coef_table(const double* __restrict__ coef, int pmax, int ncl,
-                           const int32_t* __restrict__ p, float* __restrict__ c_tab) {
+                           const int32_t* __restrict__ p, float4* __restrict__ c_tab) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (int64_t)pmax * ncl) return;
   const int j = (int)(t / ncl), ci = (int)(t - (int64_t)j * ncl);
-  c_tab[t] = j < p[ci] ? (float)coef[(int64_t)ci * pmax + j] : 0.f;
+  c_tab[t] = make_float4(j < p[ci] ? (float)coef[(int64_t)ci * pmax + j] : 0.f, 0.f, 0.f, 0.f);
 }
 
 // b_{p-1} = c_{p-1} r into the buffer that is "current" when the cluster joins the backward
@@ -566,7 +568,7 @@ extern "C" int tbk_batched_density_and_forces(
     coefficients(ctx, TBK_FN_FREE, pc[ci], emin[c], emax[c], mu[c], kT[c], damping,
                  coefd + (size_t)ci * pmax);
   }
-  float* c_tab = (float*)scratch(ctx, WS_NODES, sizeof(float) * (size_t)pmax * ncl + 64);
+  float4* c_tab = (float4*)scratch(ctx, WS_NODES, sizeof(float4) * (size_t)pmax * ncl + 64);
   coef_table<<<ceil_div((int64_t)pmax * ncl, 256), 256, 0, ctx->stream>>>(coefd, pmax, ncl, d_p, c_tab);
   post_launch(ctx, "coef_table");
   // ---- panels and the checkpoint plan (as in the single-cluster adjoint) ----
@@ -658,7 +660,8 @@ extern "C" int tbk_batched_density_and_forces(
         o.n_atoms = active(j);
         if (o.n_atoms > 0)
           launch_fused(ctx, o, bcur, bprev, j >= 1 ? bprev : nullptr, j >= 1 ? Y(j - t0 + 1) : nullptr,
-                       0.0, 0, s, j == 0 ? 1.0 : 2.0, Gacc, err, br, c_tab + (size_t)j * ncl);
+                       make_float4(0.f, 0.f, 0.f, 0.f), 0, s, j == 0 ? 1.0 : 2.0, Gacc, err, br,
+                       c_tab + (size_t)j * ncl, nullptr, nullptr);
         if (j >= 1) std::swap(bcur, bprev);
       }
     }

@@ -550,9 +550,9 @@ int step_grid_ctas(tbk_ctx* ctx, const HOp& op, int s) {
   int per_sm = o.simple;
   const int cw = bulk_warps(op, s);
   if (cw && o.bulk[cw] > 0) per_sm = std::min(per_sm, o.bulk[cw]);
-  int G = std::max(1, per_sm * ctx->num_sms);
-  if (tc_eligible(op, s)) G = std::min(G, tc_grid(ctx));
-  return G;
+  // (the tensor-core step, when selected, runs on this same grid so that the per-CTA partial
+  // sums line up; its own occupancy does not shrink the grid of the default kernels)
+  return std::max(1, per_sm * ctx->num_sms);
 }
 
 template <typename T, int B>

@@ -326,3 +326,23 @@ def test_tensor_core_step_matches_fp32_kernels_and_oracle(api, ctx, s):
     mu, Om, E, N = api.fermi_level(ctx, m_tc, emin, emax, wk.n_electrons, wk.kT)
     assert abs(Om - est["Omega"]) / wk.n_atoms < 1e-4
     assert abs(E - est["E"]) / wk.n_atoms < 1e-4
+
+
+def test_doubled_adjoint_checkpoints_and_orders(api, ctx):
+    """The fused (doubled-moment) adjoint: segment replays equal storing every panel, and odd and
+    even orders match the oracle's estimator forces."""
+    wk = small_fcc(30, n_probes=128, kT=0.5)
+    rp, col, H = oracle_H(wk)
+    for p in (2, 3, 37, 90):
+        s_, pos, res = _gpu_run(api, ctx, wk, p, fp64=False)
+        est = oracle_estimator(wk, H, res.emin, res.emax, p)
+        args = (ctx, res.H, s_.model, pos, None, res.emin, res.emax, wk.probe_seed, 128, p,
+                est["mu"], wk.kT, False, False)
+        G1, F1 = api.density_and_forces(*args)
+        _, F = oracle_estimator_forces(wk, rp, col, est, res.emin, res.emax, p)
+        assert np.abs(F1.cpu().numpy() - F).max() < 1e-3, p
+        if p >= 37:
+            # below the p/2 + 4 panels of the all-stored plan, above the checkpoint plan's need
+            panel = wk.n_atoms * 9 * 128 * 4
+            G2, F2 = api.density_and_forces(*args, max_panel_bytes=(20 if p == 37 else 26) * panel)
+            assert torch.equal(G1, G2) and torch.equal(F1, F2), p

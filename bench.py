@@ -194,11 +194,11 @@ def run_reference(args, rank, world):
 # our arm
 # ---------------------------------------------------------------------------------------------
 
-def traffic_from_profile(kernel_file: str):
-    """Per-launch DRAM bytes of the recurrence kernel from the committed ncu summary, if it was
-    taken on the current kernel source (matching sha256 prefix); else None."""
+def traffic_from_profile(kernel_file: str, src_name: str):
+    """Per-launch DRAM bytes of a kernel from its committed ncu summary, if that summary was taken
+    on the current source of the file that holds the kernel (matching sha256 prefix); else None."""
     import hashlib
-    src = os.path.join(ROOT, "paper_1812_05264_gb300", "csrc", "recurrence.cu")
+    src = os.path.join(ROOT, "paper_1812_05264_gb300", "csrc", src_name)
     sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     path = os.path.join(ROOT, "profiles", kernel_file)
     if not os.path.exists(path):
@@ -208,12 +208,16 @@ def traffic_from_profile(kernel_file: str):
         if ":" in ln and ln.strip().startswith("- "):
             k, v = ln.strip()[2:].split(":", 1)
             vals[k.strip()] = v.strip()
-    if vals.get("recurrence.cu sha256[:16]") != sha:
+    if vals.get(f"{src_name} sha256[:16]") != sha:
         return None
     try:
         return float(vals["dram bytes per launch (full size)"])
     except (KeyError, ValueError):
         return None
+
+
+# FP32 FMA issue of one GB300: 152 SMs x 128 lanes x 2 flops per cycle at the maximum SM clock
+SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 
 
 def run_ours(args, rank, world):
@@ -242,26 +246,18 @@ def run_ours(args, rank, world):
     box = solver.box
     fp64 = not wk.mixed
     esz = 8 if fp64 else 4
-    mom_ev = []
+    fused = wk.mixed and wk.n_orb == 9 and wk.n_probes in (128, 256, 512)
 
-    def step(p_dev, record=False):
+    def step(p_dev):
         g = api.build_neighbors(ctx, p_dev, wk.cutoff, box)
         H = api.assemble_H(ctx, solver.model, p_dev, g, box)
         emin, emax = api.spectral_bounds(ctx, H)
         p = wk.order or order_rule(emax - emin, wk.kT)
-        if record:
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-        mom = api.chebyshev_moments(ctx, H, emin, emax, wk.probe_seed, wk.n_probes, p, fp64)
-        if record:
-            e1.record(stream)
-            mom_ev.append((e0, e1, p // 2, H.graph.nnzb))
-        mu, Om, E, N = api.fermi_level(ctx, mom, emin, emax, wk.n_electrons, wk.kT, wk.jackson)
-        G, F = api.density_and_forces(ctx, H, solver.model, p_dev, box, emin, emax, wk.probe_seed,
-                                      wk.n_probes, p, mu, wk.kT, wk.jackson, fp64,
-                                      want_G=not solver.model.is_sk, want_forces=solver.model.is_sk)
-        return p, (mu, Om, E, N), F
+        _, obs, _, F = api.energies_and_forces(
+            ctx, H, solver.model if solver.model.is_sk else None, p_dev, box, emin, emax,
+            wk.probe_seed, wk.n_probes, p, wk.n_electrons, wk.kT, wk.jackson, fp64,
+            want_G=not solver.model.is_sk, want_forces=solver.model.is_sk)
+        return p, obs, F, H.graph.nnzb
 
     if args.only_moments:
         return moments_only(args, ctx, solver, wk, pos)
@@ -270,9 +266,11 @@ def run_ours(args, rank, world):
     if args.compare_fp64:
         return precision_compare(args, ctx, solver, wk, pos)
     for _ in range(max(args.warmup, 0)):
-        p, _, _ = step(pos)
+        step(pos)
     torch.cuda.synchronize()
     barrier()
+    # the dominant kernel: the fused adjoint step where it runs, else the recurrence step
+    ctx.time_kernel("backward" if fused else "step")
     clocks = ClockSampler(local, enabled=not args.no_clocks)
     clocks.start()
     launches0 = ctx.launches
@@ -281,10 +279,12 @@ def run_ours(args, rank, world):
     torch.cuda.synchronize()
     t0.record(stream)
     for _ in range(args.steps):
-        p, obs, F = step(pos, record=True)
+        p, obs, F, nnzb = step(pos)
     t1.record(stream)
     torch.cuda.synchronize()
     launches = ctx.launches - launches0
+    k_ms, k_launches = ctx.kernel_time()
+    ctx.time_kernel(None)
     barrier()
     ms = t0.elapsed_time(t1) / args.steps
     # end to end: positions from pinned host memory in, energies and forces back to the host
@@ -296,7 +296,7 @@ def run_ours(args, rank, world):
         s1 = torch.cuda.Event(enable_timing=True)
         s0.record(stream)
         pos_e = pos_host.to(f"cuda:{local}", non_blocking=True)
-        p_e, obs_e, F_e = step(pos_e)
+        p_e, obs_e, F_e, _ = step(pos_e)
         out = F_e.cpu() if F_e is not None else None
         s1.record(stream)
         torch.cuda.synchronize()
@@ -311,19 +311,43 @@ def run_ours(args, rank, world):
         e_med = statistics.median(e_ms)
     units = wk.n_atoms * wk.n_probes * p
     value = units * world / (ms / 1e3)
-    # roofline of the recurrence kernel from the moments phase of the timed steps
-    mom_ms = sum(a.elapsed_time(b) for a, b, _, _ in mom_ev)
-    launches_k = sum(k for _, _, k, _ in mom_ev)
-    nnzb = mom_ev[-1][3]
+    # roofline of the dominant kernel from its own launches inside the timed steps
     n_rows = wk.n_atoms * wk.n_orb
-    bytes_per_launch = 3 * n_rows * wk.n_probes * esz + nnzb * wk.n_orb ** 2 * esz
-    achieved = bytes_per_launch * launches_k / (mom_ms / 1e3) / 1e9
+    panel = n_rows * wk.n_probes * esz
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         pass
-    peak = float(peaks.get("hbm_gbs", 6800.0))
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    avg_s = k_ms / max(k_launches, 1) / 1e3
+    B2 = wk.n_orb ** 2
+    if fused:
+        # reads ybar_{k+1}, ybar_{k+2}, y_k, y_{k-1}, y_{k+1}, writes ybar_k; H^ blocks; the FP64
+        # accumulator of G read and written once
+        bytes_pl = 6 * panel + nnzb * B2 * (esz + 16)
+        flops_pl = 4 * nnzb * B2 * wk.n_probes   # block product + outer product, 2 flops per FMA
+        alu = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+        t_mem, t_alu = bytes_pl / (hbm * 1e9), flops_pl / (alu * 1e12)
+        if t_alu >= t_mem:
+            roof = {"bound": "alu", "achieved": flops_pl / avg_s / 1e12, "peak": alu, "unit": "TFLOP/s",
+                    "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz (derived, FP32 FMA)"}
+        else:
+            roof = {"bound": "hbm", "achieved": bytes_pl / avg_s / 1e9, "peak": hbm, "unit": "GB/s",
+                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+        roof.update(kernel="clenshaw_sddmm_bulk", algorithmic_bytes_per_launch=bytes_pl,
+                    algorithmic_flops_per_launch=flops_pl,
+                    traffic=traffic_from_profile("clenshaw_sddmm_bulk_fcc10000.md", "adjoint.cu"))
+    else:
+        bytes_pl = 3 * panel + nnzb * B2 * esz
+        roof = {"bound": "hbm", "achieved": bytes_pl / avg_s / 1e9, "peak": hbm, "unit": "GB/s",
+                "kernel": "cheb_step_kernel", "algorithmic_bytes_per_launch": bytes_pl,
+                "traffic": traffic_from_profile("cheb_step_bulk_fcc10000.md", "recurrence.cu"),
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["avg_launch_ms"] = k_ms / max(k_launches, 1)
+    roof["launches_timed"] = k_launches
+    roof["share_of_step"] = k_ms / (ms * args.steps)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -336,10 +360,7 @@ def run_ours(args, rank, world):
         "e2e": {"value": units * world / (e_med / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": traffic_from_profile("cheb_step_bulk_fcc10000.md"),
-                     "kernel": "cheb_step_kernel", "algorithmic_bytes_per_launch": bytes_per_launch,
-                     "avg_launch_ms": mom_ms / launches_k, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"},
+        "roofline": roof,
         "clocks": clk,
         "observables_per_atom": {"mu": obs[0], "Omega": obs[1] / wk.n_atoms,
                                  "E": obs[2] / wk.n_atoms, "N": obs[3] / wk.n_atoms},

@@ -112,6 +112,18 @@ const char* tbk_last_error(void);
 /* Number of kernel launches this context has issued (for launch accounting). */
 int64_t tbk_launch_count(tbk_ctx* ctx);
 
+/* Kernel families that tbk_kernel_timer can bracket with CUDA events. */
+#define TBK_KERNEL_NONE 0
+#define TBK_KERNEL_STEP 1     /* one recurrence step y_{k+1} = 2 H^ y_k - y_{k-1} (Eq. cheb_rec) */
+#define TBK_KERNEL_BACKWARD 2 /* one fused adjoint step: ybar update and the G outer product */
+/* Select the kernel family whose launches on ctx's stream are from now on bracketed by a pair of
+   CUDA events (TBK_KERNEL_NONE switches timing off), and forget earlier pairs.  Launches captured
+   into CUDA graphs are not bracketed.  Host-side only; no GPU work. */
+int tbk_kernel_timer(tbk_ctx* ctx, int32_t kernel);
+/* Synchronise ctx's stream and return the summed device time (milliseconds) and the number of
+   bracketed launches since the last tbk_kernel_timer call.  total_ms, launches: host pointers. */
+int tbk_kernel_timer_read(tbk_ctx* ctx, double* total_ms, int64_t* launches);
+
 /* ---- a1: neighbour list (Sec. II.A mask M; Sec. II.E uniform-cube cell lists) ---------- */
 
 /* Pairs (i, j) with |r_j - r_i|^2 <= cutoff^2, self included, as CSR with ascending columns.
@@ -196,6 +208,19 @@ int tbk_density_and_forces(tbk_ctx* ctx, const tbk_bsr* H, const tbk_model* mode
                            uint64_t probe_seed, int32_t n_probes, int32_t order, double mu,
                            double kT, int32_t damping, int32_t flags, int64_t max_panel_bytes,
                            double* G, double* forces);
+
+/* tbk_energies_and_forces: tbk_chebyshev_moments + tbk_fermi_level + tbk_density_and_forces in
+   one call, for the same results.  In mixed precision with 9x9 blocks and n_probes 128, 256 or
+   512 the forward sweep of the adjoint produces the moments as it goes, so no separate moment
+   pass runs.  moments: device, order doubles, or NULL.  observables: host, 4 doubles {mu, Omega,
+   E, N}.  G, forces as in tbk_density_and_forces (either may be NULL).  flags: TBK_MIXED or
+   TBK_FP64, optionally | TBK_PLAIN_KERNEL.  Synchronises the stream. */
+int tbk_energies_and_forces(tbk_ctx* ctx, const tbk_bsr* H, const tbk_model* model,
+                            const double* pos, const double* box, double emin, double emax,
+                            uint64_t probe_seed, int32_t n_probes, int32_t order,
+                            double n_electrons, double kT, int32_t damping, int32_t flags,
+                            int64_t max_panel_bytes, double* moments, double* observables,
+                            double* G, double* forces);
 
 /* ---- a11: batches of clusters ------------------------------------------------------------
 

@@ -31,6 +31,9 @@ TBK_FN_ENERGY = 1
 TBK_FN_FREE = 2
 TBK_MODEL_SK = 1
 TBK_MODEL_TABLE = 2
+TBK_KERNEL_NONE = 0
+TBK_KERNEL_STEP = 1
+TBK_KERNEL_BACKWARD = 2
 
 _NAMES = {TBK_ERR_ARG: "TBK_ERR_ARG", TBK_ERR_CUDA: "TBK_ERR_CUDA", TBK_ERR_OOM: "TBK_ERR_OOM",
           TBK_ERR_SPECTRUM: "TBK_ERR_SPECTRUM", TBK_ERR_NOCONV: "TBK_ERR_NOCONV",
@@ -65,12 +68,16 @@ _U = C.c_uint64
 SIGNATURES = {
     "tbk_create": [C.POINTER(_P), C.c_int, _P],
     "tbk_destroy": [_P],
+    "tbk_kernel_timer": [_P, _I],
+    "tbk_kernel_timer_read": [_P, C.POINTER(_D), C.POINTER(_L)],
     "tbk_build_neighbors": [_P, _P, _I, _P, _D, _P, _P, _L, C.POINTER(_L)],
     "tbk_assemble_H": [_P, C.POINTER(tbk_model), _P, _I, _P, _P, _P, _L, _P],
     "tbk_spectral_bounds": [_P, C.POINTER(tbk_bsr), _I, _D, _U, C.POINTER(_D), C.POINTER(_D)],
     "tbk_chebyshev_coefficients": [_P, _I, _I, _D, _D, _D, _D, _I, _P],
     "tbk_chebyshev_moments": [_P, C.POINTER(tbk_bsr), _D, _D, _U, _I, _I, _I, _P],
     "tbk_chebyshev_moments_noalloc": [_P, C.POINTER(tbk_bsr), _D, _D, _U, _I, _I, _I, _P],
+    "tbk_energies_and_forces": [_P, C.POINTER(tbk_bsr), C.POINTER(tbk_model), _P, _P, _D, _D, _U,
+                                _I, _I, _D, _D, _I, _I, _L, _P, C.POINTER(_D), _P, _P],
     "tbk_batched_moments": [_P, _I, C.POINTER(tbk_bsr), C.POINTER(_D), C.POINTER(_D), C.POINTER(_U),
                             _I, C.POINTER(_I), _I, _P],
     "tbk_batched_fermi_level": [_P, _I, _P, C.POINTER(_I), C.POINTER(_D), C.POINTER(_D),

@@ -40,6 +40,19 @@ class Context:
     def launches(self) -> int:
         return int(L.load().tbk_launch_count(self._h))
 
+    def time_kernel(self, kernel: str | None):
+        """Bracket every launch of one kernel family ("step", "backward", or None for off) with
+        CUDA events on this context's stream; read the sum with kernel_time()."""
+        k = {None: L.TBK_KERNEL_NONE, "step": L.TBK_KERNEL_STEP,
+             "backward": L.TBK_KERNEL_BACKWARD}[kernel]
+        L.call("tbk_kernel_timer", self._h, k)
+
+    def kernel_time(self) -> tuple[float, int]:
+        """(total milliseconds, launches) of the timed family since time_kernel()."""
+        ms, n = C.c_double(), C.c_int64()
+        L.call("tbk_kernel_timer_read", self._h, C.byref(ms), C.byref(n))
+        return ms.value, n.value
+
     def close(self):
         if self._h:
             L.load().tbk_destroy(self._h)
@@ -255,6 +268,25 @@ def batched_density_and_forces(ctx: Context, Hs: list, model: Model, positions: 
     return Gs, Fs
 
 
+def energies_and_forces(ctx: Context, H: BSR, model: Model | None, pos: torch.Tensor | None, box,
+                        emin: float, emax: float, seed: int, n_probes: int, order: int,
+                        n_electrons: float, kT: float, jackson: bool = False, fp64: bool = False,
+                        want_G: bool = False, want_forces: bool = True, max_panel_bytes: int = 0):
+    """a5-a10 in one call: (moments, (mu, Omega, E, N), G or None, forces or None)."""
+    dev = H.val.device
+    mom = torch.empty(order, dtype=torch.float64, device=dev)
+    G = torch.empty_like(H.val) if want_G else None
+    F = torch.empty((H.graph.n_atoms, 3), dtype=torch.float64, device=dev) if want_forces else None
+    obs = (C.c_double * 4)()
+    _keep, bx = _box_arg(box)
+    L.call("tbk_energies_and_forces", ctx.handle, C.byref(H.struct()),
+           C.byref(model.s) if model is not None else None, _ptr(pos), bx, emin, emax,
+           C.c_uint64(seed), int(n_probes), int(order), float(n_electrons), float(kT),
+           L.TBK_DAMP_JACKSON if jackson else L.TBK_DAMP_NONE, L.TBK_FP64 if fp64 else L.TBK_MIXED,
+           int(max_panel_bytes), _ptr(mom), obs, _ptr(G), _ptr(F))
+    return mom, tuple(obs[:]), G, F
+
+
 def order_for(W: float, kT: float, eps: float = 1e-7, p_min: int = 64) -> int:
     """Chebyshev terms from the paper's error model eps_poly ~ exp(-6.4 p kT / W) (Sec. II.B.1)."""
     return max(p_min, int(math.ceil((W / kT) * math.log(1.0 / eps) / 6.4)))
@@ -321,6 +353,24 @@ class Solver:
                                   want_forces=self.model.is_sk, max_panel_bytes=max_panel_bytes)
         res.G, res.forces = G, F
         return res
+
+    def energies_and_forces(self, pos: torch.Tensor, order: int | None = None,
+                            fp64: bool | None = None, bounds=None, want_G: bool = False,
+                            max_panel_bytes: int = 0) -> Result:
+        """energies() then forces() in one library call (one forward sweep instead of two)."""
+        wk = self.wk
+        fp64 = (not wk.mixed) if fp64 is None else fp64
+        self.graph = build_neighbors(self.ctx, pos, wk.cutoff, self.box)
+        H = assemble_H(self.ctx, self.model, pos, self.graph, self.box)
+        emin, emax = bounds if bounds is not None else spectral_bounds(
+            self.ctx, H, self.lanczos_steps, self.margin, self.bounds_seed)
+        p = order or wk.order or order_for(emax - emin, wk.kT)
+        is_sk = self.model.is_sk
+        mom, (mu, Om, E, N), G, F = energies_and_forces(
+            self.ctx, H, self.model if is_sk else None, pos if is_sk else None, self.box, emin,
+            emax, wk.probe_seed, wk.n_probes, p, wk.n_electrons, wk.kT, wk.jackson, fp64,
+            want_G=want_G or not is_sk, want_forces=is_sk, max_panel_bytes=max_panel_bytes)
+        return Result(emin, emax, p, mu, Om, E, N, mom, H, G, F)
 
 
 class FreeEnergy(torch.autograd.Function):

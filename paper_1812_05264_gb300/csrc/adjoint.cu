@@ -11,6 +11,7 @@
 // is recomputed into a panel buffer just before its backward steps.
 #include <algorithm>
 #include <cmath>
+#include <functional>
 #include <vector>
 
 #include "bulk.cuh"
@@ -461,6 +462,7 @@ void launch_fused(tbk_ctx* ctx, const HOp& op, const void* bin, const void* bpre
                   const void* ypan, float4 cf, uint64_t seed, int s, double w, double* Gacc,
                   int* err, const BatchRows& batch, const float4* cf_cl, const void* ym1,
                   const void* yp1) {
+  KernelTimerScope timer(ctx, TBK_KERNEL_BACKWARD);
   if (s == 512)
     launch_fused_cw<4>(ctx, op, bin, bprev, bout, ypan, cf, seed, s, w, Gacc, err, batch, cf_cl, ym1, yp1);
   else if (s == 256)
@@ -549,19 +551,29 @@ __global__ void ybar_init(int64_t n, int s, float ca, const float* __restrict__ 
   out[i] = fmaf(ca, yk[i], cb * prev);
 }
 
-void adjoint_doubling(tbk_ctx* ctx, const HOp& op, uint64_t probe_seed, int s, const std::vector<double>& c,
+// get_coefs() is called once every y_1 .. y_K has been formed for the first time (with
+// `partials` != NULL those steps also wrote their moment partial sums at partials + 2 nctas (t-1),
+// so the caller can finish the moments, solve for mu and return the coefficients c_0 .. c_{p-1}).
+void adjoint_doubling(tbk_ctx* ctx, const HOp& op, uint64_t probe_seed, int s, int p,
+                      const std::function<std::vector<double>()>& get_coefs, double* partials, int nctas,
                       int64_t max_panel_bytes, double* Gacc, int* err) {
-  const int p = (int)c.size();
   const int K = p / 2;
-  if (K < 1) return;  // p = 1: the estimate does not depend on H
-  // source-term coefficients
-  std::vector<double> w(K + 2, 0.0), v(K + 2, 0.0);
-  for (int k = 1; k <= K; ++k) {
-    if (2 * k < p) w[k] = 2.0 * c[2 * k];
-    if (k >= 2 && 2 * k - 1 < p) v[k] = 2.0 * c[2 * k - 1];
+  if (K < 1) {
+    get_coefs();
+    return;  // p = 1: the estimate does not depend on H
   }
-  v[1] = p > 1 ? c[1] : 0.0;
-  for (int k = 2; 2 * k - 1 < p; ++k) v[1] -= c[2 * k - 1];
+  std::vector<double> w(K + 2, 0.0), v(K + 2, 0.0);
+  bool have_coefs = false;
+  auto load_coefs = [&]() {
+    const std::vector<double> c = get_coefs();
+    for (int k = 1; k <= K; ++k) {
+      if (2 * k < p) w[k] = 2.0 * c[2 * k];
+      if (k >= 2 && 2 * k - 1 < p) v[k] = 2.0 * c[2 * k - 1];
+    }
+    v[1] = p > 1 ? c[1] : 0.0;
+    for (int k = 2; 2 * k - 1 < p; ++k) v[1] -= c[2 * k - 1];
+    have_coefs = true;
+  };
   auto ca = [&](int k) { return (float)(2.0 * w[k] / s); };
   auto cb = [&](int k) { return (float)(v[k] / s); };
   auto cc = [&](int k) { return (float)(v[k + 1] / s); };
@@ -593,7 +605,7 @@ void adjoint_doubling(tbk_ctx* ctx, const HOp& op, uint64_t probe_seed, int s, c
   void* E = P(n_seg_pan + n_ckpt);
   void* bcur = P(n_seg_pan + n_ckpt + 1);
   void* bprev = P(n_seg_pan + n_ckpt + 2);
-  auto forward_step = [&](int t, const void* yin, const void* yprev, void* yout) {
+  auto forward_step = [&](int t, const void* yin, const void* yprev, void* yout, bool first_time) {
     StepArgs a;
     a.seed = probe_seed;
     a.s = s;
@@ -604,6 +616,7 @@ void adjoint_doubling(tbk_ctx* ctx, const HOp& op, uint64_t probe_seed, int s, c
     else if (t >= 3) a.yprev = const_cast<void*>(yprev);
     a.yout = yout;
     a.err = err;
+    if (partials && first_time) a.partials = partials + (size_t)(t - 1) * nctas * 2;
     launch_step(ctx, op, a);
   };
   if (!all_stored) {
@@ -611,7 +624,7 @@ void adjoint_doubling(tbk_ctx* ctx, const HOp& op, uint64_t probe_seed, int s, c
     const int last = seg * (nseg - 1);
     for (int t = 1; t <= last; ++t) {
       void* out = t == 1 ? P(0) : (t == 2 ? P(1) : prv);
-      forward_step(t, cur, prv, out);
+      forward_step(t, cur, prv, out, true);
       prv = cur;
       cur = out;
       if (t % seg == 0) {
@@ -631,17 +644,19 @@ void adjoint_doubling(tbk_ctx* ctx, const HOp& op, uint64_t probe_seed, int s, c
         // y_{t1+1} is the first panel of the segment just finished
         TBK_CUDA(cudaMemcpyAsync(E, P(1), panel, cudaMemcpyDeviceToDevice, ctx->stream));
       }
+      const bool first_time = sg == nseg - 1;  // the last segment was never formed before
       int t = t0;
       if (sg > 0) {
         TBK_CUDA(cudaMemcpyAsync(P(0), CK(sg, 1), panel, cudaMemcpyDeviceToDevice, ctx->stream));
-        forward_step(t0, P(0), CK(sg, 0), P(1));
+        forward_step(t0, P(0), CK(sg, 0), P(1), first_time);
         ++t;
       }
       for (; t <= t1; ++t) {
         const int i = t - t0 + 1;
-        forward_step(t, t == 1 ? nullptr : P(i - 1), t >= 3 ? P(i - 2) : nullptr, P(i));
+        forward_step(t, t == 1 ? nullptr : P(i - 1), t >= 3 ? P(i - 2) : nullptr, P(i), first_time);
       }
     }
+    if (!have_coefs) load_coefs();
     // y_j for j in [t0 - 1, t1 + 1] (nullptr = the probe block r = y_0)
     auto Y = [&](int j) -> const void* {
       if (j == 0) return nullptr;
@@ -725,7 +740,7 @@ extern "C" int tbk_density_and_forces(tbk_ctx* ctx, const tbk_bsr* H, const tbk_
   const size_t panel = (size_t)op.n_rows * s * esz;
   double scale = 2.0 / (W * s);
   if (fused) {
-    adjoint_doubling(ctx, op, probe_seed, s, c, max_panel_bytes, Gacc, err);
+    adjoint_doubling(ctx, op, probe_seed, s, p, [&]() { return c; }, nullptr, 0, max_panel_bytes, Gacc, err);
     scale = 2.0 / W;  // the 1/s of the moments is inside the source terms
   } else {
     // Panels y_1 .. y_{p-2} are needed in reverse order: all of them are kept when they fit the
@@ -848,6 +863,117 @@ extern "C" int tbk_density_and_forces(tbk_ctx* ctx, const tbk_bsr* H, const tbk_
     gather_forces<<<ceil_div(op.n_atoms, 128), 128, 0, ctx->stream>>>(op.n_atoms, op.row_ptr, op.col,
                                                                       tr, tq, forces);
     post_launch(ctx, "gather_forces");
+  }
+  int herr = 0;
+  TBK_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  sync(ctx);
+  if (herr & 2) throw Error(TBK_ERR_TIMEOUT, "a bounded wait in the recurrence kernel expired");
+  TBK_CHECK_ARG(herr == 0, "the block pattern is not symmetric");
+  TBK_API_END
+}
+
+namespace tbk {
+void fermi_enqueue(tbk_ctx* ctx, const double* moments, int order, double emin, double emax,
+                   double n_electrons, double mu_fixed, double kT, int damping, double* tab,
+                   double* rho, double* res);
+int quad_nodes(int p);
+}  // namespace tbk
+
+// Energies and forces in one call: the adjoint's forward sweep over y_1 .. y_{p/2} also yields
+// the (doubled) moments, so no separate moment pass is run.
+extern "C" int tbk_energies_and_forces(tbk_ctx* ctx, const tbk_bsr* H, const tbk_model* model,
+                                       const double* pos, const double* box, double emin,
+                                       double emax, uint64_t probe_seed, int32_t n_probes,
+                                       int32_t order, double n_electrons, double kT,
+                                       int32_t damping, int32_t flags, int64_t max_panel_bytes,
+                                       double* moments, double* observables, double* G,
+                                       double* forces) {
+  TBK_API_BEGIN
+  TBK_CHECK_ARG(ctx != nullptr && observables != nullptr, "NULL argument");
+  TBK_CHECK_ARG(order >= 1, "order must be >= 1");
+  TBK_CHECK_ARG(n_probes >= 4 && n_probes % 4 == 0, "n_probes must be a positive multiple of 4");
+  TBK_CHECK_ARG((flags & ~(TBK_FP64 | TBK_PLAIN_KERNEL)) == 0, "unknown flag");
+  TBK_CHECK_ARG(kT > 0.0 && n_electrons >= 0.0, "kT must be positive and n_electrons >= 0");
+  DeviceGuard dg(ctx);
+  const int prec = (flags & TBK_FP64) ? TBK_FP64 : TBK_MIXED;
+  const int plain = (flags & TBK_PLAIN_KERNEL) ? 1 : 0;
+  HOp shape;
+  shape.B = H ? H->n_orb : 0;
+  shape.prec = prec;
+  if (!H || !fused_eligible(shape, n_probes, plain)) {
+    // the separate calls give the same results for the other shapes and precisions
+    double* mom = moments ? moments : (double*)scratch(ctx, WS_SEGMENT, sizeof(double) * (size_t)order);
+    int rc = tbk_chebyshev_moments(ctx, H, emin, emax, probe_seed, n_probes, order, flags, mom);
+    if (rc != TBK_OK) throw Error(rc, tbk_last_error());
+    rc = tbk_fermi_level(ctx, mom, order, emin, emax, n_electrons, 0.0, kT, damping, observables);
+    if (rc != TBK_OK) throw Error(rc, tbk_last_error());
+    if (G || forces) {
+      rc = tbk_density_and_forces(ctx, H, model, pos, box, emin, emax, probe_seed, n_probes, order,
+                                  observables[0], kT, damping, flags, max_panel_bytes, G, forces);
+      if (rc != TBK_OK) throw Error(rc, tbk_last_error());
+    }
+    return TBK_OK;
+  }
+  DevModel M{};
+  if (forces) {
+    M = upload_model(ctx, model, box, WS_TABLE);
+    TBK_CHECK_ARG(M.kind == TBK_MODEL_SK, "forces need the Slater-Koster model");
+    TBK_CHECK_ARG(pos != nullptr, "pos is NULL");
+  }
+  HOp op = prepare_hop(ctx, H, emin, emax, prec, WS_HHAT);
+  const int p = order, s = n_probes, BB = op.B * op.B;
+  const double W = emax - emin;
+  int32_t* tr = (int32_t*)scratch(ctx, WS_TRANSPOSE, sizeof(int32_t) * (size_t)op.nnzb);
+  // err: bit 2 = a bounded wait expired, bit 1 = the pattern is not symmetric; err[1] bit 1 = a
+  // panel outgrew ||r|| (the spectrum is not inside [emin, emax])
+  int* err = (int*)scratch(ctx, WS_FLAGS, 64);
+  TBK_CUDA(cudaMemsetAsync(err, 0, 2 * sizeof(int), ctx->stream));
+  launch_transpose_map(ctx, op.n_atoms, op.row_ptr, op.col, tr, err);
+  double* Gacc = (double*)scratch(ctx, WS_GACC, sizeof(double) * (size_t)op.nnzb * BB * 2);
+  double* Gsym = Gacc + (size_t)op.nnzb * BB;
+  TBK_CUDA(cudaMemsetAsync(Gacc, 0, sizeof(double) * (size_t)op.nnzb * BB, ctx->stream));
+  const int K = p / 2;
+  const int nctas = step_grid_ctas(ctx, op, s);
+  double* partials = (double*)scratch(ctx, WS_PARTIALS, sizeof(double) * 2 * (size_t)std::max(1, K) * nctas);
+  const int M_nodes = quad_nodes(p);
+  double* fbuf = (double*)scratch(ctx, WS_SEGMENT, sizeof(double) * ((size_t)2 * K + 64 + 5 * (size_t)M_nodes + 16 +
+                                                                     (size_t)p + 8));
+  double* sums = fbuf;
+  double* tab = sums + 2 * (size_t)K + 64;
+  double* rho = tab + 4 * (size_t)M_nodes;
+  double* res = rho + M_nodes;
+  double* mom = moments ? moments : res + 16;
+  double* dcoef = (double*)scratch(ctx, WS_COEF, sizeof(double) * (size_t)p);
+  auto after_forward = [&]() {
+    // moments from the doubling identities, then mu, Omega, E, N, then c_k = d_k beta_k[g](mu)
+    launch_moment_reduction(ctx, partials, nctas, K, p, s, op.n_rows, 0, sums, mom, err + 1);
+    fermi_enqueue(ctx, mom, p, emin, emax, n_electrons, 0.0, kT, damping, tab, rho, res);
+    double h[5];
+    int herr[2] = {0, 0};
+    TBK_CUDA(cudaMemcpyAsync(h, res, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
+    TBK_CUDA(cudaMemcpyAsync(herr, err, sizeof(herr), cudaMemcpyDeviceToHost, ctx->stream));
+    sync(ctx);
+    if ((herr[0] | herr[1]) & 2) throw Error(TBK_ERR_TIMEOUT, "a bounded wait in the recurrence kernel expired");
+    TBK_CHECK_ARG(herr[0] == 0, "the block pattern is not symmetric");
+    if (herr[1])
+      throw Error(TBK_ERR_SPECTRUM, "a Chebyshev panel grew beyond ||r||: the spectrum of H is not "
+                                    "inside [emin, emax]");
+    if (h[4] != 0.0) throw Error(TBK_ERR_NOCONV, "n_electrons is outside the range of the estimated N(mu)");
+    for (int i = 0; i < 4; ++i) observables[i] = h[i];
+    coefficients(ctx, TBK_FN_FREE, p, emin, emax, h[0], kT, damping, dcoef);
+    std::vector<double> c(p);
+    TBK_CUDA(cudaMemcpyAsync(c.data(), dcoef, sizeof(double) * p, cudaMemcpyDeviceToHost, ctx->stream));
+    sync(ctx);
+    return c;
+  };
+  adjoint_doubling(ctx, op, probe_seed, s, p, after_forward, partials, nctas, max_panel_bytes, Gacc, err);
+  double* Gout = G ? G : Gsym;
+  const int64_t tot = op.nnzb * BB;
+  symmetrize<9><<<(unsigned)((tot + 255) / 256), 256, 0, ctx->stream>>>(op.nnzb, tr, Gacc, 2.0 / W, Gout);
+  post_launch(ctx, "symmetrize");
+  if (forces) {
+    double* tq = (double*)scratch(ctx, WS_MISC, sizeof(double) * 3 * (size_t)op.nnzb);
+    launch_forces(ctx, M, pos, op.n_atoms, op.row_ptr, op.col, tr, Gout, tq, forces);
   }
   int herr = 0;
   TBK_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));

@@ -52,6 +52,9 @@ struct tbk_ctx {
   size_t slot_bytes[tbk::WS_NSLOTS] = {};
   void* pinned = nullptr;        // small pinned host buffer for scalar read-back
   size_t pinned_bytes = 0;
+  int timed_kernel = 0;          // TBK_KERNEL_* whose launches are bracketed by events
+  std::vector<cudaEvent_t> timer_events;
+  size_t timer_used = 0;
 };
 
 namespace tbk {
@@ -69,6 +72,13 @@ struct DeviceGuard {
   ~DeviceGuard();
 };
 void sync(tbk_ctx* ctx);
+// Brackets the launches of one kernel family with events on ctx->stream when that family is the
+// one selected by tbk_kernel_timer (and the stream is not being captured into a graph).
+struct KernelTimerScope {
+  tbk_ctx* ctx = nullptr;
+  KernelTimerScope(tbk_ctx* c, int kernel);
+  ~KernelTimerScope();
+};
 
 inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 

@@ -57,6 +57,35 @@ DeviceGuard::~DeviceGuard() {
 
 void sync(tbk_ctx* ctx) { TBK_CUDA(cudaStreamSynchronize(ctx->stream)); }
 
+static void timer_record(tbk_ctx* ctx) {
+  if (ctx->timer_used == ctx->timer_events.size()) {
+    cudaEvent_t e;
+    TBK_CUDA(cudaEventCreate(&e));
+    ctx->timer_events.push_back(e);
+  }
+  TBK_CUDA(cudaEventRecord(ctx->timer_events[ctx->timer_used], ctx->stream));
+  ctx->timer_used++;
+}
+
+KernelTimerScope::KernelTimerScope(tbk_ctx* c, int kernel) {
+  if (c->timed_kernel == 0 || c->timed_kernel != kernel) return;
+  cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+  TBK_CUDA(cudaStreamIsCapturing(c->stream, &st));
+  if (st != cudaStreamCaptureStatusNone) return;
+  timer_record(c);
+  ctx = c;
+}
+
+KernelTimerScope::~KernelTimerScope() {
+  if (!ctx) return;
+  // the end event of the pair; on failure the begin event is dropped so pairs stay aligned
+  try {
+    timer_record(ctx);
+  } catch (...) {
+    ctx->timer_used--;
+  }
+}
+
 }  // namespace tbk
 
 extern "C" {
@@ -88,12 +117,39 @@ int tbk_destroy(tbk_ctx* ctx) {
     for (int s = 0; s < tbk::WS_NSLOTS; ++s)
       if (ctx->slot_ptr[s]) cudaFree(ctx->slot_ptr[s]);
     if (ctx->pinned) cudaFreeHost(ctx->pinned);
+    for (cudaEvent_t e : ctx->timer_events) cudaEventDestroy(e);
   }
   delete ctx;
   TBK_API_END
 }
 
 const char* tbk_last_error(void) { return tbk::g_last_error.c_str(); }
+
+int tbk_kernel_timer(tbk_ctx* ctx, int32_t kernel) {
+  TBK_API_BEGIN
+  TBK_CHECK_ARG(ctx != nullptr, "ctx is NULL");
+  TBK_CHECK_ARG(kernel == TBK_KERNEL_NONE || kernel == TBK_KERNEL_STEP || kernel == TBK_KERNEL_BACKWARD,
+                "unknown kernel family");
+  ctx->timed_kernel = kernel;
+  ctx->timer_used = 0;
+  TBK_API_END
+}
+
+int tbk_kernel_timer_read(tbk_ctx* ctx, double* total_ms, int64_t* launches) {
+  TBK_API_BEGIN
+  TBK_CHECK_ARG(ctx && total_ms && launches, "NULL argument");
+  tbk::DeviceGuard g(ctx);
+  tbk::sync(ctx);
+  double t = 0.0;
+  for (size_t i = 0; i + 1 < ctx->timer_used; i += 2) {
+    float ms = 0.f;
+    TBK_CUDA(cudaEventElapsedTime(&ms, ctx->timer_events[i], ctx->timer_events[i + 1]));
+    t += ms;
+  }
+  *total_ms = t;
+  *launches = (int64_t)(ctx->timer_used / 2);
+  TBK_API_END
+}
 
 int64_t tbk_launch_count(tbk_ctx* ctx) { return ctx ? ctx->launches : -1; }
 

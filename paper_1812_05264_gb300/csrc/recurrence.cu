@@ -581,6 +581,7 @@ static void launch_bulk(tbk_ctx* ctx, const HOp& op, const StepArgs& a, int G) {
 }
 
 void launch_step(tbk_ctx* ctx, const HOp& op, const StepArgs& a) {
+  KernelTimerScope timer(ctx, TBK_KERNEL_STEP);
   const int G = step_grid_ctas(ctx, op, a.s);
   if (a.use_tc && !a.cur_is_probe && a.err && !a.force_simple && !a.batch.atom_cl && !a.per_task &&
       tc_eligible(op, a.s)) {

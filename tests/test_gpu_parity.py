@@ -346,3 +346,56 @@ def test_doubled_adjoint_checkpoints_and_orders(api, ctx):
             panel = wk.n_atoms * 9 * 128 * 4
             G2, F2 = api.density_and_forces(*args, max_panel_bytes=(20 if p == 37 else 26) * panel)
             assert torch.equal(G1, G2) and torch.equal(F1, F2), p
+
+
+# ---- energies and forces in one call ---------------------------------------------------------
+
+@pytest.mark.parametrize("s,p,fp64,budget", [(128, 90, False, 0), (256, 37, False, 20), (128, 61, True, 0),
+                                             (16, 40, False, 0)])
+def test_energies_and_forces_one_call_equals_separate_calls(api, ctx, s, p, fp64, budget):
+    """The combined entry point takes its moments from the adjoint's own forward sweep (or, for the
+    shapes the fused kernels do not take, runs the separate calls): every output is bit-identical
+    to moments + Fermi level + density and forces, and matches the oracle."""
+    wk = small_fcc(40, n_probes=s, kT=0.5)
+    rp, col, H = oracle_H(wk)
+    sv, pos, res = _gpu_run(api, ctx, wk, p, fp64=fp64)
+    mpb = budget * wk.n_atoms * 9 * s * 4
+    sv.forces(pos, res, fp64=fp64, want_G=True, max_panel_bytes=mpb)
+    r2 = sv.energies_and_forces(pos, order=p, fp64=fp64, bounds=(res.emin, res.emax), want_G=True,
+                                max_panel_bytes=mpb)
+    assert torch.equal(res.moments, r2.moments)
+    assert (res.mu, res.Omega, res.E, res.N) == (r2.mu, r2.Omega, r2.E, r2.N)
+    assert torch.equal(res.G, r2.G) and torch.equal(res.forces, r2.forces)
+    est = oracle_estimator(wk, H, res.emin, res.emax, p)
+    tol = 1e-6 if fp64 else 1e-4
+    assert abs(r2.Omega - est["Omega"]) / wk.n_atoms < tol
+    _, F = oracle_estimator_forces(wk, rp, col, est, res.emin, res.emax, p)
+    assert np.abs(r2.forces.cpu().numpy() - F).max() < (1e-6 if fp64 else 1e-3)
+
+
+def test_energies_and_forces_rejects_bad_arguments(api, ctx):
+    from paper_1812_05264_gb300._lib import TbkError
+    wk = small_fcc(20, n_probes=128)
+    sv, pos, res = _gpu_run(api, ctx, wk, 20, fp64=False)
+    with pytest.raises(TbkError):
+        api.energies_and_forces(ctx, res.H, sv.model, pos, None, res.emin, res.emax, 1, 128, 20,
+                                wk.n_electrons, -1.0)
+    with pytest.raises(TbkError):  # no Fermi level inside the bounds
+        api.energies_and_forces(ctx, res.H, sv.model, pos, None, res.emin, res.emax, 1, 128, 20,
+                                1e9, wk.kT)
+
+
+def test_kernel_timer_counts_the_recurrence_launches(api, ctx):
+    wk = small_fcc(40, n_probes=128)
+    sv, pos, res = _gpu_run(api, ctx, wk, 30, fp64=False)
+    ctx.time_kernel("step")
+    api.chebyshev_moments(ctx, res.H, res.emin, res.emax, wk.probe_seed, 128, 30, False)
+    ms, n = ctx.kernel_time()
+    ctx.time_kernel(None)
+    assert n == 15 and ms > 0.0
+    ctx.time_kernel("backward")
+    api.density_and_forces(ctx, res.H, sv.model, pos, None, res.emin, res.emax, wk.probe_seed, 128,
+                           30, res.mu, wk.kT, False, False)
+    ms, n = ctx.kernel_time()
+    ctx.time_kernel(None)
+    assert n == 15 and ms > 0.0

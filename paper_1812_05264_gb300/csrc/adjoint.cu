@@ -579,12 +579,7 @@ void adjoint_doubling(tbk_ctx* ctx, const HOp& op, uint64_t probe_seed, int s, i
   auto cc = [&](int k) { return (float)(v[k + 1] / s); };
 
   const size_t panel = (size_t)op.n_rows * s * 4;
-  size_t budget = (size_t)std::max<int64_t>(0, max_panel_bytes);
-  if (budget == 0) {
-    size_t fr = 0, tot = 0;
-    TBK_CUDA(cudaMemGetInfo(&fr, &tot));
-    budget = (size_t)(0.6 * (double)fr);
-  }
+  size_t budget = max_panel_bytes > 0 ? (size_t)max_panel_bytes : panel_budget(ctx, WS_CHECKPOINTS);
   const int npan = K;  // y_1 .. y_K
   int seg = std::max(1, npan);
   if ((size_t)(npan + 4) * panel > budget && npan > 2) {
@@ -594,12 +589,21 @@ void adjoint_doubling(tbk_ctx* ctx, const HOp& op, uint64_t probe_seed, int s, i
       throw Error(TBK_ERR_OOM, "panel scratch budget of " + std::to_string(budget) +
                                    " bytes is below the checkpoint plan's " + std::to_string(need));
   }
-  const int nseg = (npan + seg - 1) / seg;
-  const bool all_stored = nseg <= 1;
+  int nseg = (npan + seg - 1) / seg;
   // P(0 .. seg): segment panels (P(i) = y_{t0 - 1 + i}); checkpoints (y_{t0-2}, y_{t0-1}); E = y_{t1+1};
   // two ybar panels
+  char* base = nullptr;
+  try {
+    base = (char*)scratch(ctx, WS_CHECKPOINTS, panel * ((size_t)seg + 1 + (nseg <= 1 ? 0 : 2 * (size_t)nseg) + 3));
+  } catch (const Error& e) {
+    // the device could not map the all-stored plan after all: replay segments instead
+    if (e.code != TBK_ERR_OOM || nseg > 1 || npan <= 2) throw;
+    seg = std::max(2, (int)std::ceil(std::sqrt(2.0 * npan)));
+    nseg = (npan + seg - 1) / seg;
+    base = (char*)scratch(ctx, WS_CHECKPOINTS, panel * ((size_t)seg + 1 + 2 * (size_t)nseg + 3));
+  }
+  const bool all_stored = nseg <= 1;
   const size_t n_seg_pan = (size_t)seg + 1, n_ckpt = all_stored ? 0 : 2 * (size_t)nseg;
-  char* base = (char*)scratch(ctx, WS_CHECKPOINTS, panel * (n_seg_pan + n_ckpt + 3));
   auto P = [&](size_t i) { return (void*)(base + i * panel); };
   auto CK = [&](int sg, int which) { return P(n_seg_pan + 2 * (size_t)sg + which); };
   void* E = P(n_seg_pan + n_ckpt);
@@ -746,12 +750,7 @@ extern "C" int tbk_density_and_forces(tbk_ctx* ctx, const tbk_bsr* H, const tbk_
     // Panels y_1 .. y_{p-2} are needed in reverse order: all of them are kept when they fit the
     // budget, else segments of ~sqrt(2p) steps are replayed from checkpoints.
     const int npan = std::max(0, p - 2);  // y_1 .. y_{p-2}
-    size_t budget = (size_t)std::max<int64_t>(0, max_panel_bytes);
-    if (budget == 0) {
-      size_t fr = 0, tot = 0;
-      TBK_CUDA(cudaMemGetInfo(&fr, &tot));
-      budget = (size_t)(0.6 * (double)fr);
-    }
+    size_t budget = max_panel_bytes > 0 ? (size_t)max_panel_bytes : panel_budget(ctx, WS_CHECKPOINTS);
     int seg = std::max(1, npan);
     if ((size_t)(npan + 3) * panel > budget && npan > 2) {
       seg = std::max(2, (int)std::ceil(std::sqrt(2.0 * npan)));

@@ -574,12 +574,7 @@ extern "C" int tbk_batched_density_and_forces(
   // ---- panels and the checkpoint plan (as in the single-cluster adjoint) ----
   const size_t panel = (size_t)op.n_rows * s * 4;
   const int npm = std::max(0, jmax);
-  size_t budget = (size_t)std::max<int64_t>(0, max_panel_bytes);
-  if (budget == 0) {
-    size_t fr = 0, tot = 0;
-    TBK_CUDA(cudaMemGetInfo(&fr, &tot));
-    budget = (size_t)(0.6 * (double)fr);
-  }
+  size_t budget = max_panel_bytes > 0 ? (size_t)max_panel_bytes : panel_budget(ctx, WS_CHECKPOINTS);
   int seg = std::max(1, npm);
   if ((size_t)(npm + 4) * panel > budget && npm > 2) {
     seg = std::max(2, (int)std::ceil(std::sqrt(2.0 * npm)));

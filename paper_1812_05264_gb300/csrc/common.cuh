@@ -72,6 +72,9 @@ struct DeviceGuard {
   ~DeviceGuard();
 };
 void sync(tbk_ctx* ctx);
+// Device bytes that slot s may grow to: what is free plus what s already holds, less a reserve
+// of 2 GiB + 3 % of the device for everything else.
+size_t panel_budget(tbk_ctx* ctx, Slot s);
 // Brackets the launches of one kernel family with events on ctx->stream when that family is the
 // one selected by tbk_kernel_timer (and the stream is not being captured into a graph).
 struct KernelTimerScope {

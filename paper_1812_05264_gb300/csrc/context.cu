@@ -1,4 +1,6 @@
 // Context, scratch management and the error channel of the C ABI.
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace tbk {
@@ -7,15 +9,33 @@ static thread_local std::string g_last_error;
 
 void set_error(const char* msg) { g_last_error = msg ? msg : ""; }
 
+size_t panel_budget(tbk_ctx* ctx, Slot s) {
+  size_t fr = 0, tot = 0;
+  TBK_CUDA(cudaMemGetInfo(&fr, &tot));
+  const size_t have = fr + ctx->slot_bytes[s];
+  const size_t reserve = ((size_t)2 << 30) + tot / 100 * 3;
+  return have > reserve ? have - reserve : 0;
+}
+
 void* scratch(tbk_ctx* ctx, Slot s, size_t bytes) {
   if (bytes == 0) bytes = 256;
   if (ctx->slot_bytes[s] >= bytes) return ctx->slot_ptr[s];
   if (ctx->slot_ptr[s]) {
+    const bool large = ctx->slot_bytes[s] > ((size_t)256 << 20);
     TBK_CUDA(cudaFreeAsync(ctx->slot_ptr[s], ctx->stream));
     ctx->slot_ptr[s] = nullptr;
     ctx->slot_bytes[s] = 0;
+    if (large) {
+      // hand the old block back to the device before the larger one is mapped, so that the two
+      // never have to fit side by side
+      TBK_CUDA(cudaStreamSynchronize(ctx->stream));
+      cudaMemPool_t pool;
+      TBK_CUDA(cudaDeviceGetDefaultMemPool(&pool, ctx->device));
+      TBK_CUDA(cudaMemPoolTrimTo(pool, 0));
+    }
   }
-  size_t want = bytes + bytes / 8;  // headroom so that slowly growing sizes do not thrash
+  // headroom so that slowly growing sizes do not thrash (at most 1 GiB)
+  size_t want = bytes + std::min(bytes / 8, (size_t)1 << 30);
   want = (want + 255) & ~(size_t)255;
   void* p = nullptr;
   cudaError_t e = cudaMallocAsync(&p, want, ctx->stream);

@@ -11,8 +11,11 @@ recurrence with FP64 moments; the number of Chebyshev terms p follows the error 
 exp(-6.4 p kT / W) of Sec. II.B.1 with eps = 1e-7.
 
 Metric: atom*vector*Chebyshev-steps/s = N_atoms * probes * p / (time of one full step, energies
-and forces).  `roofline` reports the fused recurrence kernel (cheb_step_kernel) against the
-measured HBM copy bandwidth; `cpu_baseline` times the FP64 oracle on a bounded sub-cluster.
+and forces).  Every launch of the three kernel families of the path (recurrence step, adjoint
+step, windowed outer products) is bracketed by CUDA events inside the timed steps; `kernels`
+gives each family's roofline (HBM bytes or FP32 FMA flops, whichever bounds it) and `roofline`
+repeats the one with the largest share of the step.  `cpu_baseline` times the FP64 oracle on a
+bounded sub-cluster.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Under torchrun (N > 1) every rank runs an independent replica (replicas only: the path has no
@@ -41,9 +44,10 @@ METRIC = "atom*vector*Chebyshev-steps/s"
 UNIT = "atom*vector*steps/s"
 
 
-def make_workload(name: str, rank: int = 0):
+def make_workload(name: str, rank: int = 0, atom_order: str = "radial"):
     if name == "fcc10k":
-        return wl.fcc_cu(10000, kT=0.025, n_probes=512, seed=5264, probe_seed=52640 + rank)
+        return wl.fcc_cu(10000, kT=0.025, n_probes=512, seed=5264, probe_seed=52640 + rank,
+                         atom_order=atom_order)
     if name == "fcc1k":
         return wl.fcc_cu(1000, kT=0.5, n_probes=256, seed=5264, probe_seed=52640 + rank)
     if name == "sc1k":
@@ -124,7 +128,7 @@ class ClockSampler:
 # oracle timing (cpu_baseline and the reference arm)
 # ---------------------------------------------------------------------------------------------
 
-SAMPLE_ATOMS = 400
+SAMPLE_ATOMS = 600
 
 
 def oracle_sample(wk_full, n_atoms: int = SAMPLE_ATOMS):
@@ -165,7 +169,7 @@ def cpu_cores() -> int:
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
-    wk = oracle_sample(make_workload(args.workload))
+    wk = oracle_sample(make_workload(args.workload, 0, args.atom_order))
     if wk is None:
         print(json.dumps({"impl": "reference", "unavailable": "oracle sample defined for the fcc workloads only"}))
         return 0
@@ -237,7 +241,7 @@ def run_ours(args, rank, world):
         if dist:
             torch.distributed.barrier()
 
-    wk = make_workload(args.workload, rank)
+    wk = make_workload(args.workload, rank, args.atom_order)
     ctx = api.Context()
     solver = api.Solver(wk, ctx)
     stream = ctx.stream
@@ -246,8 +250,6 @@ def run_ours(args, rank, world):
     box = solver.box
     fp64 = not wk.mixed
     esz = 8 if fp64 else 4
-    fused = wk.mixed and wk.n_orb == 9 and wk.n_probes in (128, 256, 512)
-
     def step(p_dev):
         g = api.build_neighbors(ctx, p_dev, wk.cutoff, box)
         H = api.assemble_H(ctx, solver.model, p_dev, g, box)
@@ -256,7 +258,8 @@ def run_ours(args, rank, world):
         _, obs, _, F = api.energies_and_forces(
             ctx, H, solver.model if solver.model.is_sk else None, p_dev, box, emin, emax,
             wk.probe_seed, wk.n_probes, p, wk.n_electrons, wk.kT, wk.jackson, fp64,
-            want_G=not solver.model.is_sk, want_forces=solver.model.is_sk)
+            want_G=not solver.model.is_sk, want_forces=solver.model.is_sk,
+            windowed=args.adjoint == "windowed")
         return p, obs, F, H.graph.nnzb
 
     if args.only_moments:
@@ -269,8 +272,8 @@ def run_ours(args, rank, world):
         step(pos)
     torch.cuda.synchronize()
     barrier()
-    # the dominant kernel: the fused adjoint step where it runs, else the recurrence step
-    ctx.time_kernel("backward" if fused else "step")
+    # every launch of the three kernel families of the path is bracketed by events
+    ctx.time_kernels("step", "backward", "window")
     clocks = ClockSampler(local, enabled=not args.no_clocks)
     clocks.start()
     launches0 = ctx.launches
@@ -283,8 +286,8 @@ def run_ours(args, rank, world):
     t1.record(stream)
     torch.cuda.synchronize()
     launches = ctx.launches - launches0
-    k_ms, k_launches = ctx.kernel_time()
-    ctx.time_kernel(None)
+    fam = {f: ctx.kernel_time(f) for f in ("step", "backward", "window")}
+    ctx.time_kernels()
     barrier()
     ms = t0.elapsed_time(t1) / args.steps
     # end to end: positions from pinned host memory in, energies and forces back to the host
@@ -320,34 +323,49 @@ def run_ours(args, rank, world):
     except Exception:
         pass
     hbm = float(peaks.get("hbm_gbs", 6800.0))
-    avg_s = k_ms / max(k_launches, 1) / 1e3
     B2 = wk.n_orb ** 2
-    if fused:
-        # reads ybar_{k+1}, ybar_{k+2}, y_k, y_{k-1}, y_{k+1}, writes ybar_k; H^ blocks; the FP64
-        # accumulator of G read and written once
-        bytes_pl = 6 * panel + nnzb * B2 * (esz + 16)
-        flops_pl = 4 * nnzb * B2 * wk.n_probes   # block product + outer product, 2 flops per FMA
-        alu = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
-        t_mem, t_alu = bytes_pl / (hbm * 1e9), flops_pl / (alu * 1e12)
+    alu = 1.25 if fp64 else SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    K = p // 2
+    nwin = (K - 1 + 3) // 4 + 1 if K >= 1 else 0
+    # algorithmic bytes and flops (2 per FMA) of each family over the timed steps
+    hb, blk = nnzb * B2 * esz, 2 * nnzb * B2 * wk.n_probes
+    alg = {
+        # y_{k+1} = 2 H^ y_k - y_{k-1}: reads y_k, y_{k-1}, the H^ blocks, writes y_{k+1}
+        "step": (lambda n: n * (3 * panel + hb), lambda n: n * blk, "cheb_step_bulk",
+                 "cheb_step_bulk_fcc10000.md", "recurrence.cu"),
+        # ybar_k = g_k + 2 H^ ybar_{k+1} - ybar_{k+2}: reads ybar_{k+1}, ybar_{k+2}, y_k, y_{k-1},
+        # y_{k+1}, the H^ blocks, writes ybar_k
+        "backward": (lambda n: n * (6 * panel + hb), lambda n: n * blk, "clenshaw_sddmm_bulk",
+                     "clenshaw_bulk_fcc10000.md", "adjoint.cu"),
+        # G += sum_j y_j ybar_{j+1}^T (j = 0 .. K-1, K pairs a step): reads both panels of every
+        # pair, reads and writes the FP64 accumulator once per window
+        "window": (lambda n: args.steps * (K * 2 * panel + nwin * nnzb * B2 * 16),
+                   lambda n: args.steps * K * blk, "sddmm_window", "sddmm_window_fcc10000.md",
+                   "adjoint.cu"),
+    }
+    kernels = {}
+    for f, (tms, nl) in fam.items():
+        if nl == 0:
+            continue
+        byf, flf, kname, prof, src = alg[f]
+        by, fl = byf(nl) / args.steps, flf(nl) / args.steps
+        sec = tms / 1e3 / args.steps
+        t_mem, t_alu = by / (hbm * 1e9), fl / (alu * 1e12)
         if t_alu >= t_mem:
-            roof = {"bound": "alu", "achieved": flops_pl / avg_s / 1e12, "peak": alu, "unit": "TFLOP/s",
-                    "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz (derived, FP32 FMA)"}
+            r = {"bound": "alu", "achieved": fl / sec / 1e12, "peak": alu, "unit": "TFLOP/s",
+                 "peak_source": ("152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz (derived, FP32 FMA)"
+                                 if not fp64 else "152 SMs x 64 FP64 ops x 2070 MHz / 64 (derived)")}
         else:
-            roof = {"bound": "hbm", "achieved": bytes_pl / avg_s / 1e9, "peak": hbm, "unit": "GB/s",
-                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
-        roof.update(kernel="clenshaw_sddmm_bulk", algorithmic_bytes_per_launch=bytes_pl,
-                    algorithmic_flops_per_launch=flops_pl,
-                    traffic=traffic_from_profile("clenshaw_sddmm_bulk_fcc10000.md", "adjoint.cu"))
-    else:
-        bytes_pl = 3 * panel + nnzb * B2 * esz
-        roof = {"bound": "hbm", "achieved": bytes_pl / avg_s / 1e9, "peak": hbm, "unit": "GB/s",
-                "kernel": "cheb_step_kernel", "algorithmic_bytes_per_launch": bytes_pl,
-                "traffic": traffic_from_profile("cheb_step_bulk_fcc10000.md", "recurrence.cu"),
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
-    roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["avg_launch_ms"] = k_ms / max(k_launches, 1)
-    roof["launches_timed"] = k_launches
-    roof["share_of_step"] = k_ms / (ms * args.steps)
+            r = {"bound": "hbm", "achieved": by / sec / 1e9, "peak": hbm, "unit": "GB/s",
+                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+        r["frac"] = r["achieved"] / r["peak"]
+        r.update(kernel=kname, traffic=traffic_from_profile(prof, src),
+                 algorithmic_bytes_per_launch=by * args.steps / nl,
+                 algorithmic_flops_per_launch=fl * args.steps / nl,
+                 avg_launch_ms=tms / nl, launches_timed=nl, share_of_step=tms / (ms * args.steps))
+        kernels[f] = r
+    dom = max(kernels, key=lambda f: kernels[f]["share_of_step"])
+    roof = dict(kernels[dom])
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -356,11 +374,13 @@ def run_ours(args, rank, world):
                    "probes": wk.n_probes, "order_p": p, "kT": wk.kT, "nnzb": nnzb,
                    "moments": "FP64", "recurrence": "FP64" if fp64 else "FP32",
                    "l2": "panels (%.0f MB each) larger than L2" % (n_rows * wk.n_probes * esz / 1e6),
-                   "parallelism": f"replicas x{world}", "seeds": [5264, wk.probe_seed]},
+                   "parallelism": f"replicas x{world}", "seeds": [5264, wk.probe_seed],
+                   "adjoint": args.adjoint},
         "e2e": {"value": units * world / (e_med / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "roofline": roof,
+        "kernels": {f: {k: v for k, v in r.items() if k != "peak_source"} for f, r in kernels.items()},
         "clocks": clk,
         "observables_per_atom": {"mu": obs[0], "Omega": obs[1] / wk.n_atoms,
                                  "E": obs[2] / wk.n_atoms, "N": obs[3] / wk.n_atoms},
@@ -581,6 +601,10 @@ def main():
     ap.add_argument("--no-clocks", action="store_true",
                     help="do not run the nvidia-smi clock sampler (for runs under a profiler)")
     ap.add_argument("--order", type=int, default=64, help="order for --only-moments / --only-adjoint")
+    ap.add_argument("--atom-order", default="radial", choices=["radial", "morton"],
+                    help="listing order of the fcc10k atoms (same cluster)")
+    ap.add_argument("--adjoint", default="fused", choices=["fused", "windowed"],
+                    help="outer products inside each backward step, or over windows of 4 steps")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

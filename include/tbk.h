@@ -51,6 +51,8 @@ typedef enum {
 #define TBK_PLAIN_KERNEL 4     /* use the plain load/FMA step kernel instead of the TMA-fed one */
 #define TBK_NO_GRAPH 8         /* batched calls: enqueue the kernels directly, no CUDA graph */
 #define TBK_TENSOR_CORES 16    /* mixed mode: recurrence steps on the tensor cores (tcgen05, TF32 x3) */
+#define TBK_WINDOWED 32        /* adjoint: outer products summed over windows of 4 steps by their own
+                                  kernel instead of inside each backward step */
 
 /* Damping of the Chebyshev series. */
 #define TBK_DAMP_NONE 0
@@ -115,14 +117,16 @@ int64_t tbk_launch_count(tbk_ctx* ctx);
 /* Kernel families that tbk_kernel_timer can bracket with CUDA events. */
 #define TBK_KERNEL_NONE 0
 #define TBK_KERNEL_STEP 1     /* one recurrence step y_{k+1} = 2 H^ y_k - y_{k-1} (Eq. cheb_rec) */
-#define TBK_KERNEL_BACKWARD 2 /* one fused adjoint step: ybar update and the G outer product */
-/* Select the kernel family whose launches on ctx's stream are from now on bracketed by a pair of
-   CUDA events (TBK_KERNEL_NONE switches timing off), and forget earlier pairs.  Launches captured
-   into CUDA graphs are not bracketed.  Host-side only; no GPU work. */
-int tbk_kernel_timer(tbk_ctx* ctx, int32_t kernel);
-/* Synchronise ctx's stream and return the summed device time (milliseconds) and the number of
-   bracketed launches since the last tbk_kernel_timer call.  total_ms, launches: host pointers. */
-int tbk_kernel_timer_read(tbk_ctx* ctx, double* total_ms, int64_t* launches);
+#define TBK_KERNEL_BACKWARD 2 /* one adjoint step ybar_k = g_k + 2 H^ ybar_{k+1} - ybar_{k+2} */
+#define TBK_KERNEL_WINDOW 3   /* the sampled outer products sum y_j ybar_{j+1}^T of a few steps */
+/* Select the kernel families whose launches on ctx's stream are from now on bracketed by pairs
+   of CUDA events: mask = sum of (1 << TBK_KERNEL_*) (0 switches timing off); earlier pairs are
+   forgotten.  Launches captured into CUDA graphs are not bracketed.  Host-side only. */
+int tbk_kernel_timer(tbk_ctx* ctx, int32_t mask);
+/* Synchronise ctx's stream and return, for one family TBK_KERNEL_*, the summed device time
+   (milliseconds) and the number of its bracketed launches since the last tbk_kernel_timer call.
+   total_ms, launches: host pointers. */
+int tbk_kernel_timer_read(tbk_ctx* ctx, int32_t kernel, double* total_ms, int64_t* launches);
 
 /* ---- a1: neighbour list (Sec. II.A mask M; Sec. II.E uniform-cube cell lists) ---------- */
 
@@ -198,11 +202,15 @@ int tbk_fermi_level(tbk_ctx* ctx, const double* moments, int32_t order, double e
    q = sum_k d_k beta_k[g] C_k, with the bounds held fixed:
      G = dOmega^/dH = (2/W)(1/s) sum_i sum_{j<order-1} y_ij x_ij^T on the pattern of H,
      y_ij = C_j(H^) r_i,  x_ij = (2 - delta_j0) sum_{k>j} d_k beta_k U_{k-j-1}(H^) r_i,
-   returned symmetrised, G_ab <- (G_ab + G_ba^T)/2.  The panels y_j are recomputed from
-   checkpoints when they do not fit in max_panel_bytes of scratch (0 = choose automatically).
+   returned symmetrised, G_ab <- (G_ab + G_ba^T)/2.  In mixed precision with 9x9 blocks and
+   n_probes 128, 256 or 512 the same gradient is taken through the doubled moments
+   mu_2k = 2<y_k, y_k>/s - mu_0, mu_2k-1 = 2<y_k, y_k-1>/s - mu_1, which needs y_j only up to
+   j = order/2.  The panels y_j are recomputed from checkpoints when they do not fit in
+   max_panel_bytes of scratch (0 = what the device has free, less a reserve).
    G: device, nnzb * n_orb^2 FP64, or NULL.  forces: device, n_atoms x 3 FP64, or NULL;
    F_c = -sum_ab <G_ab, dH_ab/dR_c> needs model->kind == TBK_MODEL_SK and pos (device) / box as
-   in tbk_assemble_H.  flags: TBK_MIXED or TBK_FP64, optionally | TBK_PLAIN_KERNEL. */
+   in tbk_assemble_H.  flags: TBK_MIXED or TBK_FP64, optionally | TBK_PLAIN_KERNEL |
+   TBK_WINDOWED (both ways give the same G up to FP32 summation order). */
 int tbk_density_and_forces(tbk_ctx* ctx, const tbk_bsr* H, const tbk_model* model,
                            const double* pos, const double* box, double emin, double emax,
                            uint64_t probe_seed, int32_t n_probes, int32_t order, double mu,
@@ -214,7 +222,7 @@ int tbk_density_and_forces(tbk_ctx* ctx, const tbk_bsr* H, const tbk_model* mode
    512 the forward sweep of the adjoint produces the moments as it goes, so no separate moment
    pass runs.  moments: device, order doubles, or NULL.  observables: host, 4 doubles {mu, Omega,
    E, N}.  G, forces as in tbk_density_and_forces (either may be NULL).  flags: TBK_MIXED or
-   TBK_FP64, optionally | TBK_PLAIN_KERNEL.  Synchronises the stream. */
+   TBK_FP64, optionally | TBK_PLAIN_KERNEL | TBK_WINDOWED.  Synchronises the stream. */
 int tbk_energies_and_forces(tbk_ctx* ctx, const tbk_bsr* H, const tbk_model* model,
                             const double* pos, const double* box, double emin, double emax,
                             uint64_t probe_seed, int32_t n_probes, int32_t order,

@@ -24,6 +24,7 @@ TBK_MOMENTS_DIRECT = 2
 TBK_PLAIN_KERNEL = 4
 TBK_NO_GRAPH = 8
 TBK_TENSOR_CORES = 16
+TBK_WINDOWED = 32
 TBK_DAMP_NONE = 0
 TBK_DAMP_JACKSON = 1
 TBK_FN_FERMI = 0
@@ -34,6 +35,7 @@ TBK_MODEL_TABLE = 2
 TBK_KERNEL_NONE = 0
 TBK_KERNEL_STEP = 1
 TBK_KERNEL_BACKWARD = 2
+TBK_KERNEL_WINDOW = 3
 
 _NAMES = {TBK_ERR_ARG: "TBK_ERR_ARG", TBK_ERR_CUDA: "TBK_ERR_CUDA", TBK_ERR_OOM: "TBK_ERR_OOM",
           TBK_ERR_SPECTRUM: "TBK_ERR_SPECTRUM", TBK_ERR_NOCONV: "TBK_ERR_NOCONV",
@@ -69,7 +71,7 @@ SIGNATURES = {
     "tbk_create": [C.POINTER(_P), C.c_int, _P],
     "tbk_destroy": [_P],
     "tbk_kernel_timer": [_P, _I],
-    "tbk_kernel_timer_read": [_P, C.POINTER(_D), C.POINTER(_L)],
+    "tbk_kernel_timer_read": [_P, _I, C.POINTER(_D), C.POINTER(_L)],
     "tbk_build_neighbors": [_P, _P, _I, _P, _D, _P, _P, _L, C.POINTER(_L)],
     "tbk_assemble_H": [_P, C.POINTER(tbk_model), _P, _I, _P, _P, _P, _L, _P],
     "tbk_spectral_bounds": [_P, C.POINTER(tbk_bsr), _I, _D, _U, C.POINTER(_D), C.POINTER(_D)],

@@ -40,17 +40,22 @@ class Context:
     def launches(self) -> int:
         return int(L.load().tbk_launch_count(self._h))
 
-    def time_kernel(self, kernel: str | None):
-        """Bracket every launch of one kernel family ("step", "backward", or None for off) with
-        CUDA events on this context's stream; read the sum with kernel_time()."""
-        k = {None: L.TBK_KERNEL_NONE, "step": L.TBK_KERNEL_STEP,
-             "backward": L.TBK_KERNEL_BACKWARD}[kernel]
-        L.call("tbk_kernel_timer", self._h, k)
+    _FAMILIES = {"step": L.TBK_KERNEL_STEP, "backward": L.TBK_KERNEL_BACKWARD,
+                 "window": L.TBK_KERNEL_WINDOW}
 
-    def kernel_time(self) -> tuple[float, int]:
-        """(total milliseconds, launches) of the timed family since time_kernel()."""
+    def time_kernels(self, *families: str):
+        """Bracket every launch of the named kernel families ("step": one recurrence step,
+        "backward": one adjoint step, "window": the outer products of a window of steps) with CUDA
+        events on this context's stream; no names switches timing off.  Read with kernel_time()."""
+        mask = 0
+        for f in families:
+            mask |= 1 << self._FAMILIES[f]
+        L.call("tbk_kernel_timer", self._h, mask)
+
+    def kernel_time(self, family: str) -> tuple[float, int]:
+        """(total milliseconds, launches) of one family since time_kernels()."""
         ms, n = C.c_double(), C.c_int64()
-        L.call("tbk_kernel_timer_read", self._h, C.byref(ms), C.byref(n))
+        L.call("tbk_kernel_timer_read", self._h, self._FAMILIES[family], C.byref(ms), C.byref(n))
         return ms.value, n.value
 
     def close(self):
@@ -204,7 +209,8 @@ def fermi_level(ctx: Context, moments: torch.Tensor, emin: float, emax: float,
 def density_and_forces(ctx: Context, H: BSR, model: Model | None, pos: torch.Tensor | None, box,
                        emin: float, emax: float, seed: int, n_probes: int, order: int, mu: float,
                        kT: float, jackson: bool = False, fp64: bool = False, want_G: bool = True,
-                       want_forces: bool = True, max_panel_bytes: int = 0, plain: bool = False):
+                       want_forces: bool = True, max_panel_bytes: int = 0, plain: bool = False,
+                       windowed: bool = False):
     """a9-a10: (G, F) with G = dOmega^/dH (nnzb, b, b) and F = -dOmega^/dR (N, 3)."""
     dev = H.val.device
     G = torch.empty_like(H.val) if want_G else None
@@ -214,7 +220,8 @@ def density_and_forces(ctx: Context, H: BSR, model: Model | None, pos: torch.Ten
            C.byref(model.s) if model is not None else None, _ptr(pos), bx, emin, emax,
            C.c_uint64(seed), int(n_probes), int(order), float(mu), float(kT),
            L.TBK_DAMP_JACKSON if jackson else L.TBK_DAMP_NONE,
-           (L.TBK_FP64 if fp64 else L.TBK_MIXED) | (L.TBK_PLAIN_KERNEL if plain else 0),
+           (L.TBK_FP64 if fp64 else L.TBK_MIXED) | (L.TBK_PLAIN_KERNEL if plain else 0)
+           | (L.TBK_WINDOWED if windowed else 0),
            int(max_panel_bytes), _ptr(G), _ptr(F))
     return G, F
 
@@ -271,7 +278,8 @@ def batched_density_and_forces(ctx: Context, Hs: list, model: Model, positions: 
 def energies_and_forces(ctx: Context, H: BSR, model: Model | None, pos: torch.Tensor | None, box,
                         emin: float, emax: float, seed: int, n_probes: int, order: int,
                         n_electrons: float, kT: float, jackson: bool = False, fp64: bool = False,
-                        want_G: bool = False, want_forces: bool = True, max_panel_bytes: int = 0):
+                        want_G: bool = False, want_forces: bool = True, max_panel_bytes: int = 0,
+                        windowed: bool = False):
     """a5-a10 in one call: (moments, (mu, Omega, E, N), G or None, forces or None)."""
     dev = H.val.device
     mom = torch.empty(order, dtype=torch.float64, device=dev)
@@ -282,7 +290,8 @@ def energies_and_forces(ctx: Context, H: BSR, model: Model | None, pos: torch.Te
     L.call("tbk_energies_and_forces", ctx.handle, C.byref(H.struct()),
            C.byref(model.s) if model is not None else None, _ptr(pos), bx, emin, emax,
            C.c_uint64(seed), int(n_probes), int(order), float(n_electrons), float(kT),
-           L.TBK_DAMP_JACKSON if jackson else L.TBK_DAMP_NONE, L.TBK_FP64 if fp64 else L.TBK_MIXED,
+           L.TBK_DAMP_JACKSON if jackson else L.TBK_DAMP_NONE,
+           (L.TBK_FP64 if fp64 else L.TBK_MIXED) | (L.TBK_WINDOWED if windowed else 0),
            int(max_panel_bytes), _ptr(mom), obs, _ptr(G), _ptr(F))
     return mom, tuple(obs[:]), G, F
 

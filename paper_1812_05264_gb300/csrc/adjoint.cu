@@ -12,6 +12,7 @@
 #include <algorithm>
 #include <cmath>
 #include <functional>
+#include <type_traits>
 #include <vector>
 
 #include "bulk.cuh"
@@ -76,14 +77,14 @@ sddmm_kernel(int n_atoms, const int32_t* __restrict__ row_ptr, const int32_t* __
 // lanes cover interleaved 4-probe groups, and a butterfly reduce-scatter over the lanes leaves
 // one entry per lane, added to the FP64 accumulator (one CTA owns each block: no atomics).
 
-template <int CW>
+template <int CW, bool SD = true>
 struct SdCfg {
-  static constexpr int D = 2;
+  static constexpr int D = SD ? 2 : 3;
   static constexpr int P = 128 * CW;
   static constexpr int XB = 9 * P * 4;
   static constexpr int HB = Layout<float, 9>::BS * 4;
   static constexpr int SB = ((XB + HB + 127) / 128) * 128;
-  static constexpr int YB = ((XB + 127) / 128) * 128;
+  static constexpr int YB = SD ? ((XB + 127) / 128) * 128 : 0;
   static constexpr int SMEM = (D + 1) * SB + YB + 8 * (2 * D + 6);
   static constexpr int THREADS = 32 * (CW + 1);
 };
@@ -122,7 +123,7 @@ __device__ __forceinline__ void sddmm_quadrant(int q, const float* Y, const floa
 #pragma unroll 1
   for (int m = 0; m < P / 128; ++m) {
     const int pb = 4 * (lane + 32 * m);
-    float yv[5][4], xv[5][4];
+    float yv[5][4];
 #pragma unroll
     for (int i = 0; i < 5; ++i) {
       if (y_probe) {
@@ -132,17 +133,17 @@ __device__ __forceinline__ void sddmm_quadrant(int q, const float* Y, const floa
         const float4 u = *reinterpret_cast<const float4*>(Y + ri[i] * P + pb);
         yv[i][0] = u.x; yv[i][1] = u.y; yv[i][2] = u.z; yv[i][3] = u.w;
       }
-      const float4 u = *reinterpret_cast<const float4*>(X + rl[i] * P + pb);
-      xv[i][0] = u.x; xv[i][1] = u.y; xv[i][2] = u.z; xv[i][3] = u.w;
     }
+    // one column row of X at a time keeps 4 of its values live instead of 20
 #pragma unroll
-    for (int i = 0; i < 5; ++i)
+    for (int l = 0; l < 5; ++l) {
+      const float4 u = *reinterpret_cast<const float4*>(X + rl[l] * P + pb);
 #pragma unroll
-      for (int l = 0; l < 5; ++l)
-#pragma unroll
-        for (int t = 0; t < 4; t += 2)
-          v2[i * 5 + l] = __ffma2_rn(make_float2(yv[i][t], yv[i][t + 1]),
-                                     make_float2(xv[l][t], xv[l][t + 1]), v2[i * 5 + l]);
+      for (int i = 0; i < 5; ++i) {
+        v2[i * 5 + l] = __ffma2_rn(make_float2(yv[i][0], yv[i][1]), make_float2(u.x, u.y), v2[i * 5 + l]);
+        v2[i * 5 + l] = __ffma2_rn(make_float2(yv[i][2], yv[i][3]), make_float2(u.z, u.w), v2[i * 5 + l]);
+      }
+    }
   }
   float v[32];
 #pragma unroll
@@ -154,7 +155,9 @@ __device__ __forceinline__ void sddmm_quadrant(int q, const float* Y, const floa
     atomicAdd(Gacc + k * 81 + i * 9 + l, w * (double)v[0]);
 }
 
-template <int CW>
+// SD = false: the Clenshaw step alone (the outer products are left to sddmm_window); the own-row
+// tile y_j then streams through the ring like the other source terms.
+template <int CW, bool SD>
 __global__ void __launch_bounds__(32 * (CW + 1))
 clenshaw_sddmm_bulk(const int n_atoms, const int32_t* __restrict__ row_ptr,
                     const int32_t* __restrict__ col, const float* __restrict__ hv,
@@ -163,7 +166,7 @@ clenshaw_sddmm_bulk(const int n_atoms, const int32_t* __restrict__ row_ptr,
                     const int s, const double w, double* __restrict__ Gacc, int* __restrict__ err,
                     const BatchRows batch, const float4* __restrict__ cf_cl,
                     const float* __restrict__ ym1, const float* __restrict__ yp1) {
-  using C = SdCfg<CW>;
+  using C = SdCfg<CW, SD>;
   constexpr int D = C::D;
   extern __shared__ __align__(128) unsigned char smem[];
   unsigned char* own = smem + D * C::SB;
@@ -175,7 +178,9 @@ clenshaw_sddmm_bulk(const int n_atoms, const int32_t* __restrict__ row_ptr,
   const uint32_t own_full = bar0 + 8u * (2 * D), own_empty = bar0 + 8u * (2 * D + 1);
   const uint32_t y_full = bar0 + 8u * (2 * D + 2), y_empty = bar0 + 8u * (2 * D + 3);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const bool has_prev = bprev != nullptr, y_probe = ypan == nullptr, has_out = bout != nullptr;
+  const bool has_prev = bprev != nullptr, has_out = bout != nullptr;
+  // y_tile: the own-row tile y_j is staged once per task for the outer products
+  const bool y_probe = ypan == nullptr, y_tile = SD && !y_probe;
   if (threadIdx.x == 0) {
     for (int i = 0; i < D; ++i) {
       mbar_init(full(i), 1);
@@ -190,12 +195,13 @@ clenshaw_sddmm_bulk(const int n_atoms, const int32_t* __restrict__ row_ptr,
   __syncthreads();
 
   // own-row tiles streamed after the neighbour tiles, with their coefficients:
-  // b_prev (-1), y_{k-1} (cf.z), y_{k+1} (cf.w)
-  const float* extra_src[3];
-  float extra_cf[3];
+  // b_prev (-1), y_{k-1} (cf.z), y_{k+1} (cf.w), and y_k (cf.y) when it is not staged
+  const float* extra_src[4];
+  float extra_cf[4];
   int n_extra = 0;
   if (has_out) {
     if (has_prev) { extra_src[n_extra] = bprev; extra_cf[n_extra++] = -1.f; }
+    if (!SD && ypan && cf.y != 0.f) { extra_src[n_extra] = ypan; extra_cf[n_extra++] = cf.y; }
     if (ym1 && cf.z != 0.f) { extra_src[n_extra] = ym1; extra_cf[n_extra++] = cf.z; }
     if (yp1 && cf.w != 0.f) { extra_src[n_extra] = yp1; extra_cf[n_extra++] = cf.w; }
   }
@@ -205,7 +211,7 @@ clenshaw_sddmm_bulk(const int n_atoms, const int32_t* __restrict__ row_ptr,
       bool ok = true;
       for (int a = blockIdx.x; a < n_atoms && ok; a += gridDim.x) {
         const int k0 = __ldg(row_ptr + a), k1 = __ldg(row_ptr + a + 1);
-        if (!y_probe) {
+        if (y_tile) {
           ok = mbar_wait(y_empty, (y_it & 1) ^ 1);
           if (!ok) break;
           mbar_expect_tx(y_full, C::XB);
@@ -263,7 +269,7 @@ clenshaw_sddmm_bulk(const int n_atoms, const int32_t* __restrict__ row_ptr,
       rloc = (int64_t)9 * (a - __ldg(batch.atom0 + cl));
       if (cf_cl) cfa = cf_cl[cl];
     }
-    if (!y_probe) {
+    if (y_tile) {
       ok = mbar_wait(y_full, y_it & 1);
       if (!ok) break;
     }
@@ -287,15 +293,17 @@ clenshaw_sddmm_bulk(const int n_atoms, const int32_t* __restrict__ row_ptr,
       if (!ok) break;
       const float* X = reinterpret_cast<const float*>(base);
       if (has_out) spmm_tile_f2(X, reinterpret_cast<const float*>(base + C::XB), C::P, pl, acc);
-      for (int qd = warp; qd < 4; qd += CW)
-        sddmm_quadrant<C::P>(qd, Ys, X, y_probe, sd, rloc, lane, (int64_t)(k0 + q), w, Gacc);
+      if constexpr (SD) {
+        for (int qd = warp; qd < 4; qd += CW)
+          sddmm_quadrant<C::P>(qd, Ys, X, y_probe, sd, rloc, lane, (int64_t)(k0 + q), w, Gacc);
+      }
       __syncwarp();
       if (lane == 0) mbar_arrive(is_own ? own_empty : empty(st));
       if (is_own) ++own_it; else ++it;
     }
     if (!ok) break;
     if (!has_out) {
-      if (!y_probe) {
+      if (y_tile) {
         __syncwarp();
         if (lane == 0) mbar_arrive(y_empty);
         ++y_it;
@@ -314,7 +322,7 @@ clenshaw_sddmm_bulk(const int n_atoms, const int32_t* __restrict__ row_ptr,
 #pragma unroll
         for (int v = 0; v < 4; ++v) yo[i][v] = fmaf(cfa.x, tbk_probe_sign(sd, rloc + i, pl + v), yo[i][v]);
     }
-    if (cfa.y != 0.f && !y_probe) {
+    if (y_tile && cfa.y != 0.f) {
 #pragma unroll
       for (int i = 0; i < 9; ++i) {
         const float4 t = *reinterpret_cast<const float4*>(Ys + i * C::P + pl);
@@ -344,11 +352,193 @@ clenshaw_sddmm_bulk(const int n_atoms, const int32_t* __restrict__ row_ptr,
       const int64_t row = (int64_t)9 * a + i;
       *reinterpret_cast<float4*>(bout + row * s + pl) = make_float4(yo[i][0], yo[i][1], yo[i][2], yo[i][3]);
     }
-    if (!y_probe) {
+    if (y_tile) {
       __syncwarp();
       if (lane == 0) mbar_arrive(y_empty);
       ++y_it;
     }
+  }
+  if (!ok) atomicOr(err, 2);
+}
+
+// ---- outer products of a window of backward steps (TMA-fed, FP32, 9x9 blocks) ------------------
+//
+// Gacc_ab += w sum_{t < nw} sum_probes y_{k_t}[a] ybar_{k_t + 1}[b]^T for every stored block (a, b).
+// Summing nw steps before the cross-lane reduction spreads its cost over nw block products.
+// One CTA task is one block row a: the producer warp stages the nw own-row tiles y_{k_t}[a] (or
+// writes the probe block when y[0] is NULL, nw = 1) and streams the nw neighbour tiles
+// ybar_{k_t+1}[b] of every block through a D-stage ring.  Consumer thread t owns probes
+// 4t .. 4t+3 of all 81 entries, accumulated as (even probe, odd probe) pairs with FFMA2.  Per
+// block, a reduce-scatter over the lanes and a fixed-order sum over the warps (in shared memory)
+// give one total per entry, added to the FP64 accumulator by one thread: the result does not
+// depend on timing.
+
+constexpr int SDW = 4;  // steps per window
+
+struct WindowPanels {
+  const float* y[SDW];  // y_{k_t} panels (n_rows x s); y[0] = NULL: the probe block
+  const float* x[SDW];  // ybar_{k_t + 1} panels
+};
+
+template <int CW>
+struct WinCfg {
+  static constexpr int D = 8;  // tiles in flight: one 18 KB tile is consumed every ~0.2 us
+  static constexpr int P = 128 * CW;
+  static constexpr int XB = 9 * P * 4;
+  static constexpr int RED = 2 * CW * 96 * 4;
+  static constexpr int SMEM = (SDW + D) * XB + RED + 8 * (2 * D + 6);
+  static constexpr int THREADS = 32 * (CW + 1);
+};
+
+template <int CW>
+__global__ void __launch_bounds__(32 * (CW + 1), CW == 4 ? 1 : 2)
+sddmm_window(const int n_atoms, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+             const WindowPanels wp, const int nw, const uint64_t seed, const int s, const double w,
+             double* __restrict__ Gacc, int* __restrict__ err) {
+  using C = WinCfg<CW>;
+  constexpr int D = C::D, P = C::P;
+  extern __shared__ __align__(128) unsigned char smem[];
+  float* Yw = reinterpret_cast<float*>(smem);                       // SDW own-row tiles
+  unsigned char* ring = smem + SDW * C::XB;                          // D neighbour tiles
+  float* red = reinterpret_cast<float*>(smem + (SDW + D) * C::XB);   // [2][CW][96]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (SDW + D) * C::XB + C::RED);
+  const uint32_t bar0 = smem_u32(bars);
+  auto full = [&](int i) { return bar0 + 8u * i; };
+  auto empty = [&](int i) { return bar0 + 8u * (D + i); };
+  const uint32_t y_full = bar0 + 8u * (2 * D), y_empty = bar0 + 8u * (2 * D + 1);
+  auto red_full = [&](int b) { return bar0 + 8u * (2 * D + 2 + b); };
+  auto red_empty = [&](int b) { return bar0 + 8u * (2 * D + 4 + b); };
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const bool probe = wp.y[0] == nullptr;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < D; ++i) {
+      mbar_init(full(i), 1);
+      mbar_init(empty(i), CW);
+    }
+    mbar_init(y_full, 1);
+    mbar_init(y_empty, CW);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(red_full(b), CW);
+      mbar_init(red_empty(b), 1);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+
+  if (warp == CW) {
+    // producer warp: lane 0 issues the copies; in the probe case all lanes write the probe block
+    int it = 0, y_it = 0;
+    bool ok = true;
+    for (int a = blockIdx.x; a < n_atoms && ok; a += gridDim.x) {
+      if (lane == 0) ok = mbar_wait(y_empty, (y_it & 1) ^ 1);
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      if (!ok) break;
+      if (probe) {
+        for (int e = lane; e < 9 * P; e += 32) {
+          const int i = e / P, pr = e - i * P;
+          Yw[e] = tbk_probe_sign(seed, (int64_t)9 * a + i, pr);
+        }
+        __threadfence_block();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(y_full);
+      } else if (lane == 0) {
+        mbar_expect_tx(y_full, nw * C::XB);
+        for (int t = 0; t < nw; ++t)
+          bulk_g2s(smem_u32(Yw + t * 9 * P), wp.y[t] + (int64_t)9 * a * s, C::XB, y_full);
+      }
+      ++y_it;
+      if (lane == 0) {
+        const int k0 = __ldg(row_ptr + a), k1 = __ldg(row_ptr + a + 1);
+        for (int q = k0; q < k1 && ok; ++q) {
+          const int b = __ldg(col + q);
+          for (int t = 0; t < nw && ok; ++t) {
+            const int st = it % D;
+            ok = mbar_wait(empty(st), ((it / D) & 1) ^ 1);
+            if (!ok) break;
+            mbar_expect_tx(full(st), C::XB);
+            bulk_g2s(smem_u32(ring + st * C::XB), wp.x[t] + (int64_t)9 * b * s, C::XB, full(st));
+            ++it;
+          }
+        }
+      }
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+    }
+    if (!ok && lane == 0) {
+      atomicOr(err, 2);
+      for (int j = (it > D ? it - D : 0); j < it; ++j) mbar_wait(full(j % D), (j / D) & 1);
+      if (y_it > 0 && !probe) mbar_wait(y_full, (y_it - 1) & 1);
+    }
+    return;
+  }
+
+  int it = 0, y_it = 0, r_it = 0;
+  bool ok = true;
+  const int pl = 4 * threadIdx.x;
+  for (int a = blockIdx.x; a < n_atoms && ok; a += gridDim.x) {
+    const int k0 = __ldg(row_ptr + a), k1 = __ldg(row_ptr + a + 1);
+    ok = mbar_wait(y_full, y_it & 1);
+    if (!ok) break;
+    for (int q = k0; q < k1 && ok; ++q) {
+      float2 acc[81];
+#pragma unroll
+      for (int e = 0; e < 81; ++e) acc[e] = make_float2(0.f, 0.f);
+      for (int t = 0; t < nw; ++t) {
+        const int st = it % D;
+        ok = mbar_wait(full(st), (it / D) & 1);
+        if (!ok) break;
+        const float* X = reinterpret_cast<const float*>(ring + st * C::XB);
+        const float* Y = Yw + t * 9 * P;
+        float4 xv[9];
+#pragma unroll
+        for (int l = 0; l < 9; ++l) xv[l] = *reinterpret_cast<const float4*>(X + l * P + pl);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+          const float4 yv = *reinterpret_cast<const float4*>(Y + i * P + pl);
+#pragma unroll
+          for (int l = 0; l < 9; ++l) {
+            acc[i * 9 + l] = __ffma2_rn(make_float2(yv.x, yv.y), make_float2(xv[l].x, xv[l].y), acc[i * 9 + l]);
+            acc[i * 9 + l] = __ffma2_rn(make_float2(yv.z, yv.w), make_float2(xv[l].z, xv[l].w), acc[i * 9 + l]);
+          }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(empty(st));
+        ++it;
+      }
+      if (!ok) break;
+      // lanes -> one partial per entry and warp (entries padded to 3 x 32)
+      const int rb = r_it & 1, use = r_it >> 1;
+      float* R = red + rb * CW * 96;
+#pragma unroll
+      for (int blk = 0; blk < 3; ++blk) {
+        float v[32];
+#pragma unroll
+        for (int e = 0; e < 32; ++e) v[e] = blk * 32 + e < 81 ? acc[blk * 32 + e].x + acc[blk * 32 + e].y : 0.f;
+        butterfly32(v, lane);
+        if (blk == 0 && use > 0) ok = mbar_wait(red_empty(rb), (use - 1) & 1);
+        R[warp * 96 + blk * 32 + lane] = v[0];
+      }
+      if (!ok) break;
+      __syncwarp();
+      if (lane == 0) mbar_arrive(red_full(rb));
+      if (warp == 0) {
+        // fixed-order sum over the warps, one writer per entry
+        ok = mbar_wait(red_full(rb), use & 1);
+        if (!ok) break;
+        for (int e = lane; e < 81; e += 32) {
+          float tsum = R[e];
+#pragma unroll
+          for (int v = 1; v < CW; ++v) tsum += R[v * 96 + e];
+          atomicAdd(Gacc + (int64_t)q * 81 + e, w * (double)tsum);
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(red_empty(rb));
+      }
+      ++r_it;
+    }
+    if (!ok) break;
+    __syncwarp();
+    if (lane == 0) mbar_arrive(y_empty);
+    ++y_it;
   }
   if (!ok) atomicOr(err, 2);
 }
@@ -440,18 +630,18 @@ bool fused_eligible(const HOp& op, int s, int plain) {
   return !plain && op.prec == TBK_MIXED && op.B == 9 && (s == 128 || s == 256 || s == 512);
 }
 
-template <int CW>
+template <int CW, bool SD>
 static void launch_fused_cw(tbk_ctx* ctx, const HOp& op, const void* bin, const void* bprev, void* bout,
                             const void* ypan, float4 cf, uint64_t seed, int s, double w, double* Gacc,
                             int* err, const BatchRows& batch, const float4* cf_cl, const void* ym1,
                             const void* yp1) {
-  using C = SdCfg<CW>;
-  TBK_CUDA(cudaFuncSetAttribute(clenshaw_sddmm_bulk<CW>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
+  using C = SdCfg<CW, SD>;
+  TBK_CUDA(cudaFuncSetAttribute(clenshaw_sddmm_bulk<CW, SD>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
   int occ = 0;
-  TBK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, clenshaw_sddmm_bulk<CW>, C::THREADS, C::SMEM));
+  TBK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, clenshaw_sddmm_bulk<CW, SD>, C::THREADS, C::SMEM));
   TBK_CHECK_ARG(occ > 0, "fused adjoint kernel does not fit on this device");
   const int G = std::max(1, std::min(op.n_atoms, occ * ctx->num_sms));
-  clenshaw_sddmm_bulk<CW><<<G, C::THREADS, C::SMEM, ctx->stream>>>(
+  clenshaw_sddmm_bulk<CW, SD><<<G, C::THREADS, C::SMEM, ctx->stream>>>(
       op.n_atoms, op.row_ptr, op.col, (const float*)op.hv, (const float*)bin, (const float*)bprev,
       (float*)bout, (const float*)ypan, cf, seed, s, w, Gacc, err, batch, cf_cl, (const float*)ym1,
       (const float*)yp1);
@@ -463,12 +653,16 @@ void launch_fused(tbk_ctx* ctx, const HOp& op, const void* bin, const void* bpre
                   int* err, const BatchRows& batch, const float4* cf_cl, const void* ym1,
                   const void* yp1) {
   KernelTimerScope timer(ctx, TBK_KERNEL_BACKWARD);
-  if (s == 512)
-    launch_fused_cw<4>(ctx, op, bin, bprev, bout, ypan, cf, seed, s, w, Gacc, err, batch, cf_cl, ym1, yp1);
-  else if (s == 256)
-    launch_fused_cw<2>(ctx, op, bin, bprev, bout, ypan, cf, seed, s, w, Gacc, err, batch, cf_cl, ym1, yp1);
-  else
-    launch_fused_cw<1>(ctx, op, bin, bprev, bout, ypan, cf, seed, s, w, Gacc, err, batch, cf_cl, ym1, yp1);
+  // Gacc == nullptr: the Clenshaw step alone
+  auto go = [&](auto cw, auto sd) {
+    launch_fused_cw<decltype(cw)::value, decltype(sd)::value>(ctx, op, bin, bprev, bout, ypan, cf, seed, s, w,
+                                                              Gacc, err, batch, cf_cl, ym1, yp1);
+  };
+  using T = std::true_type;
+  using F = std::false_type;
+  if (s == 512) Gacc ? go(std::integral_constant<int, 4>(), T()) : go(std::integral_constant<int, 4>(), F());
+  else if (s == 256) Gacc ? go(std::integral_constant<int, 2>(), T()) : go(std::integral_constant<int, 2>(), F());
+  else Gacc ? go(std::integral_constant<int, 1>(), T()) : go(std::integral_constant<int, 1>(), F());
 }
 
 static void launch_sddmm(tbk_ctx* ctx, const HOp& op, const void* y, int y_is_probe, uint64_t seed,
@@ -528,6 +722,30 @@ void launch_forces(tbk_ctx* ctx, const DevModel& M, const double* pos, int n_ato
   post_launch(ctx, "gather_forces");
 }
 
+template <int CW>
+static void launch_window_cw(tbk_ctx* ctx, const HOp& op, const WindowPanels& wp, int nw, uint64_t seed,
+                             int s, double w, double* Gacc, int* err) {
+  using C = WinCfg<CW>;
+  TBK_CUDA(cudaFuncSetAttribute(sddmm_window<CW>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
+  int occ = 0;
+  TBK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, sddmm_window<CW>, C::THREADS, C::SMEM));
+  TBK_CHECK_ARG(occ > 0, "windowed outer-product kernel does not fit on this device");
+  const int G = std::max(1, std::min(op.n_atoms, occ * ctx->num_sms));
+  sddmm_window<CW><<<G, C::THREADS, C::SMEM, ctx->stream>>>(op.n_atoms, op.row_ptr, op.col, wp, nw, seed,
+                                                             s, w, Gacc, err);
+  post_launch(ctx, "sddmm_window");
+}
+
+// Gacc_ab += w sum_t sum_probes y_t[a] x_t[b]^T over the stored blocks, 1 <= nw <= SDW steps.
+void launch_window(tbk_ctx* ctx, const HOp& op, const WindowPanels& wp, int nw, uint64_t seed, int s,
+                   double w, double* Gacc, int* err) {
+  KernelTimerScope timer(ctx, TBK_KERNEL_WINDOW);
+  TBK_CHECK_ARG(nw >= 1 && nw <= SDW && (wp.y[0] != nullptr || nw == 1), "bad outer-product window");
+  if (s == 512) launch_window_cw<4>(ctx, op, wp, nw, seed, s, w, Gacc, err);
+  else if (s == 256) launch_window_cw<2>(ctx, op, wp, nw, seed, s, w, Gacc, err);
+  else launch_window_cw<1>(ctx, op, wp, nw, seed, s, w, Gacc, err);
+}
+
 // ---- adjoint of the doubled moments (TMA-fed fused path) ------------------------------------
 //
 // The moments come from the doubling identities (C_m C_n = (C_{m+n} + C_{|m-n|})/2):
@@ -556,7 +774,7 @@ __global__ void ybar_init(int64_t n, int s, float ca, const float* __restrict__ 
 // so the caller can finish the moments, solve for mu and return the coefficients c_0 .. c_{p-1}).
 void adjoint_doubling(tbk_ctx* ctx, const HOp& op, uint64_t probe_seed, int s, int p,
                       const std::function<std::vector<double>()>& get_coefs, double* partials, int nctas,
-                      int64_t max_panel_bytes, double* Gacc, int* err) {
+                      int64_t max_panel_bytes, double* Gacc, int* err, bool windowed) {
   const int K = p / 2;
   if (K < 1) {
     get_coefs();
@@ -581,34 +799,44 @@ void adjoint_doubling(tbk_ctx* ctx, const HOp& op, uint64_t probe_seed, int s, i
   const size_t panel = (size_t)op.n_rows * s * 4;
   size_t budget = max_panel_bytes > 0 ? (size_t)max_panel_bytes : panel_budget(ctx, WS_CHECKPOINTS);
   const int npan = K;  // y_1 .. y_K
+  // ybar_j lives in ring slot j mod NB: the two of the recurrence, plus the window's SDW panels
+  // when the outer products are summed over windows of steps
+  const int NB = windowed ? SDW + 2 : 2;
   int seg = std::max(1, npan);
-  if ((size_t)(npan + 4) * panel > budget && npan > 2) {
-    seg = std::max(2, (int)std::ceil(std::sqrt(2.0 * npan)));
-    const size_t need = (size_t)(2 * ((npan + seg - 1) / seg) + seg + 4) * panel;
+  auto seg_plan = [&]() {
+    // segments of a multiple of SDW steps, so that windows never straddle a segment
+    const int r = std::max(2, (int)std::ceil(std::sqrt(2.0 * npan)));
+    return ((r + SDW - 1) / SDW) * SDW;
+  };
+  if ((size_t)(npan + 2 + NB) * panel > budget && npan > 2) {
+    seg = seg_plan();
+    const size_t need = (size_t)(2 * ((npan + seg - 1) / seg) + seg + 2 + NB) * panel;
     if (need > budget)
       throw Error(TBK_ERR_OOM, "panel scratch budget of " + std::to_string(budget) +
                                    " bytes is below the checkpoint plan's " + std::to_string(need));
   }
   int nseg = (npan + seg - 1) / seg;
   // P(0 .. seg): segment panels (P(i) = y_{t0 - 1 + i}); checkpoints (y_{t0-2}, y_{t0-1}); E = y_{t1+1};
-  // two ybar panels
+  // NB ybar panels
+  auto plan_bytes = [&]() {
+    return panel * ((size_t)seg + 1 + (nseg <= 1 ? 0 : 2 * (size_t)nseg) + 1 + NB);
+  };
   char* base = nullptr;
   try {
-    base = (char*)scratch(ctx, WS_CHECKPOINTS, panel * ((size_t)seg + 1 + (nseg <= 1 ? 0 : 2 * (size_t)nseg) + 3));
+    base = (char*)scratch(ctx, WS_CHECKPOINTS, plan_bytes());
   } catch (const Error& e) {
     // the device could not map the all-stored plan after all: replay segments instead
     if (e.code != TBK_ERR_OOM || nseg > 1 || npan <= 2) throw;
-    seg = std::max(2, (int)std::ceil(std::sqrt(2.0 * npan)));
+    seg = seg_plan();
     nseg = (npan + seg - 1) / seg;
-    base = (char*)scratch(ctx, WS_CHECKPOINTS, panel * ((size_t)seg + 1 + 2 * (size_t)nseg + 3));
+    base = (char*)scratch(ctx, WS_CHECKPOINTS, plan_bytes());
   }
   const bool all_stored = nseg <= 1;
   const size_t n_seg_pan = (size_t)seg + 1, n_ckpt = all_stored ? 0 : 2 * (size_t)nseg;
   auto P = [&](size_t i) { return (void*)(base + i * panel); };
   auto CK = [&](int sg, int which) { return P(n_seg_pan + 2 * (size_t)sg + which); };
   void* E = P(n_seg_pan + n_ckpt);
-  void* bcur = P(n_seg_pan + n_ckpt + 1);
-  void* bprev = P(n_seg_pan + n_ckpt + 2);
+  auto YB = [&](int j) { return P(n_seg_pan + n_ckpt + 1 + (size_t)(j % NB)); };
   auto forward_step = [&](int t, const void* yin, const void* yprev, void* yout, bool first_time) {
     StepArgs a;
     a.seed = probe_seed;
@@ -639,7 +867,6 @@ void adjoint_doubling(tbk_ctx* ctx, const HOp& op, uint64_t probe_seed, int s, i
     }
   }
   int k = K;
-  bool have_bprev = false;
   for (int sg = nseg - 1; sg >= -1 && k >= 0; --sg) {
     const int t0 = sg >= 0 ? 1 + seg * sg : 0;
     const int t1 = sg >= 0 ? std::min(npan, t0 + seg - 1) : 0;
@@ -672,20 +899,33 @@ void adjoint_doubling(tbk_ctx* ctx, const HOp& op, uint64_t probe_seed, int s, i
         // ybar_K = g_K (y_{K+1} does not enter)
         const int64_t n = op.n_rows * s;
         ybar_init<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(
-            op.n_rows, s, ca(K), (const float*)Y(K), cb(K), (const float*)Y(K - 1), probe_seed, (float*)bcur);
+            op.n_rows, s, ca(K), (const float*)Y(K), cb(K), (const float*)Y(K - 1), probe_seed, (float*)YB(K));
         post_launch(ctx, "ybar_init");
         continue;
       }
       if (k >= 1) {
-        // ybar_k = g_k + 2 H^ ybar_{k+1} - ybar_{k+2}, and G += 2 y_k ybar_{k+1}^T on the pattern
+        // ybar_k = g_k + 2 H^ ybar_{k+1} - ybar_{k+2}; fused: and G += 2 y_k ybar_{k+1}^T on the pattern
         const float4 cf = make_float4(k == 1 ? cb(1) : 0.f, ca(k), k == 1 ? 0.f : cb(k), cc(k));
-        launch_fused(ctx, op, bcur, have_bprev ? bprev : nullptr, bprev, Y(k), cf, probe_seed, s, 2.0, Gacc,
-                     err, BatchRows(), nullptr, k >= 2 ? Y(k - 1) : nullptr, Y(k + 1));
-        std::swap(bcur, bprev);
-        have_bprev = true;
-      } else {
+        launch_fused(ctx, op, YB(k + 1), k + 2 <= K ? YB(k + 2) : nullptr, YB(k), Y(k), cf, probe_seed, s, 2.0,
+                     windowed ? nullptr : Gacc, err, BatchRows(), nullptr, k >= 2 ? Y(k - 1) : nullptr, Y(k + 1));
+        if (windowed && (k - 1) % SDW == 0) {
+          // G += 2 y_j ybar_{j+1}^T on the pattern for the window j = k .. min(k + SDW, K) - 1
+          WindowPanels wp{};
+          const int nw = std::min(SDW, K - k);
+          for (int t = 0; t < nw; ++t) {
+            wp.y[t] = (const float*)Y(k + t);
+            wp.x[t] = (const float*)YB(k + t + 1);
+          }
+          launch_window(ctx, op, wp, nw, probe_seed, s, 2.0, Gacc, err);
+        }
+      } else if (windowed) {
         // G += y_0 ybar_1^T
-        launch_fused(ctx, op, bcur, nullptr, nullptr, nullptr, make_float4(0.f, 0.f, 0.f, 0.f), probe_seed, s,
+        WindowPanels wp{};
+        wp.y[0] = nullptr;
+        wp.x[0] = (const float*)YB(1);
+        launch_window(ctx, op, wp, 1, probe_seed, s, 1.0, Gacc, err);
+      } else {
+        launch_fused(ctx, op, YB(1), nullptr, nullptr, nullptr, make_float4(0.f, 0.f, 0.f, 0.f), probe_seed, s,
                      1.0, Gacc, err, BatchRows(), nullptr, nullptr, nullptr);
       }
     }
@@ -707,7 +947,7 @@ extern "C" int tbk_density_and_forces(tbk_ctx* ctx, const tbk_bsr* H, const tbk_
   TBK_CHECK_ARG(G || forces, "nothing to compute: G and forces are both NULL");
   TBK_CHECK_ARG(order >= 1, "order must be >= 1");
   TBK_CHECK_ARG(n_probes >= 4 && n_probes % 4 == 0, "n_probes must be a positive multiple of 4");
-  TBK_CHECK_ARG((flags & ~(TBK_FP64 | TBK_PLAIN_KERNEL)) == 0, "unknown flag");
+  TBK_CHECK_ARG((flags & ~(TBK_FP64 | TBK_PLAIN_KERNEL | TBK_WINDOWED)) == 0, "unknown flag");
   const int plain = (flags & TBK_PLAIN_KERNEL) ? 1 : 0;
   TBK_CHECK_ARG(kT > 0.0, "kT must be positive");
   DeviceGuard dg(ctx);
@@ -744,7 +984,8 @@ extern "C" int tbk_density_and_forces(tbk_ctx* ctx, const tbk_bsr* H, const tbk_
   const size_t panel = (size_t)op.n_rows * s * esz;
   double scale = 2.0 / (W * s);
   if (fused) {
-    adjoint_doubling(ctx, op, probe_seed, s, p, [&]() { return c; }, nullptr, 0, max_panel_bytes, Gacc, err);
+    adjoint_doubling(ctx, op, probe_seed, s, p, [&]() { return c; }, nullptr, 0, max_panel_bytes, Gacc, err,
+                       (flags & TBK_WINDOWED) != 0);
     scale = 2.0 / W;  // the 1/s of the moments is inside the source terms
   } else {
     // Panels y_1 .. y_{p-2} are needed in reverse order: all of them are kept when they fit the
@@ -891,7 +1132,7 @@ extern "C" int tbk_energies_and_forces(tbk_ctx* ctx, const tbk_bsr* H, const tbk
   TBK_CHECK_ARG(ctx != nullptr && observables != nullptr, "NULL argument");
   TBK_CHECK_ARG(order >= 1, "order must be >= 1");
   TBK_CHECK_ARG(n_probes >= 4 && n_probes % 4 == 0, "n_probes must be a positive multiple of 4");
-  TBK_CHECK_ARG((flags & ~(TBK_FP64 | TBK_PLAIN_KERNEL)) == 0, "unknown flag");
+  TBK_CHECK_ARG((flags & ~(TBK_FP64 | TBK_PLAIN_KERNEL | TBK_WINDOWED)) == 0, "unknown flag");
   TBK_CHECK_ARG(kT > 0.0 && n_electrons >= 0.0, "kT must be positive and n_electrons >= 0");
   DeviceGuard dg(ctx);
   const int prec = (flags & TBK_FP64) ? TBK_FP64 : TBK_MIXED;
@@ -902,7 +1143,7 @@ extern "C" int tbk_energies_and_forces(tbk_ctx* ctx, const tbk_bsr* H, const tbk
   if (!H || !fused_eligible(shape, n_probes, plain)) {
     // the separate calls give the same results for the other shapes and precisions
     double* mom = moments ? moments : (double*)scratch(ctx, WS_SEGMENT, sizeof(double) * (size_t)order);
-    int rc = tbk_chebyshev_moments(ctx, H, emin, emax, probe_seed, n_probes, order, flags, mom);
+    int rc = tbk_chebyshev_moments(ctx, H, emin, emax, probe_seed, n_probes, order, flags & ~TBK_WINDOWED, mom);
     if (rc != TBK_OK) throw Error(rc, tbk_last_error());
     rc = tbk_fermi_level(ctx, mom, order, emin, emax, n_electrons, 0.0, kT, damping, observables);
     if (rc != TBK_OK) throw Error(rc, tbk_last_error());
@@ -965,7 +1206,8 @@ extern "C" int tbk_energies_and_forces(tbk_ctx* ctx, const tbk_bsr* H, const tbk
     sync(ctx);
     return c;
   };
-  adjoint_doubling(ctx, op, probe_seed, s, p, after_forward, partials, nctas, max_panel_bytes, Gacc, err);
+  adjoint_doubling(ctx, op, probe_seed, s, p, after_forward, partials, nctas, max_panel_bytes, Gacc, err,
+                   (flags & TBK_WINDOWED) != 0);
   double* Gout = G ? G : Gsym;
   const int64_t tot = op.nnzb * BB;
   symmetrize<9><<<(unsigned)((tot + 255) / 256), 256, 0, ctx->stream>>>(op.nnzb, tr, Gacc, 2.0 / W, Gout);

@@ -52,9 +52,10 @@ struct tbk_ctx {
   size_t slot_bytes[tbk::WS_NSLOTS] = {};
   void* pinned = nullptr;        // small pinned host buffer for scalar read-back
   size_t pinned_bytes = 0;
-  int timed_kernel = 0;          // TBK_KERNEL_* whose launches are bracketed by events
-  std::vector<cudaEvent_t> timer_events;
-  size_t timer_used = 0;
+  int timed_mask = 0;            // bit f set: launches of kernel family f are bracketed by events
+  std::vector<cudaEvent_t> timer_events;  // (begin, end) pairs
+  std::vector<int> timer_family;          // family of each pair
+  size_t timer_used = 0;                  // events in use
 };
 
 namespace tbk {
@@ -75,8 +76,8 @@ void sync(tbk_ctx* ctx);
 // Device bytes that slot s may grow to: what is free plus what s already holds, less a reserve
 // of 2 GiB + 3 % of the device for everything else.
 size_t panel_budget(tbk_ctx* ctx, Slot s);
-// Brackets the launches of one kernel family with events on ctx->stream when that family is the
-// one selected by tbk_kernel_timer (and the stream is not being captured into a graph).
+// Brackets the launches of one kernel family with events on ctx->stream when that family is
+// selected by tbk_kernel_timer (and the stream is not being captured into a graph).
 struct KernelTimerScope {
   tbk_ctx* ctx = nullptr;
   KernelTimerScope(tbk_ctx* c, int kernel);

@@ -88,11 +88,14 @@ static void timer_record(tbk_ctx* ctx) {
 }
 
 KernelTimerScope::KernelTimerScope(tbk_ctx* c, int kernel) {
-  if (c->timed_kernel == 0 || c->timed_kernel != kernel) return;
+  if (kernel <= 0 || kernel > 30 || !(c->timed_mask & (1 << kernel))) return;
   cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
   TBK_CUDA(cudaStreamIsCapturing(c->stream, &st));
   if (st != cudaStreamCaptureStatusNone) return;
   timer_record(c);
+  const size_t pair = (c->timer_used - 1) / 2;
+  if (c->timer_family.size() <= pair) c->timer_family.resize(pair + 1);
+  c->timer_family[pair] = kernel;
   ctx = c;
 }
 
@@ -145,29 +148,31 @@ int tbk_destroy(tbk_ctx* ctx) {
 
 const char* tbk_last_error(void) { return tbk::g_last_error.c_str(); }
 
-int tbk_kernel_timer(tbk_ctx* ctx, int32_t kernel) {
+int tbk_kernel_timer(tbk_ctx* ctx, int32_t mask) {
   TBK_API_BEGIN
   TBK_CHECK_ARG(ctx != nullptr, "ctx is NULL");
-  TBK_CHECK_ARG(kernel == TBK_KERNEL_NONE || kernel == TBK_KERNEL_STEP || kernel == TBK_KERNEL_BACKWARD,
-                "unknown kernel family");
-  ctx->timed_kernel = kernel;
+  TBK_CHECK_ARG((mask & ~((2 << TBK_KERNEL_WINDOW) - 2)) == 0, "unknown kernel family");
+  ctx->timed_mask = mask;
   ctx->timer_used = 0;
   TBK_API_END
 }
 
-int tbk_kernel_timer_read(tbk_ctx* ctx, double* total_ms, int64_t* launches) {
+int tbk_kernel_timer_read(tbk_ctx* ctx, int32_t kernel, double* total_ms, int64_t* launches) {
   TBK_API_BEGIN
   TBK_CHECK_ARG(ctx && total_ms && launches, "NULL argument");
   tbk::DeviceGuard g(ctx);
   tbk::sync(ctx);
   double t = 0.0;
+  int64_t n = 0;
   for (size_t i = 0; i + 1 < ctx->timer_used; i += 2) {
+    if (ctx->timer_family[i / 2] != kernel) continue;
     float ms = 0.f;
     TBK_CUDA(cudaEventElapsedTime(&ms, ctx->timer_events[i], ctx->timer_events[i + 1]));
     t += ms;
+    ++n;
   }
   *total_ms = t;
-  *launches = (int64_t)(ctx->timer_used / 2);
+  *launches = n;
   TBK_API_END
 }
 

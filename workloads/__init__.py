@@ -80,6 +80,19 @@ def fcc_sphere(n_atoms: int, a: float = FCC_A, jitter: float = 0.0, seed: int = 
     return pos
 
 
+def morton_order(pos: np.ndarray, cell: float) -> np.ndarray:
+    """Permutation that lists atoms by the Morton (Z-order) code of their cell on a grid of
+    spacing ``cell`` (ties by input index): atoms close in space get close indices."""
+    if len(pos) == 0:
+        return np.zeros(0, dtype=np.int64)
+    q = np.floor((pos - pos.min(axis=0)) / cell).astype(np.int64)
+    code = np.zeros(len(pos), dtype=np.int64)
+    for bit in range(20):
+        for d in range(3):
+            code |= ((q[:, d] >> bit) & 1) << (3 * bit + d)
+    return np.lexsort((np.arange(len(pos)), code))
+
+
 def sk_integrals(seed: int) -> np.ndarray:
     """The 10 bond integrals (order ``SK_NAMES``) drawn N(0, 1) eV."""
     rng = np.random.default_rng(seed)
@@ -172,10 +185,20 @@ def sc_disorder(L: int = 10, t: float = -1.0, w: float = 0.5, seed: int = 1812,
 
 
 def fcc_cu(n_atoms: int, kT: float, n_probes: int, seed: int = 5264, probe_seed: int = 52640,
-           jitter: float = 0.0, order: int | None = None, mixed: bool = True) -> Workload:
-    """Copper-like fcc sphere with a seed-drawn s/p/d Slater-Koster model, 11 electrons/atom."""
+           jitter: float = 0.0, order: int | None = None, mixed: bool = True,
+           atom_order: str = "radial") -> Workload:
+    """Copper-like fcc sphere with a seed-drawn s/p/d Slater-Koster model, 11 electrons/atom.
+
+    atom_order: "radial" lists the atoms by (r^2, x, y, z); "morton" lists the same atoms by the
+    Z-order of their FCC_A-sized cells (the same cluster, spatially local indices)."""
     pos = fcc_sphere(n_atoms, jitter=jitter, seed=seed + 1)
-    return Workload(name=f"fcc{n_atoms}-sk9-kT{kT:g}", positions=pos, n_orb=9, kT=kT,
+    tag = ""
+    if atom_order == "morton":
+        pos = pos[morton_order(pos, FCC_A)]
+        tag = "-morton"
+    elif atom_order != "radial":
+        raise ValueError(f"unknown atom order {atom_order}")
+    return Workload(name=f"fcc{n_atoms}-sk9-kT{kT:g}{tag}", positions=pos, n_orb=9, kT=kT,
                     n_electrons=11.0 * n_atoms, n_probes=n_probes, probe_seed=probe_seed,
                     sk_V=sk_integrals(seed), order=order, mixed=mixed)
 

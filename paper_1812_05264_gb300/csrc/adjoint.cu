@@ -194,16 +194,19 @@ clenshaw_sddmm_bulk(const int n_atoms, const int32_t* __restrict__ row_ptr,
   }
   __syncthreads();
 
-  // own-row tiles streamed after the neighbour tiles, with their coefficients:
-  // b_prev (-1), y_{k-1} (cf.z), y_{k+1} (cf.w), and y_k (cf.y) when it is not staged
+  // own-row tiles streamed after the neighbour tiles, with the component of the (per-cluster)
+  // coefficient vector that scales them: b_prev (-1), y_k (.y, when it is not staged), y_{k-1}
+  // (.z), y_{k+1} (.w).  With per-cluster coefficients a tile is streamed whenever it is given.
+  enum { X_PREV = 0, X_Y = 1, X_YM1 = 2, X_YP1 = 3 };
   const float* extra_src[4];
-  float extra_cf[4];
+  int extra_kind[4];
   int n_extra = 0;
   if (has_out) {
-    if (has_prev) { extra_src[n_extra] = bprev; extra_cf[n_extra++] = -1.f; }
-    if (!SD && ypan && cf.y != 0.f) { extra_src[n_extra] = ypan; extra_cf[n_extra++] = cf.y; }
-    if (ym1 && cf.z != 0.f) { extra_src[n_extra] = ym1; extra_cf[n_extra++] = cf.z; }
-    if (yp1 && cf.w != 0.f) { extra_src[n_extra] = yp1; extra_cf[n_extra++] = cf.w; }
+    const bool any = cf_cl != nullptr;
+    if (has_prev) { extra_src[n_extra] = bprev; extra_kind[n_extra++] = X_PREV; }
+    if (!SD && ypan && (any || cf.y != 0.f)) { extra_src[n_extra] = ypan; extra_kind[n_extra++] = X_Y; }
+    if (ym1 && (any || cf.z != 0.f)) { extra_src[n_extra] = ym1; extra_kind[n_extra++] = X_YM1; }
+    if (yp1 && (any || cf.w != 0.f)) { extra_src[n_extra] = yp1; extra_kind[n_extra++] = X_YP1; }
   }
   if (warp == CW) {
     if (lane == 0) {
@@ -335,12 +338,15 @@ clenshaw_sddmm_bulk(const int n_atoms, const int32_t* __restrict__ row_ptr,
       ok = mbar_wait(full(st), (it / D) & 1);
       if (!ok) break;
       const float* X = reinterpret_cast<const float*>(smem + st * C::SB);
-      const float ce = extra_cf[e];
+      const int kd = extra_kind[e];
+      const float ce = kd == X_PREV ? -1.f : (kd == X_Y ? cfa.y : (kd == X_YM1 ? cfa.z : cfa.w));
+      if (ce != 0.f) {  // a zero coefficient skips the tile (its rows may never have been formed)
 #pragma unroll
-      for (int i = 0; i < 9; ++i) {
-        const float4 t = *reinterpret_cast<const float4*>(X + i * C::P + pl);
-        yo[i][0] = fmaf(ce, t.x, yo[i][0]); yo[i][1] = fmaf(ce, t.y, yo[i][1]);
-        yo[i][2] = fmaf(ce, t.z, yo[i][2]); yo[i][3] = fmaf(ce, t.w, yo[i][3]);
+        for (int i = 0; i < 9; ++i) {
+          const float4 t = *reinterpret_cast<const float4*>(X + i * C::P + pl);
+          yo[i][0] = fmaf(ce, t.x, yo[i][0]); yo[i][1] = fmaf(ce, t.y, yo[i][1]);
+          yo[i][2] = fmaf(ce, t.z, yo[i][2]); yo[i][3] = fmaf(ce, t.w, yo[i][3]);
+        }
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(empty(st));
@@ -774,14 +780,22 @@ __global__ void ybar_init(int64_t n, int s, float ca, const float* __restrict__ 
 // so the caller can finish the moments, solve for mu and return the coefficients c_0 .. c_{p-1}).
 void adjoint_doubling(tbk_ctx* ctx, const HOp& op, uint64_t probe_seed, int s, int p,
                       const std::function<std::vector<double>()>& get_coefs, double* partials, int nctas,
-                      int64_t max_panel_bytes, double* Gacc, int* err, bool windowed) {
-  const int K = p / 2;
+                      int64_t max_panel_bytes, double* Gacc, int* err, bool windowed, const AdjBatch* bt) {
+  TBK_CHECK_ARG(!(bt && (windowed || partials)), "batched adjoint: no windows, no moment partials");
+  const int K = bt ? (bt->K.empty() ? 0 : bt->K[0]) : p / 2;
   if (K < 1) {
-    get_coefs();
+    if (!bt) get_coefs();
     return;  // p = 1: the estimate does not depend on H
   }
+  // atoms of the (order-sorted) clusters that take part in step t: a prefix of the merged rows
+  auto active = [&](int t) {
+    if (!bt) return op.n_atoms;
+    int64_t r = 0;
+    for (size_t ci = 0; ci < bt->K.size() && bt->K[ci] >= t; ++ci) r += bt->n_at[ci];
+    return (int)r;
+  };
   std::vector<double> w(K + 2, 0.0), v(K + 2, 0.0);
-  bool have_coefs = false;
+  bool have_coefs = bt != nullptr;  // a batch brings its per-cluster coefficient table
   auto load_coefs = [&]() {
     const std::vector<double> c = get_coefs();
     for (int k = 1; k <= K; ++k) {
@@ -800,26 +814,27 @@ void adjoint_doubling(tbk_ctx* ctx, const HOp& op, uint64_t probe_seed, int s, i
   size_t budget = max_panel_bytes > 0 ? (size_t)max_panel_bytes : panel_budget(ctx, WS_CHECKPOINTS);
   const int npan = K;  // y_1 .. y_K
   // ybar_j lives in ring slot j mod NB: the two of the recurrence, plus the window's SDW panels
-  // when the outer products are summed over windows of steps
+  // when the outer products are summed over windows of steps; a batch also keeps the probe panel
   const int NB = windowed ? SDW + 2 : 2;
+  const int NX = NB + (bt ? 1 : 0);
   int seg = std::max(1, npan);
   auto seg_plan = [&]() {
     // segments of a multiple of SDW steps, so that windows never straddle a segment
     const int r = std::max(2, (int)std::ceil(std::sqrt(2.0 * npan)));
     return ((r + SDW - 1) / SDW) * SDW;
   };
-  if ((size_t)(npan + 2 + NB) * panel > budget && npan > 2) {
+  if ((size_t)(npan + 2 + NX) * panel > budget && npan > 2) {
     seg = seg_plan();
-    const size_t need = (size_t)(2 * ((npan + seg - 1) / seg) + seg + 2 + NB) * panel;
+    const size_t need = (size_t)(2 * ((npan + seg - 1) / seg) + seg + 2 + NX) * panel;
     if (need > budget)
       throw Error(TBK_ERR_OOM, "panel scratch budget of " + std::to_string(budget) +
                                    " bytes is below the checkpoint plan's " + std::to_string(need));
   }
   int nseg = (npan + seg - 1) / seg;
   // P(0 .. seg): segment panels (P(i) = y_{t0 - 1 + i}); checkpoints (y_{t0-2}, y_{t0-1}); E = y_{t1+1};
-  // NB ybar panels
+  // NB ybar panels; the probe panel of a batch
   auto plan_bytes = [&]() {
-    return panel * ((size_t)seg + 1 + (nseg <= 1 ? 0 : 2 * (size_t)nseg) + 1 + NB);
+    return panel * ((size_t)seg + 1 + (nseg <= 1 ? 0 : 2 * (size_t)nseg) + 1 + NX);
   };
   char* base = nullptr;
   try {
@@ -837,19 +852,34 @@ void adjoint_doubling(tbk_ctx* ctx, const HOp& op, uint64_t probe_seed, int s, i
   auto CK = [&](int sg, int which) { return P(n_seg_pan + 2 * (size_t)sg + which); };
   void* E = P(n_seg_pan + n_ckpt);
   auto YB = [&](int j) { return P(n_seg_pan + n_ckpt + 1 + (size_t)(j % NB)); };
+  void* R0 = bt ? P(n_seg_pan + n_ckpt + 1 + NB) : nullptr;
+  const BatchRows br = bt ? bt->br : BatchRows();
+  if (bt) {
+    // the probe block of every cluster, and ybar = 0 on the rows of clusters not yet started
+    // (their first backward step then reduces to ybar_K = g_K)
+    launch_batch_probe_panel(ctx, op, br, s, R0);
+    for (int j = 0; j < NB; ++j) TBK_CUDA(cudaMemsetAsync(YB(j), 0, panel, ctx->stream));
+  }
   auto forward_step = [&](int t, const void* yin, const void* yprev, void* yout, bool first_time) {
+    HOp o = op;
+    o.n_atoms = active(t);
+    if (o.n_atoms <= 0) return;
     StepArgs a;
     a.seed = probe_seed;
     a.s = s;
-    a.yin = yin;
-    a.cur_is_probe = t == 1;
+    a.yin = t == 1 ? R0 : yin;
+    a.cur_is_probe = t == 1 && !bt;
     a.alpha = t == 1 ? 1.0 : 2.0;
-    if (t == 2) a.c_r = -1.0;
-    else if (t >= 3) a.yprev = const_cast<void*>(yprev);
+    if (t == 2) {
+      if (bt) a.yprev = R0; else a.c_r = -1.0;
+    } else if (t >= 3) {
+      a.yprev = const_cast<void*>(yprev);
+    }
     a.yout = yout;
     a.err = err;
+    a.batch = br;
     if (partials && first_time) a.partials = partials + (size_t)(t - 1) * nctas * 2;
-    launch_step(ctx, op, a);
+    launch_step(ctx, o, a);
   };
   if (!all_stored) {
     void *cur = nullptr, *prv = nullptr;
@@ -895,7 +925,9 @@ void adjoint_doubling(tbk_ctx* ctx, const HOp& op, uint64_t probe_seed, int s, i
       return P(j - t0 + 1);
     };
     for (; k >= t0; --k) {
-      if (k == K) {
+      HOp o = op;
+      o.n_atoms = active(std::max(k, 1));
+      if (k == K && !bt) {
         // ybar_K = g_K (y_{K+1} does not enter)
         const int64_t n = op.n_rows * s;
         ybar_init<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(
@@ -905,9 +937,11 @@ void adjoint_doubling(tbk_ctx* ctx, const HOp& op, uint64_t probe_seed, int s, i
       }
       if (k >= 1) {
         // ybar_k = g_k + 2 H^ ybar_{k+1} - ybar_{k+2}; fused: and G += 2 y_k ybar_{k+1}^T on the pattern
-        const float4 cf = make_float4(k == 1 ? cb(1) : 0.f, ca(k), k == 1 ? 0.f : cb(k), cc(k));
-        launch_fused(ctx, op, YB(k + 1), k + 2 <= K ? YB(k + 2) : nullptr, YB(k), Y(k), cf, probe_seed, s, 2.0,
-                     windowed ? nullptr : Gacc, err, BatchRows(), nullptr, k >= 2 ? Y(k - 1) : nullptr, Y(k + 1));
+        const float4 cf = bt ? make_float4(0.f, 0.f, 0.f, 0.f)
+                             : make_float4(k == 1 ? cb(1) : 0.f, ca(k), k == 1 ? 0.f : cb(k), cc(k));
+        const float4* cfk = bt ? bt->cft + (size_t)k * bt->K.size() : nullptr;
+        launch_fused(ctx, o, YB(k + 1), (k + 2 <= K || bt) ? YB(k + 2) : nullptr, YB(k), Y(k), cf, probe_seed, s,
+                     2.0, windowed ? nullptr : Gacc, err, br, cfk, k >= 2 ? Y(k - 1) : nullptr, Y(k + 1));
         if (windowed && (k - 1) % SDW == 0) {
           // G += 2 y_j ybar_{j+1}^T on the pattern for the window j = k .. min(k + SDW, K) - 1
           WindowPanels wp{};
@@ -925,8 +959,8 @@ void adjoint_doubling(tbk_ctx* ctx, const HOp& op, uint64_t probe_seed, int s, i
         wp.x[0] = (const float*)YB(1);
         launch_window(ctx, op, wp, 1, probe_seed, s, 1.0, Gacc, err);
       } else {
-        launch_fused(ctx, op, YB(1), nullptr, nullptr, nullptr, make_float4(0.f, 0.f, 0.f, 0.f), probe_seed, s,
-                     1.0, Gacc, err, BatchRows(), nullptr, nullptr, nullptr);
+        launch_fused(ctx, o, YB(1), nullptr, nullptr, nullptr, make_float4(0.f, 0.f, 0.f, 0.f), probe_seed, s,
+                     1.0, Gacc, err, br, nullptr, nullptr, nullptr);
       }
     }
   }
@@ -985,7 +1019,7 @@ extern "C" int tbk_density_and_forces(tbk_ctx* ctx, const tbk_bsr* H, const tbk_
   double scale = 2.0 / (W * s);
   if (fused) {
     adjoint_doubling(ctx, op, probe_seed, s, p, [&]() { return c; }, nullptr, 0, max_panel_bytes, Gacc, err,
-                       (flags & TBK_WINDOWED) != 0);
+                       (flags & TBK_WINDOWED) != 0, nullptr);
     scale = 2.0 / W;  // the 1/s of the moments is inside the source terms
   } else {
     // Panels y_1 .. y_{p-2} are needed in reverse order: all of them are kept when they fit the
@@ -1207,7 +1241,7 @@ extern "C" int tbk_energies_and_forces(tbk_ctx* ctx, const tbk_bsr* H, const tbk
     return c;
   };
   adjoint_doubling(ctx, op, probe_seed, s, p, after_forward, partials, nctas, max_panel_bytes, Gacc, err,
-                   (flags & TBK_WINDOWED) != 0);
+                   (flags & TBK_WINDOWED) != 0, nullptr);
   double* Gout = G ? G : Gsym;
   const int64_t tot = op.nnzb * BB;
   symmetrize<9><<<(unsigned)((tot + 255) / 256), 256, 0, ctx->stream>>>(op.nnzb, tr, Gacc, 2.0 / W, Gout);

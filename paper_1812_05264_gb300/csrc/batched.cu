@@ -416,39 +416,10 @@ void launch_symmetrize_batched(tbk_ctx* ctx, int n_atoms, const int32_t* row_ptr
 void launch_forces(tbk_ctx* ctx, const DevModel& M, const double* pos, int n_atoms, const int32_t* row_ptr,
                    const int32_t* col, const int32_t* tr, const double* G, double* tq, double* F);
 
-// c_tab[j * ncl + ci] = (coef[ci * pmax + j], 0, 0, 0) for j < p_ci, else 0: the Clenshaw
-// coefficient enters the backward step as the probe source term.
-__global__ void coef_table(const double* __restrict__ coef, int pmax, int ncl,
-                           const int32_t* __restrict__ p, float4* __restrict__ c_tab) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (int64_t)pmax * ncl) return;
-  const int j = (int)(t / ncl), ci = (int)(t - (int64_t)j * ncl);
-  c_tab[t] = make_float4(j < p[ci] ? (float)coef[(int64_t)ci * pmax + j] : 0.f, 0.f, 0.f, 0.f);
-}
-
-// b_{p-1} = c_{p-1} r into the buffer that is "current" when the cluster joins the backward
-// sweep, zero into the other one.
-__global__ void init_b_panels(int64_t n_rows, int s, const int32_t* __restrict__ atom_cl,
-                              const uint64_t* __restrict__ seeds, const int32_t* __restrict__ atom0,
-                              const double* __restrict__ coef, int pmax, const int32_t* __restrict__ p,
-                              const int32_t* __restrict__ parity, float* __restrict__ B0,
-                              float* __restrict__ B1) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n_rows * s) return;
-  const int64_t row = i / s;
-  const int pr = (int)(i - row * s);
-  const int a = (int)(row / 9);
-  const int cl = atom_cl[a];
-  const float v = p[cl] >= 2 ? (float)(coef[(int64_t)cl * pmax + p[cl] - 1] *
-                                       (double)tbk_probe_sign(seeds[cl], row - (int64_t)9 * atom0[cl], pr))
-                             : 0.f;
-  if (parity[cl] == 0) {
-    B0[i] = v;
-    B1[i] = 0.f;
-  } else {
-    B0[i] = 0.f;
-    B1[i] = v;
-  }
+void launch_batch_probe_panel(tbk_ctx* ctx, const HOp& op, const BatchRows& br, int s, void* out) {
+  batch_probe_panel<<<(unsigned)((op.n_rows * s + 255) / 256), 256, 0, ctx->stream>>>(
+      op.n_rows, s, br.atom_cl, br.seed, br.atom0, (float*)out);
+  post_launch(ctx, "batch_probe_panel");
 }
 
 }  // namespace tbk
@@ -487,11 +458,11 @@ extern "C" int tbk_batched_density_and_forces(
     Mdl = upload_model(ctx, model, nullptr, WS_TABLE);
     TBK_CHECK_ARG(Mdl.kind == TBK_MODEL_SK, "forces need the Slater-Koster model");
   }
-  // ---- plan: sort by order (descending); npan = p - 2 panels y_1 .. y_{p-2} per cluster ----
+  // ---- plan: sort by K = order/2 (descending); cluster c needs y_1 .. y_{K_c} ----
   std::vector<int> idx(ncl);
   std::iota(idx.begin(), idx.end(), 0);
-  std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) { return orders[x] > orders[y]; });
-  std::vector<int32_t> a_off(ncl), n_at(ncl), pc(ncl), npan(ncl), par(ncl);
+  std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) { return orders[x] / 2 > orders[y] / 2; });
+  std::vector<int32_t> a_off(ncl), n_at(ncl), pc(ncl);
   std::vector<int64_t> b_off(ncl);
   std::vector<uint64_t> sd(ncl);
   std::vector<double> scale(ncl);
@@ -505,35 +476,24 @@ extern "C" int tbk_batched_density_and_forces(
     b_off[ci] = bo;
     n_at[ci] = H[c].n_atoms;
     pc[ci] = orders[c];
-    npan[ci] = orders[c] - 2;
     sd[ci] = seeds[c];
-    scale[ci] = 2.0 / ((emax[c] - emin[c]) * s);
+    scale[ci] = 2.0 / (emax[c] - emin[c]);
     ao += H[c].n_atoms;
     bo += H[c].nnzb;
     pmax = std::max(pmax, orders[c]);
   }
   TBK_CHECK_ARG(bo < INT32_MAX && ao * 9 < INT32_MAX, "batch too large for int32 indices");
-  const int jmax = npan[0];
-  for (int ci = 0; ci < ncl; ++ci) par[ci] = ((jmax - npan[ci]) % 2 + 2) % 2;
+  const int Kmax = pc[0] / 2;
   op.n_atoms = (int)ao;
   op.nnzb = bo;
   op.n_rows = ao * 9;
-  auto active = [&](int t) {  // atoms of the clusters with npan >= t
-    int64_t r = 0;
-    for (int ci = 0; ci < ncl && npan[ci] >= t; ++ci) r += n_at[ci];
-    return (int)r;
-  };
   // ---- device metadata, merged operator and positions ----
   char* meta = (char*)scratch(ctx, WS_TABLE, 128 * (size_t)ncl + 4096);
   // (WS_TABLE also holds the uploaded model table only for TABLE models; SK needs none)
   int32_t* d_atom0 = (int32_t*)meta;
-  int32_t* d_p = d_atom0 + ncl;
-  int32_t* d_par = d_p + ncl;
-  uint64_t* d_seed = (uint64_t*)(((uintptr_t)(d_par + ncl) + 15) & ~(uintptr_t)15);
+  uint64_t* d_seed = (uint64_t*)(((uintptr_t)(d_atom0 + ncl) + 15) & ~(uintptr_t)15);
   double* d_scale = (double*)(d_seed + ncl);
   TBK_CUDA(cudaMemcpyAsync(d_atom0, a_off.data(), 4 * ncl, cudaMemcpyHostToDevice, ctx->stream));
-  TBK_CUDA(cudaMemcpyAsync(d_p, pc.data(), 4 * ncl, cudaMemcpyHostToDevice, ctx->stream));
-  TBK_CUDA(cudaMemcpyAsync(d_par, par.data(), 4 * ncl, cudaMemcpyHostToDevice, ctx->stream));
   TBK_CUDA(cudaMemcpyAsync(d_seed, sd.data(), 8 * ncl, cudaMemcpyHostToDevice, ctx->stream));
   TBK_CUDA(cudaMemcpyAsync(d_scale, scale.data(), 8 * ncl, cudaMemcpyHostToDevice, ctx->stream));
   int32_t* m_row_ptr = (int32_t*)scratch(ctx, WS_CELLS, sizeof(int32_t) * (size_t)(2 * ao + 1) + 64);
@@ -561,106 +521,45 @@ extern "C" int tbk_batched_density_and_forces(
   br.atom0 = d_atom0;
   int* err = (int*)scratch(ctx, WS_FLAGS, 64);
   TBK_CUDA(cudaMemsetAsync(err, 0, sizeof(int), ctx->stream));
-  // ---- coefficients c_k = d_k beta_k[g] per cluster, table by step ----
+  // ---- coefficients c_k = d_k beta_k[g] per cluster -> the source coefficients of each step ----
   double* coefd = (double*)scratch(ctx, WS_COEF, sizeof(double) * (size_t)pmax * ncl);
   for (int ci = 0; ci < ncl; ++ci) {
     const int c = idx[ci];
     coefficients(ctx, TBK_FN_FREE, pc[ci], emin[c], emax[c], mu[c], kT[c], damping,
                  coefd + (size_t)ci * pmax);
   }
-  float4* c_tab = (float4*)scratch(ctx, WS_NODES, sizeof(float4) * (size_t)pmax * ncl + 64);
-  coef_table<<<ceil_div((int64_t)pmax * ncl, 256), 256, 0, ctx->stream>>>(coefd, pmax, ncl, d_p, c_tab);
-  post_launch(ctx, "coef_table");
-  // ---- panels and the checkpoint plan (as in the single-cluster adjoint) ----
-  const size_t panel = (size_t)op.n_rows * s * 4;
-  const int npm = std::max(0, jmax);
-  size_t budget = max_panel_bytes > 0 ? (size_t)max_panel_bytes : panel_budget(ctx, WS_CHECKPOINTS);
-  int seg = std::max(1, npm);
-  if ((size_t)(npm + 4) * panel > budget && npm > 2) {
-    seg = std::max(2, (int)std::ceil(std::sqrt(2.0 * npm)));
-    const size_t need = (size_t)(2 * ((npm + seg - 1) / seg) + seg + 4) * panel;
-    if (need > budget)
-      throw Error(TBK_ERR_OOM, "panel scratch budget of " + std::to_string(budget) +
-                                   " bytes is below the checkpoint plan's " + std::to_string(need));
+  std::vector<double> ch((size_t)pmax * ncl);
+  TBK_CUDA(cudaMemcpyAsync(ch.data(), coefd, sizeof(double) * ch.size(), cudaMemcpyDeviceToHost, ctx->stream));
+  sync(ctx);
+  // per step k and cluster: (probe, y_k, y_{k-1}, y_{k+1}) coefficients of g_k (zero once k > K_c)
+  std::vector<float4> cft((size_t)(Kmax + 1) * ncl, make_float4(0.f, 0.f, 0.f, 0.f));
+    for (int ci = 0; ci < ncl; ++ci) {
+    const int p = pc[ci], K = p / 2;
+    const double* c = ch.data() + (size_t)ci * pmax;
+    std::vector<double> w(K + 2, 0.0), v(K + 2, 0.0);
+    for (int k = 1; k <= K; ++k) {
+      if (2 * k < p) w[k] = 2.0 * c[2 * k];
+      if (k >= 2 && 2 * k - 1 < p) v[k] = 2.0 * c[2 * k - 1];
+    }
+    v[1] = p > 1 ? c[1] : 0.0;
+    for (int k = 2; 2 * k - 1 < p; ++k) v[1] -= c[2 * k - 1];
+    for (int k = 1; k <= K; ++k)
+      cft[(size_t)k * ncl + ci] = make_float4(k == 1 ? (float)(v[1] / s) : 0.f, (float)(2.0 * w[k] / s),
+                                              k == 1 ? 0.f : (float)(v[k] / s), (float)(v[k + 1] / s));
   }
-  const int nseg = npm > 0 ? (npm + seg - 1) / seg : 0;
-  const bool all_stored = nseg <= 1;
-  const size_t n_seg_pan = (size_t)seg + 1, n_ckpt = all_stored ? 0 : 2 * (size_t)nseg;
-  char* base = (char*)scratch(ctx, WS_CHECKPOINTS, panel * (n_seg_pan + n_ckpt + 3));
-  auto P = [&](size_t i) { return (void*)(base + i * panel); };
-  auto CK = [&](int sg, int which) { return P(n_seg_pan + 2 * (size_t)sg + which); };
-  void* R0 = P(n_seg_pan + n_ckpt);
-  void* bcur = P(n_seg_pan + n_ckpt + 1);
-  void* bprev = P(n_seg_pan + n_ckpt + 2);
+  float4* d_cft = (float4*)scratch(ctx, WS_NODES, sizeof(float4) * cft.size() + 64);
+  TBK_CUDA(cudaMemcpyAsync(d_cft, cft.data(), sizeof(float4) * cft.size(), cudaMemcpyHostToDevice, ctx->stream));
+  AdjBatch bt;
+  bt.br = br;
+  bt.cft = d_cft;
+  for (int ci = 0; ci < ncl; ++ci) {
+    bt.K.push_back(pc[ci] / 2);
+    bt.n_at.push_back(n_at[ci]);
+  }
   double* Gacc = (double*)scratch(ctx, WS_GACC, sizeof(double) * (size_t)bo * 81 * 2);
   double* Gsym = Gacc + (size_t)bo * 81;
   TBK_CUDA(cudaMemsetAsync(Gacc, 0, sizeof(double) * (size_t)bo * 81, ctx->stream));
-  batch_probe_panel<<<(unsigned)((op.n_rows * s + 255) / 256), 256, 0, ctx->stream>>>(
-      op.n_rows, s, atom_cl, d_seed, d_atom0, (float*)R0);
-  post_launch(ctx, "batch_probe_panel");
-  // y_t from y_{t-1} and y_{t-2} over the clusters still needing y_t
-  auto fstep = [&](int t, const void* yin, const void* yprev, void* yout) {
-    HOp o = op;
-    o.n_atoms = active(t);
-    if (o.n_atoms <= 0) return;
-    StepArgs a;
-    a.s = s;
-    a.yin = yin;
-    a.alpha = t == 1 ? 1.0 : 2.0;
-    if (t >= 2) a.yprev = const_cast<void*>(yprev);
-    a.yout = yout;
-    a.err = err;
-    a.batch = br;
-    launch_step(ctx, o, a);
-  };
-  if (!all_stored) {
-    void *cur = R0, *prv = nullptr;
-    const int last = seg * (nseg - 1);
-    for (int t = 1; t <= last; ++t) {
-      void* out = t == 1 ? P(0) : (t == 2 ? P(1) : prv);
-      fstep(t, cur, prv, out);
-      prv = cur;
-      cur = out;
-      if (t % seg == 0) {
-        const int sg = t / seg;
-        TBK_CUDA(cudaMemcpyAsync(CK(sg, 0), prv, panel, cudaMemcpyDeviceToDevice, ctx->stream));
-        TBK_CUDA(cudaMemcpyAsync(CK(sg, 1), cur, panel, cudaMemcpyDeviceToDevice, ctx->stream));
-      }
-    }
-  }
-  if (jmax >= 0) {
-    init_b_panels<<<(unsigned)((op.n_rows * s + 255) / 256), 256, 0, ctx->stream>>>(
-        op.n_rows, s, atom_cl, d_seed, d_atom0, coefd, pmax, d_p, d_par, (float*)bcur, (float*)bprev);
-    post_launch(ctx, "init_b_panels");
-    int j = jmax;
-    for (int sg = nseg - 1; sg >= -1 && j >= 0; --sg) {
-      const int t0 = sg >= 0 ? 1 + seg * sg : 0;
-      const int t1 = sg >= 0 ? std::min(npm, t0 + seg - 1) : 0;
-      // y_{t0 - 1 + i} at Y(i); y_0 is the probe panel R0
-      auto Y = [&](int i) { return (sg == 0 && i == 0) ? R0 : P(i); };
-      if (sg >= 0) {
-        int t = t0;
-        if (sg > 0) {
-          TBK_CUDA(cudaMemcpyAsync(P(0), CK(sg, 1), panel, cudaMemcpyDeviceToDevice, ctx->stream));
-          fstep(t0, P(0), CK(sg, 0), P(1));
-          ++t;
-        }
-        for (; t <= t1; ++t) {
-          const int i = t - t0 + 1;
-          fstep(t, Y(i - 1), t >= 2 ? Y(i - 2) : nullptr, P(i));
-        }
-      }
-      for (; j >= t0; --j) {
-        HOp o = op;
-        o.n_atoms = active(j);
-        if (o.n_atoms > 0)
-          launch_fused(ctx, o, bcur, bprev, j >= 1 ? bprev : nullptr, j >= 1 ? Y(j - t0 + 1) : nullptr,
-                       make_float4(0.f, 0.f, 0.f, 0.f), 0, s, j == 0 ? 1.0 : 2.0, Gacc, err, br,
-                       c_tab + (size_t)j * ncl, nullptr, nullptr);
-        if (j >= 1) std::swap(bcur, bprev);
-      }
-    }
-  }
+  adjoint_doubling(ctx, op, 0, s, 0, nullptr, nullptr, 0, max_panel_bytes, Gacc, err, false, &bt);
   // ---- G (symmetrised, per-cluster scale) and forces on the merged pattern ----
   int32_t* tr = (int32_t*)scratch(ctx, WS_TRANSPOSE, sizeof(int32_t) * (size_t)bo);
   launch_transpose_map(ctx, op.n_atoms, op.row_ptr, op.col, tr, err);

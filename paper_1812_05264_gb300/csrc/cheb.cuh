@@ -2,6 +2,9 @@
 // recurrence kernels read, and the fused block-SpMM step shared by the forward recurrence
 // (moments) and the adjoint (Clenshaw) passes.
 #pragma once
+#include <functional>
+#include <vector>
+
 #include "common.cuh"
 
 namespace tbk {
@@ -76,5 +79,24 @@ size_t mapped_h_bytes(const tbk_bsr* H, int prec);
 HOp prepare_hop_into(tbk_ctx* ctx, const tbk_bsr* H, double emin, double emax, int prec, void* dst);
 void launch_moment_reduction(tbk_ctx* ctx, const double* partials, int nctas, int K, int order, int s,
                              int64_t n_rows, int direct, double* sums, double* moments, int* flag);
+
+// ---- the adjoint of the doubled moments (adjoint.cu) ----
+// A batch of clusters merged into one block-diagonal operator, sorted by K = order/2 descending:
+// step t runs on the atoms of the clusters with K >= t (a prefix of the merged rows).
+struct AdjBatch {
+  BatchRows br;              // atom -> cluster, per-cluster probe seed and first atom (device)
+  std::vector<int> K;        // per sorted cluster
+  std::vector<int> n_at;     // atoms per sorted cluster
+  const float4* cft = nullptr;  // device, (K_max + 1) x n_clusters: (probe, y_k, y_{k-1}, y_{k+1})
+                                // coefficients of the source g_k of step k, zero past K_c
+};
+// Gacc += the unscaled gradient sum_k 2 y_k ybar_{k+1}^T + y_0 ybar_1^T on the pattern (scale 2/W
+// afterwards).  Single system: get_coefs() returns c_0 .. c_{p-1} once y_1 .. y_{p/2} exist
+// (with partials != NULL those forward steps also write their moment partial sums).  Batch: bt
+// gives the per-cluster tables; p, get_coefs and partials are unused.
+void adjoint_doubling(tbk_ctx* ctx, const HOp& op, uint64_t probe_seed, int s, int p,
+                      const std::function<std::vector<double>()>& get_coefs, double* partials, int nctas,
+                      int64_t max_panel_bytes, double* Gacc, int* err, bool windowed, const AdjBatch* bt);
+void launch_batch_probe_panel(tbk_ctx* ctx, const HOp& op, const BatchRows& br, int s, void* out);
 
 }  // namespace tbk

@@ -115,3 +115,31 @@ def test_batched_forces_vs_oracle(api, ctx):
     for (wk, H, e0, e1, p), (rp, col, est), F in zip(b, ests, Fs):
         _, Fo = oracle_estimator_forces(wk, rp, col, est, e0, e1, p)
         assert np.abs(F.cpu().numpy() - Fo).max() < 1e-3
+
+
+def test_batched_adjoint_segments_and_odd_orders(api, ctx):
+    """Orders of both parities (so the clusters join the backward sweep at different steps), and
+    a panel budget that forces segment replays: the replayed sweep gives the same bits."""
+    sizes, kTs = [24, 41, 16], [0.5, 0.5, 0.1]
+    b = _batch(api, ctx, sizes, kTs)
+    orders = [61, 48, 7]
+    model = api.Solver(b[0][0], ctx).model
+    mus = []
+    for (wk, H, e0, e1, _), p in zip(b, orders):
+        m = api.chebyshev_moments(ctx, H, e0, e1, wk.probe_seed, 128, p)
+        mus.append(api.fermi_level(ctx, m, e0, e1, wk.n_electrons, wk.kT)[0])
+    pos = [torch.as_tensor(x[0].positions, dtype=torch.float64, device="cuda") for x in b]
+    args = (ctx, [x[1] for x in b], model, pos, [x[2] for x in b], [x[3] for x in b],
+            [x[0].probe_seed for x in b], 128, orders, mus, kTs)
+    G1, F1 = api.batched_density_and_forces(*args, want_G=True)
+    panel = sum(sizes) * 9 * 128 * 4
+    # all stored: K_max + 5 panels; the replay plan for K_max = 30 needs 2 x 4 + 8 + 5 = 21
+    G2, F2 = api.batched_density_and_forces(*args, want_G=True, max_panel_bytes=24 * panel)
+    for g1, g2, f1, f2 in zip(G1, G2, F1, F2):
+        assert torch.equal(g1, g2) and torch.equal(f1, f2)
+    for (wk, H, e0, e1, _), p, mu, G, F, ps in zip(b, orders, mus, G1, F1, pos):
+        Gs, Fs = api.density_and_forces(ctx, H, model, ps, None, e0, e1, wk.probe_seed, 128, p, mu,
+                                        wk.kT, False, False, want_G=True)
+        gmax = Gs.abs().max().item()
+        assert torch.allclose(G, Gs, rtol=0, atol=2e-5 * gmax)
+        assert torch.allclose(F, Fs, rtol=0, atol=1e-4)

@@ -388,16 +388,19 @@ def test_energies_and_forces_rejects_bad_arguments(api, ctx):
 def test_kernel_timer_counts_the_recurrence_launches(api, ctx):
     wk = small_fcc(40, n_probes=128)
     sv, pos, res = _gpu_run(api, ctx, wk, 30, fp64=False)
-    ctx.time_kernels("step", "backward", "window")
-    api.chebyshev_moments(ctx, res.H, res.emin, res.emax, wk.probe_seed, 128, 30, False)
-    api.density_and_forces(ctx, res.H, sv.model, pos, None, res.emin, res.emax, wk.probe_seed, 128,
-                           30, res.mu, wk.kT, False, False)
-    n = {f: ctx.kernel_time(f)[1] for f in ("step", "backward", "window")}
-    ms = {f: ctx.kernel_time(f)[0] for f in ("step", "backward", "window")}
-    ctx.time_kernels()
-    # K = 15: 15 moment steps + 15 forward steps, 14 adjoint steps, windows 1..4 .. 13..14 and y_0
-    assert n == {"step": 30, "backward": 14, "window": 5}, n
-    assert all(v > 0.0 for v in ms.values())
+    fams = ("step", "backward", "window")
+    # K = 15: 15 moment steps + 15 forward steps; fused: 14 adjoint steps and the y_0 outer
+    # product; windowed: 14 adjoint steps, windows 1..4 .. 13..14 and y_0
+    for windowed, want in ((False, {"step": 30, "backward": 15, "window": 0}),
+                           (True, {"step": 30, "backward": 14, "window": 5})):
+        ctx.time_kernels(*fams)
+        api.chebyshev_moments(ctx, res.H, res.emin, res.emax, wk.probe_seed, 128, 30, False)
+        api.density_and_forces(ctx, res.H, sv.model, pos, None, res.emin, res.emax, wk.probe_seed,
+                               128, 30, res.mu, wk.kT, False, False, windowed=windowed)
+        got = {f: ctx.kernel_time(f) for f in fams}
+        ctx.time_kernels()
+        assert {f: n for f, (ms, n) in got.items()} == want, got
+        assert all(ms > 0.0 for ms, n in got.values() if n > 0)
 
 
 @pytest.mark.parametrize("s,p", [(128, 61), (512, 40)])

@@ -209,8 +209,8 @@ def traffic_from_profile(kernel_file: str, src_name: str):
         return None
     vals = {}
     for ln in open(path):
-        if ":" in ln and ln.strip().startswith("- "):
-            k, v = ln.strip()[2:].split(":", 1)
+        if ": " in ln and ln.strip().startswith("- "):
+            k, v = ln.strip()[2:].split(": ", 1)
             vals[k.strip()] = v.strip()
     if vals.get(f"{src_name} sha256[:16]") != sha:
         return None
@@ -222,6 +222,7 @@ def traffic_from_profile(kernel_file: str, src_name: str):
 
 # FP32 FMA issue of one GB300: 152 SMs x 128 lanes x 2 flops per cycle at the maximum SM clock
 SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+L2_BYTES = 126 * 2 ** 20
 
 
 def run_ours(args, rank, world):
@@ -254,7 +255,7 @@ def run_ours(args, rank, world):
         g = api.build_neighbors(ctx, p_dev, wk.cutoff, box)
         H = api.assemble_H(ctx, solver.model, p_dev, g, box)
         emin, emax = api.spectral_bounds(ctx, H)
-        p = wk.order or order_rule(emax - emin, wk.kT)
+        p = args.order or wk.order or order_rule(emax - emin, wk.kT)
         _, obs, _, F = api.energies_and_forces(
             ctx, H, solver.model if solver.model.is_sk else None, p_dev, box, emin, emax,
             wk.probe_seed, wk.n_probes, p, wk.n_electrons, wk.kT, wk.jackson, fp64,
@@ -329,14 +330,17 @@ def run_ours(args, rank, world):
     nwin = (K - 1 + 3) // 4 + 1 if K >= 1 else 0
     # algorithmic bytes and flops (2 per FMA) of each family over the timed steps
     hb, blk = nnzb * B2 * esz, 2 * nnzb * B2 * wk.n_probes
+    windowed = args.adjoint == "windowed"
     alg = {
         # y_{k+1} = 2 H^ y_k - y_{k-1}: reads y_k, y_{k-1}, the H^ blocks, writes y_{k+1}
         "step": (lambda n: n * (3 * panel + hb), lambda n: n * blk, "cheb_step_bulk",
                  "cheb_step_bulk_fcc10000.md", "recurrence.cu"),
         # ybar_k = g_k + 2 H^ ybar_{k+1} - ybar_{k+2}: reads ybar_{k+1}, ybar_{k+2}, y_k, y_{k-1},
-        # y_{k+1}, the H^ blocks, writes ybar_k
-        "backward": (lambda n: n * (6 * panel + hb), lambda n: n * blk, "clenshaw_sddmm_bulk",
-                     "clenshaw_bulk_fcc10000.md", "adjoint.cu"),
+        # y_{k+1}, the H^ blocks, writes ybar_k; fused: and G += 2 y_k ybar_{k+1}^T (the same
+        # tiles, as many FMAs again, the FP64 accumulator read and written once)
+        "backward": (lambda n: n * (6 * panel + hb + (0 if windowed else nnzb * B2 * 16)),
+                     lambda n: n * blk * (1 if windowed else 2), "clenshaw_sddmm_bulk",
+                     "clenshaw_sddmm_bulk_fcc10000.md", "adjoint.cu"),
         # G += sum_j y_j ybar_{j+1}^T (j = 0 .. K-1, K pairs a step): reads both panels of every
         # pair, reads and writes the FP64 accumulator once per window
         "window": (lambda n: args.steps * (K * 2 * panel + nwin * nnzb * B2 * 16),
@@ -373,9 +377,12 @@ def run_ours(args, rank, world):
         "config": {"workload": wk.name, "n_atoms": wk.n_atoms, "orbitals": n_rows,
                    "probes": wk.n_probes, "order_p": p, "kT": wk.kT, "nnzb": nnzb,
                    "moments": "FP64", "recurrence": "FP64" if fp64 else "FP32",
-                   "l2": "panels (%.0f MB each) larger than L2" % (n_rows * wk.n_probes * esz / 1e6),
+                   "l2": ("panels (%.0f MB each) larger than L2" if panel > L2_BYTES else
+                          "panels (%.0f MB each) fit in L2: an L2-resident workload, not flushed")
+                         % (panel / 1e6),
                    "parallelism": f"replicas x{world}", "seeds": [5264, wk.probe_seed],
-                   "adjoint": args.adjoint},
+                   "adjoint": args.adjoint,
+                   "order_rule": "fixed by --order (profiling run)" if args.order else "exp(-6.4 p kT/W) = 1e-7"},
         "e2e": {"value": units * world / (e_med / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
@@ -408,7 +415,7 @@ def moments_only(args, ctx, solver, wk, pos):
     g = api.build_neighbors(ctx, pos, wk.cutoff, solver.box)
     H = api.assemble_H(ctx, solver.model, pos, g, solver.box)
     emin, emax = api.spectral_bounds(ctx, H)
-    p = args.order
+    p = args.order or 64
     for _ in range(args.warmup):
         api.chebyshev_moments(ctx, H, emin, emax, wk.probe_seed, wk.n_probes, p, not wk.mixed)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -458,7 +465,7 @@ def adjoint_only(args, ctx, solver, wk, pos):
     g = api.build_neighbors(ctx, pos, wk.cutoff, solver.box)
     H = api.assemble_H(ctx, solver.model, pos, g, solver.box)
     emin, emax = api.spectral_bounds(ctx, H)
-    p = args.order
+    p = args.order or 64
     mom = api.chebyshev_moments(ctx, H, emin, emax, wk.probe_seed, wk.n_probes, p, not wk.mixed)
     mu = api.fermi_level(ctx, mom, emin, emax, wk.n_electrons, wk.kT)[0]
     args_ = (ctx, H, solver.model, pos, solver.box, emin, emax, wk.probe_seed, wk.n_probes, p, mu,
@@ -600,7 +607,9 @@ def main():
                     help="time the mixed path against the plain FP64 GPU path (same p, probes)")
     ap.add_argument("--no-clocks", action="store_true",
                     help="do not run the nvidia-smi clock sampler (for runs under a profiler)")
-    ap.add_argument("--order", type=int, default=64, help="order for --only-moments / --only-adjoint")
+    ap.add_argument("--order", type=int, default=None,
+                    help="fixed Chebyshev order (default: the error rule; 64 for --only-moments / "
+                         "--only-adjoint); a reduced order is for profiler runs, not bench lines")
     ap.add_argument("--atom-order", default="radial", choices=["radial", "morton"],
                     help="listing order of the fcc10k atoms (same cluster)")
     ap.add_argument("--adjoint", default="fused", choices=["fused", "windowed"],

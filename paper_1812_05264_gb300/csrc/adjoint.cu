@@ -73,9 +73,10 @@ sddmm_kernel(int n_atoms, const int32_t* __restrict__ row_ptr, const int32_t* __
 //   Gacc_ab += w sum_probes y_j[a] b_{j+1}[b]^T   for every neighbour block (a, b)
 // The neighbour tiles b_{j+1}[b] and blocks H^_ab stream through a D-stage ring as in the
 // forward step; the own-row tile y_j[a] (or the probe block when j = 0) is staged once per task.
-// Each consumer warp owns quadrant(s) of the 9x9 outer product (rows/cols split 5 + 4): its 32
-// lanes cover interleaved 4-probe groups, and a butterfly reduce-scatter over the lanes leaves
-// one entry per lane, added to the FP64 accumulator (one CTA owns each block: no atomics).
+// The 9x9 outer product of each tile is split into three groups of 3 rows, each taken by one
+// consumer warp (in turn, so the load stays even): its 32 lanes cover interleaved 4-probe
+// groups, and a butterfly reduce-scatter over the lanes leaves one entry per lane, added to the
+// FP64 accumulator (one CTA owns each block, so each entry has one writer per launch).
 
 template <int CW, bool SD = true>
 struct SdCfg {
@@ -103,60 +104,49 @@ __device__ __forceinline__ void butterfly32(float (&v)[32], int lane) {
   }
 }
 
-// Quadrant q of the 9x9 outer product sum_p Y[i][p] X[l][p] over this warp's probes: rows
-// I0.. and columns L0.. with I0, L0 in {0, 5}; one 5x5 code path for all quadrants (rows and
-// columns past 8 are clamped to 8 and their results dropped).
+// Rows 3g .. 3g+2 of the 9x9 outer product sum_p Y[i][p] X[l][p] over all P probes (lanes cover
+// interleaved 4-probe groups): 27 entries, reduced over the lanes by one butterfly and added to
+// the FP64 accumulator (one lane per entry).
 template <int P>
-__device__ __forceinline__ void sddmm_quadrant(int q, const float* Y, const float* X, bool y_probe,
-                                               uint64_t seed, int64_t rloc, int lane, int64_t k,
-                                               double w, double* __restrict__ Gacc) {
-  const int I0 = (q >> 1) * 5, L0 = (q & 1) * 5;
-  int ri[5], rl[5];
+__device__ __forceinline__ void sddmm_rows3(int g, const float* Y, const float* X, bool y_probe,
+                                            uint64_t seed, int64_t rloc, int lane, int64_t k,
+                                            double w, double* __restrict__ Gacc) {
+  float2 v2[27];  // (even probe, odd probe) partial sums of entry (i - 3g) * 9 + l
 #pragma unroll
-  for (int t = 0; t < 5; ++t) {
-    ri[t] = min(I0 + t, 8);
-    rl[t] = min(L0 + t, 8);
-  }
-  float2 v2[25];  // (even probe, odd probe) partial sums of entry i * 5 + l
-#pragma unroll
-  for (int e = 0; e < 25; ++e) v2[e] = make_float2(0.f, 0.f);
+  for (int e = 0; e < 27; ++e) v2[e] = make_float2(0.f, 0.f);
 #pragma unroll 1
   for (int m = 0; m < P / 128; ++m) {
     const int pb = 4 * (lane + 32 * m);
-    float yv[5][4];
+    float yv[3][4];
 #pragma unroll
-    for (int i = 0; i < 5; ++i) {
+    for (int i = 0; i < 3; ++i) {
       if (y_probe) {
 #pragma unroll
-        for (int t = 0; t < 4; ++t) yv[i][t] = tbk_probe_sign(seed, rloc + ri[i], pb + t);
+        for (int t = 0; t < 4; ++t) yv[i][t] = tbk_probe_sign(seed, rloc + 3 * g + i, pb + t);
       } else {
-        const float4 u = *reinterpret_cast<const float4*>(Y + ri[i] * P + pb);
+        const float4 u = *reinterpret_cast<const float4*>(Y + (3 * g + i) * P + pb);
         yv[i][0] = u.x; yv[i][1] = u.y; yv[i][2] = u.z; yv[i][3] = u.w;
       }
     }
-    // one column row of X at a time keeps 4 of its values live instead of 20
 #pragma unroll
-    for (int l = 0; l < 5; ++l) {
-      const float4 u = *reinterpret_cast<const float4*>(X + rl[l] * P + pb);
+    for (int l = 0; l < 9; ++l) {
+      const float4 u = *reinterpret_cast<const float4*>(X + l * P + pb);
 #pragma unroll
-      for (int i = 0; i < 5; ++i) {
-        v2[i * 5 + l] = __ffma2_rn(make_float2(yv[i][0], yv[i][1]), make_float2(u.x, u.y), v2[i * 5 + l]);
-        v2[i * 5 + l] = __ffma2_rn(make_float2(yv[i][2], yv[i][3]), make_float2(u.z, u.w), v2[i * 5 + l]);
+      for (int i = 0; i < 3; ++i) {
+        v2[i * 9 + l] = __ffma2_rn(make_float2(yv[i][0], yv[i][1]), make_float2(u.x, u.y), v2[i * 9 + l]);
+        v2[i * 9 + l] = __ffma2_rn(make_float2(yv[i][2], yv[i][3]), make_float2(u.z, u.w), v2[i * 9 + l]);
       }
     }
   }
   float v[32];
 #pragma unroll
-  for (int e = 0; e < 32; ++e) v[e] = e < 25 ? v2[e].x + v2[e].y : 0.f;
+  for (int e = 0; e < 32; ++e) v[e] = e < 27 ? v2[e].x + v2[e].y : 0.f;
   butterfly32(v, lane);
-  const int i = I0 + lane / 5, l = L0 + lane % 5;
-  if (lane < 25 && i < 9 && l < 9)
+  if (lane < 27)
     // fire-and-forget reduction: one writer per entry and launch, so the sum stays deterministic
-    atomicAdd(Gacc + k * 81 + i * 9 + l, w * (double)v[0]);
+    atomicAdd(Gacc + k * 81 + 27 * g + lane, w * (double)v[0]);
 }
 
-// SD = false: the Clenshaw step alone (the outer products are left to sddmm_window); the own-row
-// tile y_j then streams through the ring like the other source terms.
 template <int CW, bool SD>
 __global__ void __launch_bounds__(32 * (CW + 1))
 clenshaw_sddmm_bulk(const int n_atoms, const int32_t* __restrict__ row_ptr,
@@ -297,8 +287,11 @@ clenshaw_sddmm_bulk(const int n_atoms, const int32_t* __restrict__ row_ptr,
       const float* X = reinterpret_cast<const float*>(base);
       if (has_out) spmm_tile_f2(X, reinterpret_cast<const float*>(base + C::XB), C::P, pl, acc);
       if constexpr (SD) {
-        for (int qd = warp; qd < 4; qd += CW)
-          sddmm_quadrant<C::P>(qd, Ys, X, y_probe, sd, rloc, lane, (int64_t)(k0 + q), w, Gacc);
+        // row group g of this tile goes to warp (q + g + 1) mod CW: with 4 warps one warp rests
+        // per tile, in turn
+        for (int g = 0; g < 3; ++g)
+          if ((q + g + 1) % CW == warp)
+            sddmm_rows3<C::P>(g, Ys, X, y_probe, sd, rloc, lane, (int64_t)(k0 + q), w, Gacc);
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(is_own ? own_empty : empty(st));

@@ -80,7 +80,7 @@ sddmm_kernel(int n_atoms, const int32_t* __restrict__ row_ptr, const int32_t* __
 
 template <int CW, bool SD = true>
 struct SdCfg {
-  static constexpr int D = SD ? 2 : 3;
+  static constexpr int D = SD ? 2 : 3;  // SD: 2 stages keep three CTAs within shared memory
   static constexpr int P = 128 * CW;
   static constexpr int XB = 9 * P * 4;
   static constexpr int HB = Layout<float, 9>::BS * 4;
@@ -111,9 +111,11 @@ template <int P>
 __device__ __forceinline__ void sddmm_rows3(int g, const float* Y, const float* X, bool y_probe,
                                             uint64_t seed, int64_t rloc, int lane, int64_t k,
                                             double w, double* __restrict__ Gacc) {
-  float2 v2[27];  // (even probe, odd probe) partial sums of entry (i - 3g) * 9 + l
+  // partial sums of entry (i - 3g) * 9 + l over this lane's probes; scalar accumulators keep the
+  // kernel at 128 registers, so that three CTAs fit per SM
+  float v1[27];
 #pragma unroll
-  for (int e = 0; e < 27; ++e) v2[e] = make_float2(0.f, 0.f);
+  for (int e = 0; e < 27; ++e) v1[e] = 0.f;
 #pragma unroll 1
   for (int m = 0; m < P / 128; ++m) {
     const int pb = 4 * (lane + 32 * m);
@@ -133,22 +135,28 @@ __device__ __forceinline__ void sddmm_rows3(int g, const float* Y, const float* 
       const float4 u = *reinterpret_cast<const float4*>(X + l * P + pb);
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
-        v2[i * 9 + l] = __ffma2_rn(make_float2(yv[i][0], yv[i][1]), make_float2(u.x, u.y), v2[i * 9 + l]);
-        v2[i * 9 + l] = __ffma2_rn(make_float2(yv[i][2], yv[i][3]), make_float2(u.z, u.w), v2[i * 9 + l]);
+        float t = v1[i * 9 + l];
+        t = fmaf(yv[i][0], u.x, t); t = fmaf(yv[i][1], u.y, t);
+        t = fmaf(yv[i][2], u.z, t); t = fmaf(yv[i][3], u.w, t);
+        v1[i * 9 + l] = t;
       }
     }
   }
   float v[32];
 #pragma unroll
-  for (int e = 0; e < 32; ++e) v[e] = e < 27 ? v2[e].x + v2[e].y : 0.f;
+  for (int e = 0; e < 32; ++e) v[e] = e < 27 ? v1[e] : 0.f;
   butterfly32(v, lane);
   if (lane < 27)
     // fire-and-forget reduction: one writer per entry and launch, so the sum stays deterministic
     atomicAdd(Gacc + k * 81 + 27 * g + lane, w * (double)v[0]);
 }
 
+// SD = false: the Clenshaw step alone (the outer products are left to sddmm_window); the own-row
+// tile y_j then streams through the ring like the other source terms.  SD = true: three CTAs of
+// four consumer warps per SM, whose interleaving hides the latency of the outer product's
+// reductions.
 template <int CW, bool SD>
-__global__ void __launch_bounds__(32 * (CW + 1))
+__global__ void __launch_bounds__(32 * (CW + 1), SD ? 3 : 1)
 clenshaw_sddmm_bulk(const int n_atoms, const int32_t* __restrict__ row_ptr,
                     const int32_t* __restrict__ col, const float* __restrict__ hv,
                     const float* __restrict__ bin, const float* bprev, float* bout,
@@ -271,8 +279,13 @@ clenshaw_sddmm_bulk(const int n_atoms, const int32_t* __restrict__ row_ptr,
     for (int i = 0; i < 5; ++i)
 #pragma unroll
       for (int v = 0; v < 4; ++v) acc[i][v] = make_float2(0.f, 0.f);
+    // position of the diagonal block in this row, found once per row by the whole warp
+    int q_own = -1;
+    for (int q = lane; q < k1 - k0; q += 32)
+      if (__ldg(col + k0 + q) == a) q_own = q;
+    q_own = __reduce_max_sync(0xffffffffu, q_own);
     for (int q = 0; q < k1 - k0; ++q) {
-      const bool is_own = __ldg(col + k0 + q) == a;
+      const bool is_own = q == q_own;
       const unsigned char* base;
       int st = 0;
       if (is_own) {

@@ -353,8 +353,14 @@ cheb_step_bulk(const int n_atoms, const int32_t* __restrict__ row_ptr, const int
     for (int i = 0; i < 5; ++i)
 #pragma unroll
       for (int v = 0; v < 4; ++v) acc[i][v] = make_float2(0.f, 0.f);
+    // position of the diagonal block in this row, found once per row by the whole warp
+    const int lane = threadIdx.x & 31;
+    int q_own = -1;
+    for (int q = lane; q < k1 - k0; q += 32)
+      if (__ldg(col + k0 + q) == a) q_own = q;
+    q_own = __reduce_max_sync(0xffffffffu, q_own);
     for (int q = 0; q < k1 - k0; ++q) {
-      const bool is_own = __ldg(col + k0 + q) == a;
+      const bool is_own = q == q_own;
       const unsigned char* base;
       int st = 0;
       if (is_own) {

@@ -165,27 +165,24 @@ clenshaw_sddmm_bulk(const int n_atoms, const int32_t* __restrict__ row_ptr,
                     const BatchRows batch, const float4* __restrict__ cf_cl,
                     const float* __restrict__ ym1, const float* __restrict__ yp1) {
   using C = SdCfg<CW, SD>;
-  constexpr int D = C::D;
+  // every tile, the diagonal one included, streams through a ring of R = D + 1 stages
+  constexpr int R = C::D + 1;
   extern __shared__ __align__(128) unsigned char smem[];
-  unsigned char* own = smem + D * C::SB;
-  float* Ys = reinterpret_cast<float*>(smem + (D + 1) * C::SB);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (D + 1) * C::SB + C::YB);
+  float* Ys = reinterpret_cast<float*>(smem + R * C::SB);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + R * C::SB + C::YB);
   const uint32_t bar0 = smem_u32(bars);
   auto full = [&](int i) { return bar0 + 8u * i; };
-  auto empty = [&](int i) { return bar0 + 8u * (D + i); };
-  const uint32_t own_full = bar0 + 8u * (2 * D), own_empty = bar0 + 8u * (2 * D + 1);
-  const uint32_t y_full = bar0 + 8u * (2 * D + 2), y_empty = bar0 + 8u * (2 * D + 3);
+  auto empty = [&](int i) { return bar0 + 8u * (R + i); };
+  const uint32_t y_full = bar0 + 8u * (2 * R), y_empty = bar0 + 8u * (2 * R + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const bool has_prev = bprev != nullptr, has_out = bout != nullptr;
   // y_tile: the own-row tile y_j is staged once per task for the outer products
   const bool y_probe = ypan == nullptr, y_tile = SD && !y_probe;
   if (threadIdx.x == 0) {
-    for (int i = 0; i < D; ++i) {
+    for (int i = 0; i < R; ++i) {
       mbar_init(full(i), 1);
       mbar_init(empty(i), CW);
     }
-    mbar_init(own_full, 1);
-    mbar_init(own_empty, CW);
     mbar_init(y_full, 1);
     mbar_init(y_empty, CW);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -208,7 +205,7 @@ clenshaw_sddmm_bulk(const int n_atoms, const int32_t* __restrict__ row_ptr,
   }
   if (warp == CW) {
     if (lane == 0) {
-      int it = 0, own_it = 0, y_it = 0;
+      int it = 0, y_it = 0;
       bool ok = true;
       for (int a = blockIdx.x; a < n_atoms && ok; a += gridDim.x) {
         const int k0 = __ldg(row_ptr + a), k1 = __ldg(row_ptr + a + 1);
@@ -226,21 +223,11 @@ clenshaw_sddmm_bulk(const int n_atoms, const int32_t* __restrict__ row_ptr,
           const bool is_prev = q >= nb;
           const float* extra = is_prev ? extra_src[q - nb] : nullptr;
           const int b = is_prev ? a : __ldg(col + k0 + q);
-          const bool is_own = !is_prev && b == a;
-          uint32_t dst, bar;
-          if (is_own) {
-            ok = mbar_wait(own_empty, (own_it & 1) ^ 1);
-            dst = smem_u32(own);
-            bar = own_full;
-            ++own_it;
-          } else {
-            const int st = it % D;
-            ok = mbar_wait(empty(st), ((it / D) & 1) ^ 1);
-            dst = smem_u32(smem + st * C::SB);
-            bar = full(st);
-            ++it;
-          }
+          const int st = it % R;
+          ok = mbar_wait(empty(st), ((it / R) & 1) ^ 1);
           if (!ok) break;
+          const uint32_t dst = smem_u32(smem + st * C::SB), bar = full(st);
+          ++it;
           const float* src = (is_prev ? extra : bin) + (int64_t)9 * b * s;
           mbar_expect_tx(bar, C::XB + (is_prev ? 0 : C::HB));
           bulk_g2s(dst, src, C::XB, bar);
@@ -248,14 +235,16 @@ clenshaw_sddmm_bulk(const int n_atoms, const int32_t* __restrict__ row_ptr,
         }
       }
       if (!ok) {
+        // let the copies in flight land before the CTA exits
         atomicOr(err, 2);
-        for (int j = (it > D ? it - D : 0); j < it; ++j) mbar_wait(full(j % D), (j / D) & 1);
+        for (int j = (it > R ? it - R : 0); j < it; ++j) mbar_wait(full(j % R), (j / R) & 1);
+        if (y_tile && y_it > 0) mbar_wait(y_full, (y_it - 1) & 1);
       }
     }
     return;
   }
 
-  int it = 0, own_it = 0, y_it = 0;
+  int it = 0, y_it = 0;
   bool ok = true;
   const int pl = 4 * threadIdx.x;
   for (int a = blockIdx.x; a < n_atoms && ok; a += gridDim.x) {
@@ -279,24 +268,11 @@ clenshaw_sddmm_bulk(const int n_atoms, const int32_t* __restrict__ row_ptr,
     for (int i = 0; i < 5; ++i)
 #pragma unroll
       for (int v = 0; v < 4; ++v) acc[i][v] = make_float2(0.f, 0.f);
-    // position of the diagonal block in this row, found once per row by the whole warp
-    int q_own = -1;
-    for (int q = lane; q < k1 - k0; q += 32)
-      if (__ldg(col + k0 + q) == a) q_own = q;
-    q_own = __reduce_max_sync(0xffffffffu, q_own);
     for (int q = 0; q < k1 - k0; ++q) {
-      const bool is_own = q == q_own;
-      const unsigned char* base;
-      int st = 0;
-      if (is_own) {
-        ok = mbar_wait(own_full, own_it & 1);
-        base = own;
-      } else {
-        st = it % D;
-        ok = mbar_wait(full(st), (it / D) & 1);
-        base = smem + st * C::SB;
-      }
+      const int st = it % R;
+      ok = mbar_wait(full(st), (it / R) & 1);
       if (!ok) break;
+      const unsigned char* base = smem + st * C::SB;
       const float* X = reinterpret_cast<const float*>(base);
       if (has_out) spmm_tile_f2(X, reinterpret_cast<const float*>(base + C::XB), C::P, pl, acc);
       if constexpr (SD) {
@@ -307,8 +283,8 @@ clenshaw_sddmm_bulk(const int n_atoms, const int32_t* __restrict__ row_ptr,
             sddmm_rows3<C::P>(g, Ys, X, y_probe, sd, rloc, lane, (int64_t)(k0 + q), w, Gacc);
       }
       __syncwarp();
-      if (lane == 0) mbar_arrive(is_own ? own_empty : empty(st));
-      if (is_own) ++own_it; else ++it;
+      if (lane == 0) mbar_arrive(empty(st));
+      ++it;
     }
     if (!ok) break;
     if (!has_out) {
@@ -340,8 +316,8 @@ clenshaw_sddmm_bulk(const int n_atoms, const int32_t* __restrict__ row_ptr,
       }
     }
     for (int e = 0; e < n_extra; ++e) {
-      const int st = it % D;
-      ok = mbar_wait(full(st), (it / D) & 1);
+      const int st = it % R;
+      ok = mbar_wait(full(st), (it / R) & 1);
       if (!ok) break;
       const float* X = reinterpret_cast<const float*>(smem + st * C::SB);
       const int kd = extra_kind[e];

@@ -263,11 +263,9 @@ clenshaw_sddmm_bulk(const int n_atoms, const int32_t* __restrict__ row_ptr,
       ok = mbar_wait(y_full, y_it & 1);
       if (!ok) break;
     }
-    float2 acc[5][4];  // rows (2 ip, 2 ip + 1) x probe v
+    float2 acc[9][2];  // row i x probes (2h, 2h + 1)
 #pragma unroll
-    for (int i = 0; i < 5; ++i)
-#pragma unroll
-      for (int v = 0; v < 4; ++v) acc[i][v] = make_float2(0.f, 0.f);
+    for (int i = 0; i < 9; ++i) acc[i][0] = acc[i][1] = make_float2(0.f, 0.f);
     for (int q = 0; q < k1 - k0; ++q) {
       const int st = it % R;
       ok = mbar_wait(full(st), (it / R) & 1);
@@ -300,7 +298,7 @@ clenshaw_sddmm_bulk(const int n_atoms, const int32_t* __restrict__ row_ptr,
 #pragma unroll
     for (int i = 0; i < 9; ++i)
 #pragma unroll
-      for (int v = 0; v < 4; ++v) yo[i][v] = 2.f * ((i & 1) ? acc[i >> 1][v].y : acc[i >> 1][v].x);
+      for (int v = 0; v < 4; ++v) yo[i][v] = 2.f * ((v & 1) ? acc[i][v >> 1].y : acc[i][v >> 1].x);
     if (cfa.x != 0.f) {
 #pragma unroll
       for (int i = 0; i < 9; ++i)

@@ -44,16 +44,17 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
 }
 
 
-// One neighbour tile of the FP32 block product with packed f32x2 FMAs:
-//   acc[ip][v] += (H^[2ip][l], H^[2ip+1][l]) * x[l][v]   for l = 0..8,
+// One neighbour tile of the FP32 block product with packed f32x2 FMAs over probe pairs:
+//   acc[i][h] += H^[i][l] * (x[l][2h], x[l][2h+1])   for l = 0..8,
 // X: 9 x P tile in shared memory, Hs: column-major block (columns padded to 12 floats), pl: the
-// thread's first probe.  Every accumulator sums l = 0..8 in order (same rounding as scalar FMAs).
+// thread's first probe (4 probes: h = 0, 1).  Every accumulator sums l = 0..8 in order (same
+// rounding as scalar FMAs); the 9 rows need 18 packed FMAs per column, no padding row.
 __device__ __forceinline__ void spmm_tile_f2(const float* X, const float* Hs, int P, int pl,
-                                             float2 (&acc)[5][4]) {
+                                             float2 (&acc)[9][2]) {
 #pragma unroll
   for (int l = 0; l < 9; ++l) {
     const float4 t = *reinterpret_cast<const float4*>(X + l * P + pl);
-    const float xv[4] = {t.x, t.y, t.z, t.w};
+    const float2 x01 = make_float2(t.x, t.y), x23 = make_float2(t.z, t.w);
     float hc[12];
 #pragma unroll
     for (int j = 0; j < 12; j += 4) {
@@ -61,10 +62,10 @@ __device__ __forceinline__ void spmm_tile_f2(const float* X, const float* Hs, in
       hc[j] = u.x; hc[j + 1] = u.y; hc[j + 2] = u.z; hc[j + 3] = u.w;
     }
 #pragma unroll
-    for (int ip = 0; ip < 5; ++ip) {
-      const float2 h2 = make_float2(hc[2 * ip], hc[2 * ip + 1]);
-#pragma unroll
-      for (int v = 0; v < 4; ++v) acc[ip][v] = __ffma2_rn(h2, make_float2(xv[v], xv[v]), acc[ip][v]);
+    for (int i = 0; i < 9; ++i) {
+      const float2 h2 = make_float2(hc[i], hc[i]);
+      acc[i][0] = __ffma2_rn(h2, x01, acc[i][0]);
+      acc[i][1] = __ffma2_rn(h2, x23, acc[i][1]);
     }
   }
 }

@@ -348,11 +348,9 @@ cheb_step_bulk(const int n_atoms, const int32_t* __restrict__ row_ptr, const int
     const int a = task / n_chunks, ch = task - a * n_chunks;
     const int k0 = __ldg(row_ptr + a), k1 = __ldg(row_ptr + a + 1);
     const int pl = 4 * threadIdx.x;  // probe offset inside the chunk
-    float2 acc[5][4];  // acc[ip][v] = rows (2 ip, 2 ip + 1) for probe v; row 9 is padding
+    float2 acc[9][2];  // acc[i][h] = row i for probes (2h, 2h + 1)
 #pragma unroll
-    for (int i = 0; i < 5; ++i)
-#pragma unroll
-      for (int v = 0; v < 4; ++v) acc[i][v] = make_float2(0.f, 0.f);
+    for (int i = 0; i < 9; ++i) acc[i][0] = acc[i][1] = make_float2(0.f, 0.f);
     // position of the diagonal block in this row, found once per row by the whole warp
     const int lane = threadIdx.x & 31;
     int q_own = -1;
@@ -413,7 +411,7 @@ cheb_step_bulk(const int n_atoms, const int32_t* __restrict__ row_ptr, const int
       const int64_t row = (int64_t)9 * a + i;
       float yo[4], r[4];
 #pragma unroll
-      for (int v = 0; v < 4; ++v) yo[v] = alpha * ((i & 1) ? acc[i >> 1][v].y : acc[i >> 1][v].x);
+      for (int v = 0; v < 4; ++v) yo[v] = alpha * ((v & 1) ? acc[i][v >> 1].y : acc[i][v >> 1].x);
       if (c_r != 0.f || direct) {
 #pragma unroll
         for (int v = 0; v < 4; ++v) r[v] = tbk_probe_sign(sd, rloc + i, p0 + v);

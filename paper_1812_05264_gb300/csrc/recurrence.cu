@@ -247,10 +247,10 @@ cheb_step_kernel(const int n_atoms, const int32_t* __restrict__ row_ptr,
 // CTA = CW consumer warps + 1 producer warp.  A task is one block row a and a chunk of
 // P = 128 CW probes (each consumer thread owns 4 consecutive probes).  The producer streams, for
 // every neighbour block k = (a, b) of the task, the 9 x P tile of y_in rows 9b..9b+8 and the
-// block H^_ab through a D-stage shared-memory ring with cp.async.bulk copies completing on
-// mbarriers; the diagonal block's tile goes to a separate "own" buffer that stays until the
-// epilogue (it is y_in of the row itself, needed for the moment sum), and the y_prev tile of
-// the row is streamed last.  Every wait is bounded: on expiry the CTA raises *err = 2 and leaves
+// block H^_ab through a (D + 1)-stage shared-memory ring with cp.async.bulk copies completing on
+// mbarriers, and the y_prev tile of the row last.  The row's own y_in values, needed for the
+// moment sum, are read back from global memory in the epilogue (the tile was just copied, so
+// they are normally in L2).  Every wait is bounded: on expiry the CTA raises *err = 2 and leaves
 // the loop, and the producer waits (bounded) for the copies it issued before returning.
 
 template <int CW, int D>
@@ -271,25 +271,24 @@ cheb_step_bulk(const int n_atoms, const int32_t* __restrict__ row_ptr, const int
                const int direct, double* __restrict__ partials, int* __restrict__ err,
                const BatchRows batch, const int per_task) {
   using C = BulkCfg<CW, D>;
+  // every tile, the diagonal one included, streams through a ring of R = D + 1 stages; the
+  // epilogue reads the row's own y_in values (for the moment partials) from global memory
+  constexpr int R = D + 1;
   extern __shared__ __align__(128) unsigned char smem[];
-  unsigned char* own = smem + D * C::SB;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (D + 1) * C::SB);
-  // bars: full[0..D), empty[D..2D), own_full = 2D, own_empty = 2D + 1
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + R * C::SB);
+  // bars: full[0..R), empty[R..2R)
   const uint32_t bar0 = smem_u32(bars);
   auto full = [&](int i) { return bar0 + 8u * i; };
-  auto empty = [&](int i) { return bar0 + 8u * (D + i); };
-  const uint32_t own_full = bar0 + 8u * (2 * D), own_empty = bar0 + 8u * (2 * D + 1);
+  auto empty = [&](int i) { return bar0 + 8u * (R + i); };
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n_chunks = s / C::P;
   const int n_tasks = n_atoms * n_chunks;
   const bool has_prev = yprev != nullptr;
   if (threadIdx.x == 0) {
-    for (int i = 0; i < D; ++i) {
+    for (int i = 0; i < R; ++i) {
       mbar_init(full(i), 1);
       mbar_init(empty(i), CW);
     }
-    mbar_init(own_full, 1);
-    mbar_init(own_empty, CW);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
@@ -297,7 +296,7 @@ cheb_step_bulk(const int n_atoms, const int32_t* __restrict__ row_ptr, const int
   if (warp == CW) {
     // ---------------- producer ----------------
     if (lane == 0) {
-      int it = 0, own_it = 0;
+      int it = 0;
       bool ok = true;
       for (int task = blockIdx.x; task < n_tasks && ok; task += gridDim.x) {
         const int a = task / n_chunks, ch = task - a * n_chunks;
@@ -306,21 +305,11 @@ cheb_step_bulk(const int n_atoms, const int32_t* __restrict__ row_ptr, const int
         for (int q = 0; q < nt && ok; ++q) {
           const bool is_prev = q == k1 - k0;
           const int b = is_prev ? a : __ldg(col + k0 + q);
-          const bool is_own = !is_prev && b == a;
-          uint32_t dst, bar;
-          if (is_own) {
-            ok = mbar_wait(own_empty, (own_it & 1) ^ 1);
-            dst = smem_u32(own);
-            bar = own_full;
-            ++own_it;
-          } else {
-            const int st = it % D;
-            ok = mbar_wait(empty(st), ((it / D) & 1) ^ 1);
-            dst = smem_u32(smem + st * C::SB);
-            bar = full(st);
-            ++it;
-          }
+          const int st = it % R;
+          ok = mbar_wait(empty(st), ((it / R) & 1) ^ 1);
           if (!ok) break;
+          const uint32_t dst = smem_u32(smem + st * C::SB), bar = full(st);
+          ++it;
           const float* src = (is_prev ? yprev : yin) + (int64_t)9 * b * s + (int64_t)ch * C::P;
           mbar_expect_tx(bar, C::XB + (is_prev ? 0 : C::HB));
           if (C::P == s) {
@@ -334,7 +323,7 @@ cheb_step_bulk(const int n_atoms, const int32_t* __restrict__ row_ptr, const int
       if (!ok) {
         atomicOr(err, 2);
         // wait (bounded) for copies still in flight into the ring before leaving
-        for (int j = (it > D ? it - D : 0); j < it; ++j) mbar_wait(full(j % D), (j / D) & 1);
+        for (int j = (it > R ? it - R : 0); j < it; ++j) mbar_wait(full(j % R), (j / R) & 1);
       }
     }
     return;
@@ -342,7 +331,7 @@ cheb_step_bulk(const int n_atoms, const int32_t* __restrict__ row_ptr, const int
 
   // ---------------- consumers ----------------
   double sum0 = 0.0, sum1 = 0.0;
-  int it = 0, own_it = 0;
+  int it = 0;
   bool ok = true;
   for (int task = blockIdx.x; task < n_tasks && ok; task += gridDim.x) {
     const int a = task / n_chunks, ch = task - a * n_chunks;
@@ -351,40 +340,24 @@ cheb_step_bulk(const int n_atoms, const int32_t* __restrict__ row_ptr, const int
     float2 acc[9][2];  // acc[i][h] = row i for probes (2h, 2h + 1)
 #pragma unroll
     for (int i = 0; i < 9; ++i) acc[i][0] = acc[i][1] = make_float2(0.f, 0.f);
-    // position of the diagonal block in this row, found once per row by the whole warp
-    const int lane = threadIdx.x & 31;
-    int q_own = -1;
-    for (int q = lane; q < k1 - k0; q += 32)
-      if (__ldg(col + k0 + q) == a) q_own = q;
-    q_own = __reduce_max_sync(0xffffffffu, q_own);
     for (int q = 0; q < k1 - k0; ++q) {
-      const bool is_own = q == q_own;
-      const unsigned char* base;
-      int st = 0;
-      if (is_own) {
-        ok = mbar_wait(own_full, own_it & 1);
-        base = own;
-      } else {
-        st = it % D;
-        ok = mbar_wait(full(st), (it / D) & 1);
-        base = smem + st * C::SB;
-      }
+      const int st = it % R;
+      ok = mbar_wait(full(st), (it / R) & 1);
       if (!ok) break;
+      const unsigned char* base = smem + st * C::SB;
       const float* X = reinterpret_cast<const float*>(base);
       const float* Hs = reinterpret_cast<const float*>(base + C::XB);
       spmm_tile_f2(X, Hs, C::P, pl, acc);
-      if (!is_own) {
-        __syncwarp();
-        if (lane == 0) mbar_arrive(empty(st));
-        ++it;
-      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(empty(st));
+      ++it;
     }
     if (!ok) break;
     // previous panel tile of this row (streamed last)
     float yp[9][4];
     if (has_prev) {
-      const int st = it % D;
-      ok = mbar_wait(full(st), (it / D) & 1);
+      const int st = it % R;
+      ok = mbar_wait(full(st), (it / R) & 1);
       if (!ok) break;
       const float* X = reinterpret_cast<const float*>(smem + st * C::SB);
 #pragma unroll
@@ -397,7 +370,6 @@ cheb_step_bulk(const int n_atoms, const int32_t* __restrict__ row_ptr, const int
       ++it;
     }
     // epilogue: y_out = alpha acc + c_r r - y_prev, moment partial sums
-    const float* Y = reinterpret_cast<const float*>(own);
     const int p0 = ch * C::P + pl;
     uint64_t sd = seed;          // probe stream and row index within the cluster
     int64_t rloc = (int64_t)9 * a;
@@ -431,7 +403,7 @@ cheb_step_bulk(const int n_atoms, const int32_t* __restrict__ row_ptr, const int
 #pragma unroll
           for (int v = 0; v < 4; ++v) xin[v] = r[v];
         } else {
-          const float4 t = *reinterpret_cast<const float4*>(Y + i * C::P + pl);
+          const float4 t = __ldg(reinterpret_cast<const float4*>(yin + row * s + p0));
           xin[0] = t.x; xin[1] = t.y; xin[2] = t.z; xin[3] = t.w;
         }
         float q0 = 0.f, q1 = 0.f;
@@ -444,9 +416,6 @@ cheb_step_bulk(const int n_atoms, const int32_t* __restrict__ row_ptr, const int
         sum1 += (double)q1;
       }
     }
-    __syncwarp();
-    if (lane == 0) mbar_arrive(own_empty);
-    ++own_it;
     if (per_task && partials) {
       // per (atom, warp) partial sums: no barrier between warps is needed
       for (int o = 16; o > 0; o >>= 1) {

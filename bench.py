@@ -508,10 +508,16 @@ def run_batched(args, rank, world):
     model = api.Solver(wks[0], ctx).model
     hosts = [torch.from_numpy(np.ascontiguousarray(w.positions)).pin_memory() for w in wks]
     devs = [h.to(f"cuda:{local}") for h in hosts]
-    mom_ev = []
+    phase_ev = []
+
+    def ev():
+        e = torch.cuda.Event(enable_timing=True)
+        e.record(ctx.stream)
+        return e
 
     def step(pos, record=False):
         Hs, e0, e1, ps = [], [], [], []
+        marks = [ev()] if record else None
         for w, p_ in zip(wks, pos):
             g = api.build_neighbors(ctx, p_, w.cutoff)
             H = api.assemble_H(ctx, model, p_, g)
@@ -519,15 +525,13 @@ def run_batched(args, rank, world):
             Hs.append(H); e0.append(lo); e1.append(hi); ps.append(order_rule(hi - lo, w.kT))
         seeds = [w.probe_seed for w in wks]
         if record:
-            a = torch.cuda.Event(enable_timing=True); b = torch.cuda.Event(enable_timing=True)
-            a.record(ctx.stream)
-        mom = api.batched_moments(ctx, Hs, e0, e1, seeds, s, ps)
+            marks.append(ev())
+        _, obs, _, Fs = api.batched_energies_and_forces(ctx, Hs, model, pos, e0, e1, seeds, s, ps,
+                                                        [w.n_electrons for w in wks],
+                                                        [w.kT for w in wks])
         if record:
-            b.record(ctx.stream)
-            mom_ev.append((a, b, Hs, ps))
-        obs = api.batched_fermi_level(ctx, mom, e0, e1, [w.n_electrons for w in wks], [w.kT for w in wks])
-        _, Fs = api.batched_density_and_forces(ctx, Hs, model, pos, e0, e1, seeds, s, ps, obs[:, 0],
-                                               [w.kT for w in wks])
+            marks.append(ev())
+            phase_ev.append((marks, Hs, ps))
         return ps, obs, Fs
 
     for _ in range(args.warmup):
@@ -536,6 +540,7 @@ def run_batched(args, rank, world):
     clocks = ClockSampler(local, enabled=not args.no_clocks)
     clocks.start()
     l0 = ctx.launches
+    ctx.time_kernels("step", "backward")
     t0 = torch.cuda.Event(enable_timing=True); t1 = torch.cuda.Event(enable_timing=True)
     t0.record(ctx.stream)
     for _ in range(args.steps):
@@ -543,6 +548,8 @@ def run_batched(args, rank, world):
     t1.record(ctx.stream)
     torch.cuda.synchronize()
     launches = ctx.launches - l0
+    fam = {f: ctx.kernel_time(f) for f in ("step", "backward")}
+    ctx.time_kernels()
     ms = t0.elapsed_time(t1) / args.steps
     e_ms = []
     for _ in range(max(1, min(args.steps, 2))):
@@ -556,19 +563,40 @@ def run_batched(args, rank, world):
         e_ms.append(a.elapsed_time(b))
     clk = clocks.stop()
     units = sum(w.n_atoms * s * p for w, p in zip(wks, ps))
-    # algorithmic bytes of the batched recurrence: active clusters per step
-    mom_ms = sum(a.elapsed_time(b) for a, b, _, _ in mom_ev)
-    _, _, Hs, ps_ = mom_ev[-1]
-    K = [p // 2 for p in ps_]
-    tot_bytes = 0
-    for j in range(1, max(K) + 1):
-        for H, k in zip(Hs, K):
-            if k >= j:
-                tot_bytes += 3 * H.graph.n_atoms * 9 * s * 4 + H.graph.nnzb * 81 * 4
-    tot_bytes *= len(mom_ev)
-    achieved = tot_bytes / (mom_ms / 1e3) / 1e9
-    peak = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", 6800.0)) \
-        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6800.0
+    # rooflines of the two kernel families from their own launches in the timed steps: cluster c
+    # takes part in K_c = p_c/2 recurrence steps and K_c adjoint steps
+    _, Hs, ps_ = phase_ev[-1]
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    alu = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    fb = ff = bb = bf = 0.0
+    for H, p in zip(Hs, ps_):
+        K = p // 2
+        panel = H.graph.n_atoms * 9 * s * 4
+        blocks = H.graph.nnzb * 81
+        fb += K * (3 * panel + blocks * 4)
+        ff += K * 2 * blocks * s
+        bb += K * (6 * panel + blocks * 4 + blocks * 16)
+        bf += K * 4 * blocks * s
+    kernels = {}
+    for f, by, fl, kname in (("step", fb, ff, "cheb_step_bulk (batched)"),
+                             ("backward", bb, bf, "clenshaw_sddmm_bulk (batched)")):
+        tms, nl = fam[f]
+        if nl == 0:
+            continue
+        sec = tms / 1e3 / args.steps
+        if fl / (alu * 1e12) >= by / (hbm * 1e9):
+            r = {"bound": "alu", "achieved": fl / sec / 1e12, "peak": alu, "unit": "TFLOP/s",
+                 "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz (derived, FP32 FMA)"}
+        else:
+            r = {"bound": "hbm", "achieved": by / sec / 1e9, "peak": hbm, "unit": "GB/s",
+                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+        r.update(frac=r["achieved"] / r["peak"], kernel=kname, traffic=None,
+                 algorithmic_bytes_per_step=by, algorithmic_flops_per_step=fl,
+                 avg_launch_ms=tms / nl, launches_timed=nl, share_of_step=tms / (ms * args.steps))
+        kernels[f] = r
+    dom = max(kernels, key=lambda f: kernels[f]["share_of_step"])
     h2d = sum(h.numel() * 8 for h in hosts)
     d2h = sum(w.n_atoms * 3 * 8 for w in wks)
     line = {"metric": METRIC, "value": units * world / (ms / 1e3), "unit": UNIT, "n_gpus": world,
@@ -582,9 +610,11 @@ def run_batched(args, rank, world):
             "e2e": {"value": units * world / (statistics.median(e_ms) / 1e3), "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches,
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None, "kernel": "cheb_step_bulk (batched)",
-                         "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"},
+            "roofline": dict(kernels[dom]),
+            "kernels": {f: {k: v for k, v in r.items() if k != "peak_source"} for f, r in kernels.items()},
+            "phases_ms_per_step": {
+                name: sum(m[i].elapsed_time(m[i + 1]) for m, _, _ in phase_ev) / len(phase_ev)
+                for i, name in enumerate(("neighbours_H_bounds", "energies_and_forces"))},
             "clocks": clk}
     if rank == 0:
         print(json.dumps(line))

@@ -269,6 +269,21 @@ int tbk_batched_density_and_forces(tbk_ctx* ctx, int32_t n_clusters, const tbk_b
                                    int64_t max_panel_bytes, double* const* G,
                                    double* const* forces);
 
+/* tbk_batched_energies_and_forces: tbk_batched_moments + tbk_batched_fermi_level +
+   tbk_batched_density_and_forces in one call, for the same results.  On the one-launch path the
+   forward sweep of the batched adjoint produces every cluster's moments as it goes, so no
+   separate moment pass runs.  n_electrons: host, per cluster.  moments: device, laid out as
+   tbk_batched_moments writes them, or NULL.  observables: host, 4 doubles {mu, Omega, E, N}
+   per cluster.  G, forces as in tbk_batched_density_and_forces (either may be NULL).  n_probes
+   a multiple of 128; flags: 0 (mixed).  Synchronises the stream. */
+int tbk_batched_energies_and_forces(tbk_ctx* ctx, int32_t n_clusters, const tbk_bsr* H,
+                                    const tbk_model* model, const double* const* pos,
+                                    const double* emin, const double* emax, const uint64_t* seeds,
+                                    int32_t n_probes, const int32_t* orders,
+                                    const double* n_electrons, const double* kT, int32_t damping,
+                                    int32_t flags, int64_t max_panel_bytes, double* moments,
+                                    double* observables, double* const* G, double* const* forces);
+
 /* ---- allocation-free variant of tbk_chebyshev_moments ------------------------------------
 
    No counterpart in the paper: this entry point exists for callers that cannot allocate device

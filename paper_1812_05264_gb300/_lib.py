@@ -88,6 +88,11 @@ SIGNATURES = {
                                        C.POINTER(_P), C.POINTER(_D), C.POINTER(_D),
                                        C.POINTER(_U), _I, C.POINTER(_I), C.POINTER(_D),
                                        C.POINTER(_D), _I, _I, _L, C.POINTER(_P), C.POINTER(_P)],
+    "tbk_batched_energies_and_forces": [_P, _I, C.POINTER(tbk_bsr), C.POINTER(tbk_model),
+                                        C.POINTER(_P), C.POINTER(_D), C.POINTER(_D),
+                                        C.POINTER(_U), _I, C.POINTER(_I), C.POINTER(_D),
+                                        C.POINTER(_D), _I, _I, _L, _P, C.POINTER(_D),
+                                        C.POINTER(_P), C.POINTER(_P)],
     "tbk_fermi_level": [_P, _P, _I, _D, _D, _D, _D, _D, _I, C.POINTER(_D)],
     "tbk_density_and_forces": [_P, C.POINTER(tbk_bsr), C.POINTER(tbk_model), _P, _P, _D, _D, _U,
                                _I, _I, _D, _D, _I, _I, _L, _P, _P],

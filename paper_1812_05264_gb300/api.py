@@ -275,6 +275,32 @@ def batched_density_and_forces(ctx: Context, Hs: list, model: Model, positions: 
     return Gs, Fs
 
 
+def batched_energies_and_forces(ctx: Context, Hs: list, model: Model, positions: list, emins,
+                                emaxs, seeds, n_probes: int, orders, n_electrons, kTs,
+                                jackson: bool = False, want_G: bool = False,
+                                max_panel_bytes: int = 0):
+    """a5-a11 for a batch in one call: (moments list, observables (n, 4) array of
+    (mu, Omega, E, N), G list or None, forces list)."""
+    n = len(Hs)
+    structs = (L.tbk_bsr * n)(*[h.struct() for h in Hs])
+    arr = lambda v: (C.c_double * n)(*map(float, v))
+    dev = Hs[0].val.device
+    mom = torch.empty(int(sum(orders)), dtype=torch.float64, device=dev)
+    obs = (C.c_double * (4 * n))()
+    Fs = [torch.empty((h.graph.n_atoms, 3), dtype=torch.float64, device=h.val.device) for h in Hs]
+    Gs = [torch.empty_like(h.val) for h in Hs] if want_G else None
+    pp = (C.c_void_p * n)(*[p.data_ptr() for p in positions])
+    fp = (C.c_void_p * n)(*[f.data_ptr() for f in Fs])
+    gp = (C.c_void_p * n)(*[g.data_ptr() for g in Gs]) if want_G else None
+    L.call("tbk_batched_energies_and_forces", ctx.handle, n, structs, C.byref(model.s), pp,
+           arr(emins), arr(emaxs), (C.c_uint64 * n)(*map(int, seeds)), int(n_probes),
+           (C.c_int32 * n)(*map(int, orders)), arr(n_electrons), arr(kTs),
+           L.TBK_DAMP_JACKSON if jackson else L.TBK_DAMP_NONE, 0, int(max_panel_bytes), _ptr(mom),
+           obs, gp, fp)
+    moms = list(torch.split(mom, [int(p) for p in orders]))
+    return moms, np.array(obs[:], dtype=np.float64).reshape(n, 4), Gs, Fs
+
+
 def energies_and_forces(ctx: Context, H: BSR, model: Model | None, pos: torch.Tensor | None, box,
                         emin: float, emax: float, seed: int, n_probes: int, order: int,
                         n_electrons: float, kT: float, jackson: bool = False, fp64: bool = False,

@@ -761,10 +761,10 @@ __global__ void ybar_init(int64_t n, int s, float ca, const float* __restrict__ 
 void adjoint_doubling(tbk_ctx* ctx, const HOp& op, uint64_t probe_seed, int s, int p,
                       const std::function<std::vector<double>()>& get_coefs, double* partials, int nctas,
                       int64_t max_panel_bytes, double* Gacc, int* err, bool windowed, const AdjBatch* bt) {
-  TBK_CHECK_ARG(!(bt && (windowed || partials)), "batched adjoint: no windows, no moment partials");
+  TBK_CHECK_ARG(!(bt && windowed), "batched adjoint: no windowed outer products");
   const int K = bt ? (bt->K.empty() ? 0 : bt->K[0]) : p / 2;
   if (K < 1) {
-    if (!bt) get_coefs();
+    if (get_coefs) get_coefs();
     return;  // p = 1: the estimate does not depend on H
   }
   // atoms of the (order-sorted) clusters that take part in step t: a prefix of the merged rows
@@ -775,16 +775,18 @@ void adjoint_doubling(tbk_ctx* ctx, const HOp& op, uint64_t probe_seed, int s, i
     return (int)r;
   };
   std::vector<double> w(K + 2, 0.0), v(K + 2, 0.0);
-  bool have_coefs = bt != nullptr;  // a batch brings its per-cluster coefficient table
+  // a batch brings its per-cluster coefficient table (filled by get_coefs() when given)
+  bool have_coefs = bt != nullptr && !get_coefs;
   auto load_coefs = [&]() {
     const std::vector<double> c = get_coefs();
+    have_coefs = true;
+    if (bt) return;
     for (int k = 1; k <= K; ++k) {
       if (2 * k < p) w[k] = 2.0 * c[2 * k];
       if (k >= 2 && 2 * k - 1 < p) v[k] = 2.0 * c[2 * k - 1];
     }
     v[1] = p > 1 ? c[1] : 0.0;
     for (int k = 2; 2 * k - 1 < p; ++k) v[1] -= c[2 * k - 1];
-    have_coefs = true;
   };
   auto ca = [&](int k) { return (float)(2.0 * w[k] / s); };
   auto cb = [&](int k) { return (float)(v[k] / s); };
@@ -858,7 +860,15 @@ void adjoint_doubling(tbk_ctx* ctx, const HOp& op, uint64_t probe_seed, int s, i
     a.yout = yout;
     a.err = err;
     a.batch = br;
-    if (partials && first_time) a.partials = partials + (size_t)(t - 1) * nctas * 2;
+    if (partials && first_time) {
+      if (bt) {
+        // per (atom, consumer warp) partial sums, reduced per cluster by the caller
+        a.partials = partials + (size_t)(t - 1) * bt->pstride;
+        a.per_task = 1;
+      } else {
+        a.partials = partials + (size_t)(t - 1) * nctas * 2;
+      }
+    }
     launch_step(ctx, o, a);
   };
   if (!all_stored) {

@@ -368,21 +368,32 @@ extern "C" int tbk_batched_fermi_level(tbk_ctx* ctx, int32_t n_clusters, const d
   TBK_CHECK_ARG(n_clusters >= 1, "n_clusters must be >= 1");
   TBK_CHECK_ARG(damping == TBK_DAMP_NONE || damping == TBK_DAMP_JACKSON, "unknown damping");
   DeviceGuard dg(ctx);
+  std::vector<FermiJob> jobs(n_clusters);
   size_t need = 0;
+  int64_t moff = 0;
+  int M_max = 1;
   for (int c = 0; c < n_clusters; ++c) {
     TBK_CHECK_ARG(orders[c] >= 1 && orders[c] <= (1 << 22), "order out of range");
-    need += 5 * (size_t)quad_nodes(orders[c]) + 8;
+    TBK_CHECK_ARG(kT[c] > 0.0 && std::isfinite(kT[c]) && emax[c] > emin[c], "bad kT or bounds");
+    FermiJob& j = jobs[c];
+    j.M = quad_nodes(orders[c]);
+    j.p = orders[c];
+    j.emin = emin[c];
+    j.emax = emax[c];
+    j.n_e = n_electrons[c];
+    j.kT = kT[c];
+    j.mom_off = moff;
+    j.tab_off = (int64_t)need;
+    j.rho_off = j.tab_off + 4 * (int64_t)j.M;
+    need += 5 * (size_t)j.M + 8;
+    moff += orders[c];
+    M_max = std::max(M_max, j.M);
   }
   double* buf = (double*)scratch(ctx, WS_COEF, sizeof(double) * need);
-  double* res = (double*)scratch(ctx, WS_NODES, sizeof(double) * 8 * (size_t)n_clusters);
-  size_t off = 0, moff = 0;
-  for (int c = 0; c < n_clusters; ++c) {
-    const int M = quad_nodes(orders[c]);
-    fermi_enqueue(ctx, moments + moff, orders[c], emin[c], emax[c], n_electrons[c], 0.0, kT[c],
-                  damping, buf + off, buf + off + 4 * (size_t)M, res + 8 * (size_t)c);
-    off += 5 * (size_t)M + 8;
-    moff += orders[c];
-  }
+  double* res = (double*)scratch(ctx, WS_NODES, sizeof(double) * 8 * (size_t)n_clusters + sizeof(FermiJob) * n_clusters + 64);
+  FermiJob* d_jobs = (FermiJob*)(res + 8 * (size_t)n_clusters);
+  TBK_CUDA(cudaMemcpyAsync(d_jobs, jobs.data(), sizeof(FermiJob) * n_clusters, cudaMemcpyHostToDevice, ctx->stream));
+  fermi_enqueue_batched(ctx, n_clusters, d_jobs, M_max, moments, damping, buf, res);
   std::vector<double> h(8 * (size_t)n_clusters);
   TBK_CUDA(cudaMemcpyAsync(h.data(), res, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, ctx->stream));
   sync(ctx);
@@ -424,35 +435,21 @@ void launch_batch_probe_panel(tbk_ctx* ctx, const HOp& op, const BatchRows& br, 
 
 }  // namespace tbk
 
-extern "C" int tbk_batched_density_and_forces(
-    tbk_ctx* ctx, int32_t n_clusters, const tbk_bsr* H, const tbk_model* model,
-    const double* const* pos, const double* emin, const double* emax, const uint64_t* seeds,
-    int32_t n_probes, const int32_t* orders, const double* mu, const double* kT, int32_t damping,
-    int32_t flags, int64_t max_panel_bytes, double* const* G, double* const* forces) {
-  TBK_API_BEGIN
-  TBK_CHECK_ARG(ctx && H && emin && emax && seeds && orders && mu && kT, "NULL argument");
-  TBK_CHECK_ARG(n_clusters >= 1, "n_clusters must be >= 1");
-  TBK_CHECK_ARG(G || forces, "nothing to compute: G and forces are both NULL");
-  TBK_CHECK_ARG(flags == 0, "batched adjoint runs in mixed precision; no flags are supported");
-  TBK_CHECK_ARG(!forces || pos, "forces need positions");
-  DeviceGuard dg(ctx);
-  const int s = n_probes, ncl = n_clusters;
+namespace tbk {
+
+// The adjoint of the doubled moments over a merged batch of clusters.  mu != NULL: chemical
+// potentials given (tbk_batched_density_and_forces).  mu == NULL: the forward sweep also yields
+// the moments, then mu, Omega, E, N of every cluster are solved for before the backward sweep
+// (tbk_batched_energies_and_forces; moments / observables receive them).
+static void batched_adjoint(tbk_ctx* ctx, int ncl, const tbk_bsr* H, const tbk_model* model,
+                            const double* const* pos, const double* emin, const double* emax,
+                            const uint64_t* seeds, int s, const int32_t* orders, const double* mu,
+                            const double* n_electrons, const double* kT, int damping,
+                            int64_t max_panel_bytes, double* moments, double* observables,
+                            double* const* G, double* const* forces) {
   HOp op;
   op.B = 9;
   op.prec = TBK_MIXED;
-  bool merged = fused_eligible(op, s, 0);
-  for (int c = 0; c < ncl; ++c) merged = merged && H[c].n_orb == 9;
-  if (!merged) {
-    // same kernels, one cluster after the other
-    for (int c = 0; c < ncl; ++c) {
-      const int rc = tbk_density_and_forces(ctx, &H[c], model, pos ? pos[c] : nullptr, nullptr, emin[c],
-                                            emax[c], seeds[c], s, orders[c], mu[c], kT[c], damping, flags,
-                                            max_panel_bytes, G ? G[c] : nullptr,
-                                            forces ? forces[c] : nullptr);
-      if (rc != TBK_OK) throw Error(rc, std::string("cluster ") + std::to_string(c) + ": " + tbk_last_error());
-    }
-    return TBK_OK;
-  }
   DevModel Mdl{};
   if (forces) {
     Mdl = upload_model(ctx, model, nullptr, WS_TABLE);
@@ -462,12 +459,16 @@ extern "C" int tbk_batched_density_and_forces(
   std::vector<int> idx(ncl);
   std::iota(idx.begin(), idx.end(), 0);
   std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) { return orders[x] / 2 > orders[y] / 2; });
-  std::vector<int32_t> a_off(ncl), n_at(ncl), pc(ncl);
-  std::vector<int64_t> b_off(ncl);
+  std::vector<int32_t> a_off(ncl), n_at(ncl), pc(ncl), ks(ncl);
+  std::vector<int64_t> b_off(ncl), out_off(ncl), out_off_u(ncl);
   std::vector<uint64_t> sd(ncl);
   std::vector<double> scale(ncl);
-  int64_t ao = 0, bo = 0;
+  int64_t ao = 0, bo = 0, mo = 0;
   int pmax = 1;
+  for (int c = 0; c < ncl; ++c) {
+    out_off_u[c] = mo;
+    mo += orders[c];
+  }
   for (int ci = 0; ci < ncl; ++ci) {
     const int c = idx[ci];
     TBK_CHECK_ARG(H[c].n_atoms >= 1 && H[c].row_ptr && H[c].col && H[c].val, "empty or NULL cluster");
@@ -476,6 +477,8 @@ extern "C" int tbk_batched_density_and_forces(
     b_off[ci] = bo;
     n_at[ci] = H[c].n_atoms;
     pc[ci] = orders[c];
+    ks[ci] = orders[c] / 2;
+    out_off[ci] = out_off_u[c];
     sd[ci] = seeds[c];
     scale[ci] = 2.0 / (emax[c] - emin[c]);
     ao += H[c].n_atoms;
@@ -483,7 +486,7 @@ extern "C" int tbk_batched_density_and_forces(
     pmax = std::max(pmax, orders[c]);
   }
   TBK_CHECK_ARG(bo < INT32_MAX && ao * 9 < INT32_MAX, "batch too large for int32 indices");
-  const int Kmax = pc[0] / 2;
+  const int Kmax = ks[0];
   op.n_atoms = (int)ao;
   op.nnzb = bo;
   op.n_rows = ao * 9;
@@ -491,11 +494,19 @@ extern "C" int tbk_batched_density_and_forces(
   char* meta = (char*)scratch(ctx, WS_TABLE, 128 * (size_t)ncl + 4096);
   // (WS_TABLE also holds the uploaded model table only for TABLE models; SK needs none)
   int32_t* d_atom0 = (int32_t*)meta;
-  uint64_t* d_seed = (uint64_t*)(((uintptr_t)(d_atom0 + ncl) + 15) & ~(uintptr_t)15);
+  int32_t* d_nat = d_atom0 + ncl;
+  int32_t* d_ks = d_nat + ncl;
+  int32_t* d_ord = d_ks + ncl;
+  uint64_t* d_seed = (uint64_t*)(((uintptr_t)(d_ord + ncl) + 15) & ~(uintptr_t)15);
   double* d_scale = (double*)(d_seed + ncl);
+  int64_t* d_out = (int64_t*)(d_scale + ncl);
   TBK_CUDA(cudaMemcpyAsync(d_atom0, a_off.data(), 4 * ncl, cudaMemcpyHostToDevice, ctx->stream));
+  TBK_CUDA(cudaMemcpyAsync(d_nat, n_at.data(), 4 * ncl, cudaMemcpyHostToDevice, ctx->stream));
+  TBK_CUDA(cudaMemcpyAsync(d_ks, ks.data(), 4 * ncl, cudaMemcpyHostToDevice, ctx->stream));
+  TBK_CUDA(cudaMemcpyAsync(d_ord, pc.data(), 4 * ncl, cudaMemcpyHostToDevice, ctx->stream));
   TBK_CUDA(cudaMemcpyAsync(d_seed, sd.data(), 8 * ncl, cudaMemcpyHostToDevice, ctx->stream));
   TBK_CUDA(cudaMemcpyAsync(d_scale, scale.data(), 8 * ncl, cudaMemcpyHostToDevice, ctx->stream));
+  TBK_CUDA(cudaMemcpyAsync(d_out, out_off.data(), 8 * ncl, cudaMemcpyHostToDevice, ctx->stream));
   int32_t* m_row_ptr = (int32_t*)scratch(ctx, WS_CELLS, sizeof(int32_t) * (size_t)(2 * ao + 1) + 64);
   int32_t* atom_cl = m_row_ptr + ao + 1;
   int32_t* m_col = (int32_t*)scratch(ctx, WS_CELLS2, sizeof(int32_t) * (size_t)bo + 64);
@@ -519,47 +530,119 @@ extern "C" int tbk_batched_density_and_forces(
   br.atom_cl = atom_cl;
   br.seed = d_seed;
   br.atom0 = d_atom0;
+  // err: bit 2 = a bounded wait expired, bit 1 = a pattern is not symmetric; err[1] bit 1 = a
+  // panel outgrew ||r|| (the spectrum is not inside [emin, emax])
   int* err = (int*)scratch(ctx, WS_FLAGS, 64);
-  TBK_CUDA(cudaMemsetAsync(err, 0, sizeof(int), ctx->stream));
-  // ---- coefficients c_k = d_k beta_k[g] per cluster -> the source coefficients of each step ----
-  double* coefd = (double*)scratch(ctx, WS_COEF, sizeof(double) * (size_t)pmax * ncl);
-  for (int ci = 0; ci < ncl; ++ci) {
-    const int c = idx[ci];
-    coefficients(ctx, TBK_FN_FREE, pc[ci], emin[c], emax[c], mu[c], kT[c], damping,
-                 coefd + (size_t)ci * pmax);
-  }
-  std::vector<double> ch((size_t)pmax * ncl);
-  TBK_CUDA(cudaMemcpyAsync(ch.data(), coefd, sizeof(double) * ch.size(), cudaMemcpyDeviceToHost, ctx->stream));
-  sync(ctx);
-  // per step k and cluster: (probe, y_k, y_{k-1}, y_{k+1}) coefficients of g_k (zero once k > K_c)
-  std::vector<float4> cft((size_t)(Kmax + 1) * ncl, make_float4(0.f, 0.f, 0.f, 0.f));
+  TBK_CUDA(cudaMemsetAsync(err, 0, 2 * sizeof(int), ctx->stream));
+  // (not WS_NODES: coefficients() keeps its cosine table there)
+  float4* d_cft = (float4*)scratch(ctx, WS_LANCZOS, sizeof(float4) * (size_t)(Kmax + 1) * ncl + 64);
+  // ---- the source coefficients of every step from c_k = d_k beta_k[g](mu) of every cluster ----
+  auto build_cft = [&](const double* mus) {
+    double* coefd = (double*)scratch(ctx, WS_COEF, sizeof(double) * (size_t)pmax * ncl);
     for (int ci = 0; ci < ncl; ++ci) {
-    const int p = pc[ci], K = p / 2;
-    const double* c = ch.data() + (size_t)ci * pmax;
-    std::vector<double> w(K + 2, 0.0), v(K + 2, 0.0);
-    for (int k = 1; k <= K; ++k) {
-      if (2 * k < p) w[k] = 2.0 * c[2 * k];
-      if (k >= 2 && 2 * k - 1 < p) v[k] = 2.0 * c[2 * k - 1];
+      const int c = idx[ci];
+      coefficients(ctx, TBK_FN_FREE, pc[ci], emin[c], emax[c], mus[c], kT[c], damping,
+                   coefd + (size_t)ci * pmax);
     }
-    v[1] = p > 1 ? c[1] : 0.0;
-    for (int k = 2; 2 * k - 1 < p; ++k) v[1] -= c[2 * k - 1];
-    for (int k = 1; k <= K; ++k)
-      cft[(size_t)k * ncl + ci] = make_float4(k == 1 ? (float)(v[1] / s) : 0.f, (float)(2.0 * w[k] / s),
-                                              k == 1 ? 0.f : (float)(v[k] / s), (float)(v[k + 1] / s));
-  }
-  float4* d_cft = (float4*)scratch(ctx, WS_NODES, sizeof(float4) * cft.size() + 64);
-  TBK_CUDA(cudaMemcpyAsync(d_cft, cft.data(), sizeof(float4) * cft.size(), cudaMemcpyHostToDevice, ctx->stream));
+    std::vector<double> ch((size_t)pmax * ncl);
+    TBK_CUDA(cudaMemcpyAsync(ch.data(), coefd, sizeof(double) * ch.size(), cudaMemcpyDeviceToHost, ctx->stream));
+    sync(ctx);
+    // per step k and cluster: (probe, y_k, y_{k-1}, y_{k+1}) coefficients of g_k (zero once k > K_c)
+    std::vector<float4> cft((size_t)(Kmax + 1) * ncl, make_float4(0.f, 0.f, 0.f, 0.f));
+    for (int ci = 0; ci < ncl; ++ci) {
+      const int p = pc[ci], K = p / 2;
+      const double* c = ch.data() + (size_t)ci * pmax;
+      std::vector<double> w(K + 2, 0.0), v(K + 2, 0.0);
+      for (int k = 1; k <= K; ++k) {
+        if (2 * k < p) w[k] = 2.0 * c[2 * k];
+        if (k >= 2 && 2 * k - 1 < p) v[k] = 2.0 * c[2 * k - 1];
+      }
+      v[1] = p > 1 ? c[1] : 0.0;
+      for (int k = 2; 2 * k - 1 < p; ++k) v[1] -= c[2 * k - 1];
+      for (int k = 1; k <= K; ++k)
+        cft[(size_t)k * ncl + ci] = make_float4(k == 1 ? (float)(v[1] / s) : 0.f, (float)(2.0 * w[k] / s),
+                                                k == 1 ? 0.f : (float)(v[k] / s), (float)(v[k + 1] / s));
+    }
+    TBK_CUDA(cudaMemcpyAsync(d_cft, cft.data(), sizeof(float4) * cft.size(), cudaMemcpyHostToDevice, ctx->stream));
+    sync(ctx);  // cft is a host vector
+  };
   AdjBatch bt;
   bt.br = br;
   bt.cft = d_cft;
   for (int ci = 0; ci < ncl; ++ci) {
-    bt.K.push_back(pc[ci] / 2);
+    bt.K.push_back(ks[ci]);
     bt.n_at.push_back(n_at[ci]);
   }
   double* Gacc = (double*)scratch(ctx, WS_GACC, sizeof(double) * (size_t)bo * 81 * 2);
   double* Gsym = Gacc + (size_t)bo * 81;
   TBK_CUDA(cudaMemsetAsync(Gacc, 0, sizeof(double) * (size_t)bo * 81, ctx->stream));
-  adjoint_doubling(ctx, op, 0, s, 0, nullptr, nullptr, 0, max_panel_bytes, Gacc, err, false, &bt);
+  if (mu) {
+    build_cft(mu);
+    adjoint_doubling(ctx, op, 0, s, 0, nullptr, nullptr, 0, max_panel_bytes, Gacc, err, false, &bt);
+  } else {
+    // moments from the forward sweep: per (atom, warp) partials, reduced per cluster
+    const int cw = bulk_consumer_warps(op, s);
+    TBK_CHECK_ARG(cw > 0, "no TMA-fed step kernel for this probe count");
+    bt.pstride = ao * cw * 2;
+    double* partials = (double*)scratch(ctx, WS_PARTIALS, sizeof(double) * (size_t)std::max(1, Kmax) * bt.pstride);
+    double* sums = (double*)scratch(ctx, WS_SEGMENT, sizeof(double) * (2 * (size_t)std::max(1, Kmax) * ncl +
+                                                                         (size_t)mo + 64));
+    double* mom = moments ? moments : sums + 2 * (size_t)std::max(1, Kmax) * ncl;
+    auto after_forward = [&]() {
+      if (Kmax >= 1) {
+        batch_reduce<<<dim3(Kmax, ncl), 256, 0, ctx->stream>>>(partials, bt.pstride, cw, d_atom0, d_nat, d_ks,
+                                                                Kmax, sums);
+        post_launch(ctx, "batch_reduce");
+      }
+      batch_finish<<<ncl, 256, 0, ctx->stream>>>(sums, std::max(1, Kmax), d_ks, d_ord, d_out, d_nat, s, 0, mom,
+                                                 err + 1);
+      post_launch(ctx, "batch_finish");
+      // mu, Omega, E, N of every cluster
+      std::vector<FermiJob> jobs(ncl);
+      size_t need = 0;
+      int M_max = 1;
+      for (int c = 0; c < ncl; ++c) {
+        FermiJob& j = jobs[c];
+        j.M = quad_nodes(orders[c]);
+        j.p = orders[c];
+        j.emin = emin[c];
+        j.emax = emax[c];
+        j.n_e = n_electrons[c];
+        j.kT = kT[c];
+        j.mom_off = out_off_u[c];
+        j.tab_off = (int64_t)need;
+        j.rho_off = j.tab_off + 4 * (int64_t)j.M;
+        need += 5 * (size_t)j.M + 8;
+        M_max = std::max(M_max, j.M);
+      }
+      double* fbuf = (double*)scratch(ctx, WS_PANEL1, sizeof(double) * need);
+      double* res = (double*)scratch(ctx, WS_PANEL2, sizeof(double) * 8 * (size_t)ncl + sizeof(FermiJob) * ncl + 64);
+      FermiJob* d_jobs = (FermiJob*)(res + 8 * (size_t)ncl);
+      TBK_CUDA(cudaMemcpyAsync(d_jobs, jobs.data(), sizeof(FermiJob) * ncl, cudaMemcpyHostToDevice, ctx->stream));
+      fermi_enqueue_batched(ctx, ncl, d_jobs, M_max, mom, damping, fbuf, res);
+      std::vector<double> h(8 * (size_t)ncl);
+      int herr[2] = {0, 0};
+      TBK_CUDA(cudaMemcpyAsync(h.data(), res, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, ctx->stream));
+      TBK_CUDA(cudaMemcpyAsync(herr, err, sizeof(herr), cudaMemcpyDeviceToHost, ctx->stream));
+      sync(ctx);
+      if ((herr[0] | herr[1]) & 2) throw Error(TBK_ERR_TIMEOUT, "a bounded wait in a recurrence kernel expired");
+      TBK_CHECK_ARG(herr[0] == 0, "a block pattern is not symmetric");
+      if (herr[1])
+        throw Error(TBK_ERR_SPECTRUM, "a Chebyshev panel grew beyond ||r||: some cluster's spectrum is not "
+                                      "inside its [emin, emax]");
+      std::vector<double> mus(ncl);
+      bool bad = false;
+      for (int c = 0; c < ncl; ++c) {
+        for (int q = 0; q < 4; ++q) observables[4 * c + q] = h[8 * c + q];
+        mus[c] = h[8 * c];
+        bad = bad || h[8 * c + 4] != 0.0;
+      }
+      if (bad) throw Error(TBK_ERR_NOCONV, "n_electrons is outside the estimated N(mu) range for some cluster");
+      build_cft(mus.data());
+      return std::vector<double>();
+    };
+    adjoint_doubling(ctx, op, 0, s, 0, after_forward, partials, 0, max_panel_bytes, Gacc, err, false, &bt);
+  }
   // ---- G (symmetrised, per-cluster scale) and forces on the merged pattern ----
   int32_t* tr = (int32_t*)scratch(ctx, WS_TRANSPOSE, sizeof(int32_t) * (size_t)bo);
   launch_transpose_map(ctx, op.n_atoms, op.row_ptr, op.col, tr, err);
@@ -584,5 +667,84 @@ extern "C" int tbk_batched_density_and_forces(
   sync(ctx);
   if (herr & 2) throw Error(TBK_ERR_TIMEOUT, "a bounded wait in a recurrence kernel expired");
   TBK_CHECK_ARG(herr == 0, "a block pattern is not symmetric");
+}
+
+static bool batch_merges(const tbk_bsr* H, int ncl, int s) {
+  HOp op;
+  op.B = 9;
+  op.prec = TBK_MIXED;
+  bool merged = fused_eligible(op, s, 0);
+  for (int c = 0; c < ncl; ++c) merged = merged && H[c].n_orb == 9;
+  return merged;
+}
+
+}  // namespace tbk
+
+extern "C" int tbk_batched_density_and_forces(
+    tbk_ctx* ctx, int32_t n_clusters, const tbk_bsr* H, const tbk_model* model,
+    const double* const* pos, const double* emin, const double* emax, const uint64_t* seeds,
+    int32_t n_probes, const int32_t* orders, const double* mu, const double* kT, int32_t damping,
+    int32_t flags, int64_t max_panel_bytes, double* const* G, double* const* forces) {
+  TBK_API_BEGIN
+  TBK_CHECK_ARG(ctx && H && emin && emax && seeds && orders && mu && kT, "NULL argument");
+  TBK_CHECK_ARG(n_clusters >= 1, "n_clusters must be >= 1");
+  TBK_CHECK_ARG(G || forces, "nothing to compute: G and forces are both NULL");
+  TBK_CHECK_ARG(flags == 0, "batched adjoint runs in mixed precision; no flags are supported");
+  TBK_CHECK_ARG(!forces || pos, "forces need positions");
+  DeviceGuard dg(ctx);
+  const int s = n_probes, ncl = n_clusters;
+  if (!batch_merges(H, ncl, s)) {
+    // same kernels, one cluster after the other
+    for (int c = 0; c < ncl; ++c) {
+      const int rc = tbk_density_and_forces(ctx, &H[c], model, pos ? pos[c] : nullptr, nullptr, emin[c],
+                                            emax[c], seeds[c], s, orders[c], mu[c], kT[c], damping, flags,
+                                            max_panel_bytes, G ? G[c] : nullptr,
+                                            forces ? forces[c] : nullptr);
+      if (rc != TBK_OK) throw Error(rc, std::string("cluster ") + std::to_string(c) + ": " + tbk_last_error());
+    }
+    return TBK_OK;
+  }
+  batched_adjoint(ctx, ncl, H, model, pos, emin, emax, seeds, s, orders, mu, nullptr, kT, damping,
+                  max_panel_bytes, nullptr, nullptr, G, forces);
+  TBK_API_END
+}
+
+extern "C" int tbk_batched_energies_and_forces(
+    tbk_ctx* ctx, int32_t n_clusters, const tbk_bsr* H, const tbk_model* model,
+    const double* const* pos, const double* emin, const double* emax, const uint64_t* seeds,
+    int32_t n_probes, const int32_t* orders, const double* n_electrons, const double* kT,
+    int32_t damping, int32_t flags, int64_t max_panel_bytes, double* moments, double* observables,
+    double* const* G, double* const* forces) {
+  TBK_API_BEGIN
+  TBK_CHECK_ARG(ctx && H && emin && emax && seeds && orders && n_electrons && kT && observables,
+                "NULL argument");
+  TBK_CHECK_ARG(n_clusters >= 1, "n_clusters must be >= 1");
+  TBK_CHECK_ARG(flags == 0, "batched energies and forces run in mixed precision; no flags are supported");
+  TBK_CHECK_ARG(!forces || pos, "forces need positions");
+  TBK_CHECK_ARG(n_probes >= 128 && n_probes % 128 == 0, "batches need n_probes a multiple of 128");
+  for (int c = 0; c < n_clusters; ++c)
+    TBK_CHECK_ARG(n_electrons[c] >= 0.0, "n_electrons must be >= 0");
+  DeviceGuard dg(ctx);
+  const int s = n_probes, ncl = n_clusters;
+  if (!batch_merges(H, ncl, s)) {
+    // the separate calls give the same results for the other shapes
+    int64_t mo = 0;
+    for (int c = 0; c < ncl; ++c) mo += orders[c];
+    double* mom = moments ? moments : (double*)scratch(ctx, WS_SEGMENT, sizeof(double) * (size_t)mo);
+    int rc = tbk_batched_moments(ctx, ncl, H, emin, emax, seeds, s, orders, 0, mom);
+    if (rc != TBK_OK) throw Error(rc, tbk_last_error());
+    rc = tbk_batched_fermi_level(ctx, ncl, mom, orders, emin, emax, n_electrons, kT, damping, observables);
+    if (rc != TBK_OK) throw Error(rc, tbk_last_error());
+    if (G || forces) {
+      std::vector<double> mus(ncl);
+      for (int c = 0; c < ncl; ++c) mus[c] = observables[4 * c];
+      rc = tbk_batched_density_and_forces(ctx, ncl, H, model, pos, emin, emax, seeds, s, orders, mus.data(), kT,
+                                          damping, 0, max_panel_bytes, G, forces);
+      if (rc != TBK_OK) throw Error(rc, tbk_last_error());
+    }
+    return TBK_OK;
+  }
+  batched_adjoint(ctx, ncl, H, model, pos, emin, emax, seeds, s, orders, nullptr, n_electrons, kT, damping,
+                  max_panel_bytes, moments, observables, G, forces);
   TBK_API_END
 }

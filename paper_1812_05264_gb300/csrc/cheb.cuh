@@ -89,11 +89,14 @@ struct AdjBatch {
   std::vector<int> n_at;     // atoms per sorted cluster
   const float4* cft = nullptr;  // device, (K_max + 1) x n_clusters: (probe, y_k, y_{k-1}, y_{k+1})
                                 // coefficients of the source g_k of step k, zero past K_c
+  int64_t pstride = 0;          // doubles of moment partials per forward step (per atom and warp)
 };
 // Gacc += the unscaled gradient sum_k 2 y_k ybar_{k+1}^T + y_0 ybar_1^T on the pattern (scale 2/W
 // afterwards).  Single system: get_coefs() returns c_0 .. c_{p-1} once y_1 .. y_{p/2} exist
 // (with partials != NULL those forward steps also write their moment partial sums).  Batch: bt
-// gives the per-cluster tables; p, get_coefs and partials are unused.
+// gives the per-cluster tables; p is unused; get_coefs, when given, is called once the forward
+// sweep is done and fills bt->cft (its return value is ignored); partials, when given, receive
+// per (atom, warp) sums of every forward step at partials + (t - 1) bt->pstride.
 void adjoint_doubling(tbk_ctx* ctx, const HOp& op, uint64_t probe_seed, int s, int p,
                       const std::function<std::vector<double>()>& get_coefs, double* partials, int nctas,
                       int64_t max_panel_bytes, double* Gacc, int* err, bool windowed, const AdjBatch* bt);

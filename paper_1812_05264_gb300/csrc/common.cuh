@@ -86,6 +86,17 @@ struct KernelTimerScope {
 
 inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
+// One cluster's chemical-potential solve in a batch: M quadrature nodes, order p, moments at
+// mom_off, cosine table (4M doubles) at tab_off and node weights (M doubles) at rho_off of one
+// scratch buffer.
+struct FermiJob {
+  int M, p;
+  double emin, emax, n_e, kT;
+  int64_t mom_off, tab_off, rho_off;
+};
+void fermi_enqueue_batched(tbk_ctx* ctx, int n, const FermiJob* d_jobs, int M_max, const double* moments,
+                           int damping, double* buf, double* res);
+
 }  // namespace tbk
 
 #define TBK_API_BEGIN try {

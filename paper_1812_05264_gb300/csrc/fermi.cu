@@ -31,9 +31,12 @@ __device__ __forceinline__ double node_energy(int j, int M, double emin, double 
   return emin * (1.0 - x) * 0.5 + emax * (1.0 + x) * 0.5;
 }
 
-__global__ void cos_table(int M, double* __restrict__ tab) {
-  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void cos_entry(int m, int M, double* __restrict__ tab) {
   if (m < 4 * M) tab[m] = cospi((double)m / (2.0 * M));
+}
+
+__global__ void cos_table(int M, double* __restrict__ tab) {
+  cos_entry(blockIdx.x * blockDim.x + threadIdx.x, M, tab);
 }
 
 __device__ __forceinline__ double damp_factor(int k, int p, int damping) {
@@ -67,9 +70,8 @@ __global__ void coeff_kernel(int fn, int p, int M, double emin, double emax, dou
 }
 
 // rho_j, one thread per node, fixed order over k.
-__global__ void rho_kernel(const double* __restrict__ mom, int p, int M, int damping,
-                           const double* __restrict__ tab, double* __restrict__ rho) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void rho_node(int j, const double* __restrict__ mom, int p, int M, int damping,
+                                         const double* __restrict__ tab, double* __restrict__ rho) {
   if (j >= M) return;
   double s = 0.0, c = 0.0;
   const int64_t step = 2 * j + 1, period = 4 * (int64_t)M;
@@ -85,10 +87,15 @@ __global__ void rho_kernel(const double* __restrict__ mom, int p, int M, int dam
   rho[j] = s / M;
 }
 
-// Single block: bisection for N(mu) = n_e (skipped when n_e < 0), then Omega, E, N.
+__global__ void rho_kernel(const double* __restrict__ mom, int p, int M, int damping,
+                           const double* __restrict__ tab, double* __restrict__ rho) {
+  rho_node(blockIdx.x * blockDim.x + threadIdx.x, mom, p, M, damping, tab, rho);
+}
+
+// One block: bisection for N(mu) = n_e (skipped when n_e < 0), then Omega, E, N.
 // out = {mu, Omega, E, N, status} with status 1 when the bracket has no sign change.
-__global__ void fermi_kernel(const double* __restrict__ rho, int M, double emin, double emax,
-                             double n_e, double mu_fixed, double kT, double* __restrict__ out) {
+__device__ void fermi_solve(const double* __restrict__ rho, int M, double emin, double emax,
+                            double n_e, double mu_fixed, double kT, double* __restrict__ out) {
   __shared__ double red[32];
   __shared__ double bc;
   auto count = [&](double mu) {
@@ -137,7 +144,42 @@ __global__ void fermi_kernel(const double* __restrict__ rho, int M, double emin,
   }
 }
 
+__global__ void fermi_kernel(const double* __restrict__ rho, int M, double emin, double emax,
+                             double n_e, double mu_fixed, double kT, double* __restrict__ out) {
+  fermi_solve(rho, M, emin, emax, n_e, mu_fixed, kT, out);
+}
+
+// ---- many clusters in three launches (blockIdx.y / blockIdx.x = cluster) ----
+
+__global__ void cos_table_batched(const FermiJob* __restrict__ jobs, double* __restrict__ buf) {
+  const FermiJob j = jobs[blockIdx.y];
+  cos_entry(blockIdx.x * blockDim.x + threadIdx.x, j.M, buf + j.tab_off);
+}
+
+__global__ void rho_batched(const FermiJob* __restrict__ jobs, const double* __restrict__ mom, int damping,
+                            double* __restrict__ buf) {
+  const FermiJob j = jobs[blockIdx.y];
+  rho_node(blockIdx.x * blockDim.x + threadIdx.x, mom + j.mom_off, j.p, j.M, damping, buf + j.tab_off,
+           buf + j.rho_off);
+}
+
+__global__ void fermi_batched(const FermiJob* __restrict__ jobs, const double* __restrict__ buf,
+                              double* __restrict__ res) {
+  const FermiJob j = jobs[blockIdx.x];
+  fermi_solve(buf + j.rho_off, j.M, j.emin, j.emax, j.n_e, 0.0, j.kT, res + 8 * (int64_t)blockIdx.x);
+}
+
 int quad_nodes(int p) { return std::max(4 * p, 256); }
+
+void fermi_enqueue_batched(tbk_ctx* ctx, int n, const FermiJob* d_jobs, int M_max, const double* moments,
+                           int damping, double* buf, double* res) {
+  cos_table_batched<<<dim3(ceil_div(4 * (int64_t)M_max, 256), n), 256, 0, ctx->stream>>>(d_jobs, buf);
+  post_launch(ctx, "cos_table_batched");
+  rho_batched<<<dim3(ceil_div(M_max, 128), n), 128, 0, ctx->stream>>>(d_jobs, moments, damping, buf);
+  post_launch(ctx, "rho_batched");
+  fermi_batched<<<n, 1024, 0, ctx->stream>>>(d_jobs, buf, res);
+  post_launch(ctx, "fermi_batched");
+}
 
 const double* make_cos_table(tbk_ctx* ctx, int M) {
   double* tab = (double*)scratch(ctx, WS_NODES, sizeof(double) * 4 * (size_t)M);

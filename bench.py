@@ -44,9 +44,9 @@ METRIC = "atom*vector*Chebyshev-steps/s"
 UNIT = "atom*vector*steps/s"
 
 
-def make_workload(name: str, rank: int = 0, atom_order: str = "radial"):
+def make_workload(name: str, rank: int = 0, atom_order: str = "radial", probes: int | None = None):
     if name == "fcc10k":
-        return wl.fcc_cu(10000, kT=0.025, n_probes=512, seed=5264, probe_seed=52640 + rank,
+        return wl.fcc_cu(10000, kT=0.025, n_probes=probes or 512, seed=5264, probe_seed=52640 + rank,
                          atom_order=atom_order)
     if name == "fcc1k":
         return wl.fcc_cu(1000, kT=0.5, n_probes=256, seed=5264, probe_seed=52640 + rank)
@@ -169,7 +169,7 @@ def cpu_cores() -> int:
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
-    wk = oracle_sample(make_workload(args.workload, 0, args.atom_order))
+    wk = oracle_sample(make_workload(args.workload, 0, args.atom_order, args.probes))
     if wk is None:
         print(json.dumps({"impl": "reference", "unavailable": "oracle sample defined for the fcc workloads only"}))
         return 0
@@ -242,7 +242,7 @@ def run_ours(args, rank, world):
         if dist:
             torch.distributed.barrier()
 
-    wk = make_workload(args.workload, rank, args.atom_order)
+    wk = make_workload(args.workload, rank, args.atom_order, args.probes)
     ctx = api.Context()
     solver = api.Solver(wk, ctx)
     stream = ctx.stream
@@ -640,6 +640,8 @@ def main():
     ap.add_argument("--order", type=int, default=None,
                     help="fixed Chebyshev order (default: the error rule; 64 for --only-moments / "
                          "--only-adjoint); a reduced order is for profiler runs, not bench lines")
+    ap.add_argument("--probes", type=int, default=None,
+                    help="probe count of the fcc10k workload (default 512; a profiling aid)")
     ap.add_argument("--atom-order", default="radial", choices=["radial", "morton"],
                     help="listing order of the fcc10k atoms (same cluster)")
     ap.add_argument("--adjoint", default="fused", choices=["fused", "windowed"],

@@ -520,11 +520,12 @@ int step_grid_ctas(tbk_ctx* ctx, const HOp& op, int s) {
     o.bulk[2] = occupancy_bulk<2, BULK_D>();
     o.bulk[4] = occupancy_bulk<4, BULK_D>();
   }
-  int per_sm = o.simple;
+  // the TMA-fed kernel's occupancy sets the grid where it runs (the first step's plain kernel
+  // then just takes more than one wave: every kernel loops over its tasks, none waits on another
+  // CTA); the tensor-core step, when selected, runs on this same grid so that the per-CTA partial
+  // sums line up
   const int cw = bulk_warps(op, s);
-  if (cw && o.bulk[cw] > 0) per_sm = std::min(per_sm, o.bulk[cw]);
-  // (the tensor-core step, when selected, runs on this same grid so that the per-CTA partial
-  // sums line up; its own occupancy does not shrink the grid of the default kernels)
+  const int per_sm = cw && o.bulk[cw] > 0 ? o.bulk[cw] : o.simple;
   return std::max(1, per_sm * ctx->num_sms);
 }
 

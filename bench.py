@@ -520,9 +520,9 @@ def run_batched(args, rank, world):
         marks = [ev()] if record else None
         for w, p_ in zip(wks, pos):
             g = api.build_neighbors(ctx, p_, w.cutoff)
-            H = api.assemble_H(ctx, model, p_, g)
-            lo, hi = api.spectral_bounds(ctx, H)
-            Hs.append(H); e0.append(lo); e1.append(hi); ps.append(order_rule(hi - lo, w.kT))
+            Hs.append(api.assemble_H(ctx, model, p_, g))
+        e0, e1 = api.batched_spectral_bounds(ctx, Hs)
+        ps = [order_rule(hi - lo, w.kT) for w, lo, hi in zip(wks, e0, e1)]
         seeds = [w.probe_seed for w in wks]
         if record:
             marks.append(ev())

@@ -159,6 +159,12 @@ int tbk_assemble_H(tbk_ctx* ctx, const tbk_model* model, const double* pos, int3
    the width on each side.  emin, emax: host.  Synchronises the stream. */
 int tbk_spectral_bounds(tbk_ctx* ctx, const tbk_bsr* H, int32_t steps, double rel_margin,
                         uint64_t seed, double* emin, double* emax);
+/* tbk_batched_spectral_bounds: tbk_spectral_bounds for every cluster of a batch (host array H
+   of n_clusters matrices), the Lanczos steps of all clusters in one launch per kernel and step;
+   each cluster gets the bounds tbk_spectral_bounds gives it alone.  emin, emax: host,
+   n_clusters each.  Synchronises the stream once. */
+int tbk_batched_spectral_bounds(tbk_ctx* ctx, int32_t n_clusters, const tbk_bsr* H, int32_t steps,
+                                double rel_margin, uint64_t seed, double* emin, double* emax);
 
 /* ---- a4: Chebyshev coefficients (Sec. II.B.1) ------------------------------------------- */
 

@@ -75,6 +75,7 @@ SIGNATURES = {
     "tbk_build_neighbors": [_P, _P, _I, _P, _D, _P, _P, _L, C.POINTER(_L)],
     "tbk_assemble_H": [_P, C.POINTER(tbk_model), _P, _I, _P, _P, _P, _L, _P],
     "tbk_spectral_bounds": [_P, C.POINTER(tbk_bsr), _I, _D, _U, C.POINTER(_D), C.POINTER(_D)],
+    "tbk_batched_spectral_bounds": [_P, _I, C.POINTER(tbk_bsr), _I, _D, _U, C.POINTER(_D), C.POINTER(_D)],
     "tbk_chebyshev_coefficients": [_P, _I, _I, _D, _D, _D, _D, _I, _P],
     "tbk_chebyshev_moments": [_P, C.POINTER(tbk_bsr), _D, _D, _U, _I, _I, _I, _P],
     "tbk_chebyshev_moments_noalloc": [_P, C.POINTER(tbk_bsr), _D, _D, _U, _I, _I, _I, _P],

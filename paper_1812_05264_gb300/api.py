@@ -171,6 +171,17 @@ def spectral_bounds(ctx: Context, H: BSR, steps: int = 64, margin: float = 0.01,
     return lo.value, hi.value
 
 
+def batched_spectral_bounds(ctx: Context, Hs: list, steps: int = 64, margin: float = 0.01,
+                            seed: int = 0x5EED) -> tuple[list, list]:
+    """a3 for a batch: per-cluster [emin, emax], the Lanczos steps of all clusters together."""
+    n = len(Hs)
+    structs = (L.tbk_bsr * n)(*[h.struct() for h in Hs])
+    lo, hi = (C.c_double * n)(), (C.c_double * n)()
+    L.call("tbk_batched_spectral_bounds", ctx.handle, n, structs, int(steps), float(margin),
+           C.c_uint64(seed), lo, hi)
+    return list(lo), list(hi)
+
+
 def chebyshev_coefficients(ctx: Context, fn: int, order: int, emin: float, emax: float, mu: float,
                            kT: float, jackson: bool = False, device=None) -> torch.Tensor:
     """a4: damped Chebyshev coefficients of f, e f or g on [emin, emax]."""

@@ -4,6 +4,7 @@
 // eigenvalues (Sturm bisection) and eigenvector end components (inverse iteration).
 #include <algorithm>
 #include <cmath>
+#include <vector>
 
 #include "common.cuh"
 
@@ -11,14 +12,14 @@ namespace tbk {
 
 // w = H v - beta * vprev (beta read from the device; vprev may be NULL), and per-CTA partial
 // sums of w . v.  One thread per orbital row.
-__global__ void lz_spmv(int n_atoms, int B, const int32_t* __restrict__ row_ptr,
-                        const int32_t* __restrict__ col, const double* __restrict__ H,
-                        const double* __restrict__ v, const double* __restrict__ vprev,
-                        const double* __restrict__ beta, double* __restrict__ w,
-                        double* __restrict__ part) {
+__device__ __forceinline__ void lz_spmv_cta(int cta, int n_atoms, int B, const int32_t* __restrict__ row_ptr,
+                                            const int32_t* __restrict__ col, const double* __restrict__ H,
+                                            const double* __restrict__ v, const double* __restrict__ vprev,
+                                            const double* __restrict__ beta, double* __restrict__ w,
+                                            double* __restrict__ part) {
   __shared__ double red[32];
   const int64_t n = (int64_t)n_atoms * B;
-  const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t row = (int64_t)cta * blockDim.x + threadIdx.x;
   double d = 0.0;
   if (row < n) {
     const int a = (int)(row / B), i = (int)(row - (int64_t)a * B);
@@ -33,14 +34,23 @@ __global__ void lz_spmv(int n_atoms, int B, const int32_t* __restrict__ row_ptr,
     d = acc * v[row];
   }
   double t = tbk_block_sum(d, red);
-  if (threadIdx.x == 0) part[blockIdx.x] = t;
+  if (threadIdx.x == 0) part[cta] = t;
+}
+
+__global__ void lz_spmv(int n_atoms, int B, const int32_t* __restrict__ row_ptr,
+                        const int32_t* __restrict__ col, const double* __restrict__ H,
+                        const double* __restrict__ v, const double* __restrict__ vprev,
+                        const double* __restrict__ beta, double* __restrict__ w,
+                        double* __restrict__ part) {
+  lz_spmv_cta(blockIdx.x, n_atoms, B, row_ptr, col, H, v, vprev, beta, w, part);
 }
 
 // w -= alpha v; per-CTA partial sums of w . w.
-__global__ void lz_orth(int64_t n, const double* __restrict__ v, const double* __restrict__ alpha,
-                        double* __restrict__ w, double* __restrict__ part) {
+__device__ __forceinline__ void lz_orth_cta(int cta, int64_t n, const double* __restrict__ v,
+                                            const double* __restrict__ alpha, double* __restrict__ w,
+                                            double* __restrict__ part) {
   __shared__ double red[32];
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t i = (int64_t)cta * blockDim.x + threadIdx.x;
   double d = 0.0;
   if (i < n) {
     double x = w[i] - (*alpha) * v[i];
@@ -48,16 +58,26 @@ __global__ void lz_orth(int64_t n, const double* __restrict__ v, const double* _
     d = x * x;
   }
   double t = tbk_block_sum(d, red);
-  if (threadIdx.x == 0) part[blockIdx.x] = t;
+  if (threadIdx.x == 0) part[cta] = t;
+}
+
+__global__ void lz_orth(int64_t n, const double* __restrict__ v, const double* __restrict__ alpha,
+                        double* __restrict__ w, double* __restrict__ part) {
+  lz_orth_cta(blockIdx.x, n, v, alpha, w, part);
 }
 
 // out = sum(part) (take_sqrt: sqrt of it), single block, fixed order.
-__global__ void lz_reduce(const double* __restrict__ part, int m, int take_sqrt, double* __restrict__ out) {
+__device__ __forceinline__ void lz_reduce_block(const double* __restrict__ part, int m, int take_sqrt,
+                                                double* __restrict__ out) {
   __shared__ double red[32];
   double s = 0.0;
   for (int i = threadIdx.x; i < m; i += blockDim.x) s += part[i];
   double t = tbk_block_sum(s, red);
   if (threadIdx.x == 0) *out = take_sqrt ? sqrt(t) : t;
+}
+
+__global__ void lz_reduce(const double* __restrict__ part, int m, int take_sqrt, double* __restrict__ out) {
+  lz_reduce_block(part, m, take_sqrt, out);
 }
 
 // v_next = w / beta (written over w).
@@ -70,6 +90,70 @@ __global__ void lz_scale(int64_t n, const double* __restrict__ beta, double* __r
 __global__ void lz_start(int64_t n, uint64_t seed, double* __restrict__ v) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) v[i] = (double)tbk_probe_sign(seed, i, 0) / sqrt((double)n);
+}
+
+// ---- many clusters: the same kernels, blockIdx.y = cluster ---------------------------------
+struct LzJob {
+  int n_atoms, B, nb, m;
+  const int32_t* row_ptr;
+  const int32_t* col;
+  const double* H;
+  double* vecs;  // vp, v, w (n each), part (nb), alpha (m + 2), beta (m + 2)
+  int64_t n;
+  uint64_t seed;
+};
+
+__device__ __forceinline__ void lz_ptrs(const LzJob& j, int step, double*& vp, double*& v, double*& w) {
+  // the rotation vp <- v, v <- w, w <- old vp of the single-cluster loop, by step parity mod 3
+  double* base[3] = {j.vecs, j.vecs + j.n, j.vecs + 2 * j.n};
+  vp = base[step % 3];
+  v = base[(step + 1) % 3];
+  w = base[(step + 2) % 3];
+}
+
+__global__ void lzb_start(const LzJob* __restrict__ jobs) {
+  const LzJob j = jobs[blockIdx.y];
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < j.n) j.vecs[j.n + i] = (double)tbk_probe_sign(j.seed, i, 0) / sqrt((double)j.n);
+}
+
+__global__ void lzb_spmv(const LzJob* __restrict__ jobs, int step) {
+  const LzJob j = jobs[blockIdx.y];
+  if (step >= j.m || (int)blockIdx.x >= j.nb) return;
+  double *vp, *v, *w;
+  lz_ptrs(j, step, vp, v, w);
+  double* part = j.vecs + 3 * j.n;
+  double* beta = part + j.nb + (j.m + 2);
+  lz_spmv_cta(blockIdx.x, j.n_atoms, j.B, j.row_ptr, j.col, j.H, v, step ? vp : nullptr, beta + step, w, part);
+}
+
+__global__ void lzb_reduce(const LzJob* __restrict__ jobs, int step, int take_sqrt) {
+  const LzJob j = jobs[blockIdx.y];
+  if (step >= j.m) return;
+  double* part = j.vecs + 3 * j.n;
+  double* alpha = part + j.nb;
+  double* beta = alpha + (j.m + 2);
+  lz_reduce_block(part, j.nb, take_sqrt, take_sqrt ? beta + step + 1 : alpha + step);
+}
+
+__global__ void lzb_orth(const LzJob* __restrict__ jobs, int step) {
+  const LzJob j = jobs[blockIdx.y];
+  if (step >= j.m || (int)blockIdx.x >= j.nb) return;
+  double *vp, *v, *w;
+  lz_ptrs(j, step, vp, v, w);
+  double* part = j.vecs + 3 * j.n;
+  lz_orth_cta(blockIdx.x, j.n, v, part + j.nb + step, w, part);
+}
+
+__global__ void lzb_scale(const LzJob* __restrict__ jobs, int step) {
+  const LzJob j = jobs[blockIdx.y];
+  if (step >= j.m) return;
+  double *vp, *v, *w;
+  lz_ptrs(j, step, vp, v, w);
+  const double* beta = j.vecs + 3 * j.n + j.nb + (j.m + 2);
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const double b = beta[step + 1];
+  if (i < j.n) w[i] = b > 0.0 ? w[i] / b : 0.0;
 }
 
 // ---- host: tridiagonal eigen-analysis -------------------------------------------------------
@@ -158,6 +242,9 @@ static double tri_last_component(const std::vector<double>& a, const std::vector
   return fabs(z[m - 1]);
 }
 
+void bounds_from_tridiagonal(const std::vector<double>& ha, const std::vector<double>& hb, int m,
+                             double rel_margin, double* emin, double* emax);
+
 }  // namespace tbk
 
 using namespace tbk;
@@ -203,6 +290,15 @@ extern "C" int tbk_spectral_bounds(tbk_ctx* ctx, const tbk_bsr* H, int32_t steps
   TBK_CUDA(cudaMemcpyAsync(ha.data(), alpha, sizeof(double) * m, cudaMemcpyDeviceToHost, ctx->stream));
   TBK_CUDA(cudaMemcpyAsync(hb.data(), beta, sizeof(double) * (m + 1), cudaMemcpyDeviceToHost, ctx->stream));
   sync(ctx);
+  bounds_from_tridiagonal(ha, hb, m, rel_margin, emin, emax);
+  TBK_API_END
+}
+
+namespace tbk {
+// Extreme Ritz values of the Lanczos tridiagonal (alpha ha[0..m), beta hb[1..m]) widened by their
+// residual norms, then by rel_margin of the width on each side.
+void bounds_from_tridiagonal(const std::vector<double>& ha, const std::vector<double>& hb, int m,
+                             double rel_margin, double* emin, double* emax) {
   // Stop at the first (numerically) vanishing beta: the Krylov space is invariant there.
   int mm = m;
   double scale = 0.0;
@@ -220,5 +316,77 @@ extern "C" int tbk_spectral_bounds(tbk_ctx* ctx, const tbk_bsr* H, int32_t steps
   *emin = lo - rel_margin * width;
   *emax = hi + rel_margin * width;
   if (!(*emax > *emin)) *emax = *emin + 1e-12;
+}
+}  // namespace tbk
+
+extern "C" int tbk_batched_spectral_bounds(tbk_ctx* ctx, int32_t n_clusters, const tbk_bsr* H,
+                                           int32_t steps, double rel_margin, uint64_t seed,
+                                           double* emin, double* emax) {
+  TBK_API_BEGIN
+  TBK_CHECK_ARG(ctx && H && emin && emax, "NULL argument");
+  TBK_CHECK_ARG(n_clusters >= 1, "n_clusters must be >= 1");
+  TBK_CHECK_ARG(steps >= 1 && steps <= 10000, "steps must be in [1, 10000]");
+  TBK_CHECK_ARG(rel_margin >= 0.0 && std::isfinite(rel_margin), "rel_margin must be >= 0");
+  DeviceGuard dg(ctx);
+  std::vector<LzJob> jobs(n_clusters);
+  size_t tot = 0;
+  int nb_max = 1, m_max = 1;
+  for (int c = 0; c < n_clusters; ++c) {
+    TBK_CHECK_ARG(H[c].n_orb == 1 || H[c].n_orb == 9, "n_orb must be 1 or 9");
+    TBK_CHECK_ARG(H[c].n_atoms >= 1 && H[c].row_ptr && H[c].col && H[c].val, "empty or NULL matrix");
+    LzJob& j = jobs[c];
+    j.n_atoms = H[c].n_atoms;
+    j.B = H[c].n_orb;
+    j.n = (int64_t)j.n_atoms * j.B;
+    j.m = (int)std::min<int64_t>(steps, j.n);
+    j.nb = ceil_div(j.n, 256);
+    j.row_ptr = H[c].row_ptr;
+    j.col = H[c].col;
+    j.H = H[c].val;
+    j.seed = seed;
+    j.vecs = nullptr;
+    tot += (size_t)(3 * j.n + j.nb + 2 * (j.m + 2));
+    nb_max = std::max(nb_max, j.nb);
+    m_max = std::max(m_max, j.m);
+  }
+  double* vecs = (double*)scratch(ctx, WS_LANCZOS, sizeof(double) * tot);
+  LzJob* d_jobs = (LzJob*)scratch(ctx, WS_MISC, sizeof(LzJob) * (size_t)n_clusters);
+  size_t off = 0;
+  for (int c = 0; c < n_clusters; ++c) {
+    LzJob& j = jobs[c];
+    j.vecs = vecs + off;
+    off += (size_t)(3 * j.n + j.nb + 2 * (j.m + 2));
+    // beta[0] = 0 (the first step has no previous vector)
+    TBK_CUDA(cudaMemsetAsync(j.vecs + 3 * j.n + j.nb + (j.m + 2), 0, sizeof(double) * (j.m + 2), ctx->stream));
+  }
+  TBK_CUDA(cudaMemcpyAsync(d_jobs, jobs.data(), sizeof(LzJob) * n_clusters, cudaMemcpyHostToDevice, ctx->stream));
+  const dim3 g(nb_max, n_clusters), g1(1, n_clusters);
+  lzb_start<<<g, 256, 0, ctx->stream>>>(d_jobs);
+  post_launch(ctx, "lzb_start");
+  for (int step = 0; step < m_max; ++step) {
+    lzb_spmv<<<g, 256, 0, ctx->stream>>>(d_jobs, step);
+    post_launch(ctx, "lzb_spmv");
+    lzb_reduce<<<g1, 256, 0, ctx->stream>>>(d_jobs, step, 0);
+    post_launch(ctx, "lzb_reduce");
+    lzb_orth<<<g, 256, 0, ctx->stream>>>(d_jobs, step);
+    post_launch(ctx, "lzb_orth");
+    lzb_reduce<<<g1, 256, 0, ctx->stream>>>(d_jobs, step, 1);
+    post_launch(ctx, "lzb_reduce");
+    lzb_scale<<<g, 256, 0, ctx->stream>>>(d_jobs, step);
+    post_launch(ctx, "lzb_scale");
+  }
+  std::vector<std::vector<double>> ha(n_clusters), hb(n_clusters);
+  for (int c = 0; c < n_clusters; ++c) {
+    const LzJob& j = jobs[c];
+    ha[c].resize(j.m);
+    hb[c].resize(j.m + 1);
+    const double* alpha = j.vecs + 3 * j.n + j.nb;
+    TBK_CUDA(cudaMemcpyAsync(ha[c].data(), alpha, sizeof(double) * j.m, cudaMemcpyDeviceToHost, ctx->stream));
+    TBK_CUDA(cudaMemcpyAsync(hb[c].data(), alpha + (j.m + 2), sizeof(double) * (j.m + 1), cudaMemcpyDeviceToHost,
+                             ctx->stream));
+  }
+  sync(ctx);
+  for (int c = 0; c < n_clusters; ++c)
+    bounds_from_tridiagonal(ha[c], hb[c], jobs[c].m, rel_margin, emin + c, emax + c);
   TBK_API_END
 }

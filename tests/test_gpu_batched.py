@@ -173,3 +173,16 @@ def test_batched_energies_and_forces_one_call_equals_separate_calls(api, ctx):
         rp, col, Hd = oracle_H(wk)
         est = oracle_estimator(wk, Hd, lo, hi, p)
         assert abs(o[1] - est["Omega"]) / wk.n_atoms < 1e-4
+
+
+def test_batched_spectral_bounds_equal_single_cluster_bounds(api, ctx):
+    """All clusters' Lanczos steps run together, each on its own vectors and scalars: the bounds
+    are those of the single-cluster call, bit for bit, for clusters of different sizes."""
+    b = _batch(api, ctx, [37, 70, 13, 52, 5], [0.5, 0.1, 0.5, 0.5, 0.5])
+    Hs = [x[1] for x in b]
+    lo, hi = api.batched_spectral_bounds(ctx, Hs)
+    for H, l_, h_ in zip(Hs, lo, hi):
+        assert (l_, h_) == api.spectral_bounds(ctx, H)
+    lo2, hi2 = api.batched_spectral_bounds(ctx, Hs, steps=20, margin=0.05, seed=7)
+    for H, l_, h_ in zip(Hs, lo2, hi2):
+        assert (l_, h_) == api.spectral_bounds(ctx, H, steps=20, margin=0.05, seed=7)

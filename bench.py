@@ -528,7 +528,8 @@ def run_batched(args, rank, world):
             marks.append(ev())
         _, obs, _, Fs = api.batched_energies_and_forces(ctx, Hs, model, pos, e0, e1, seeds, s, ps,
                                                         [w.n_electrons for w in wks],
-                                                        [w.kT for w in wks])
+                                                        [w.kT for w in wks],
+                                                        windowed=args.adjoint == "windowed")
         if record:
             marks.append(ev())
             phase_ev.append((marks, Hs, ps))
@@ -540,7 +541,7 @@ def run_batched(args, rank, world):
     clocks = ClockSampler(local, enabled=not args.no_clocks)
     clocks.start()
     l0 = ctx.launches
-    ctx.time_kernels("step", "backward")
+    ctx.time_kernels("step", "backward", "window")
     t0 = torch.cuda.Event(enable_timing=True); t1 = torch.cuda.Event(enable_timing=True)
     t0.record(ctx.stream)
     for _ in range(args.steps):
@@ -548,7 +549,7 @@ def run_batched(args, rank, world):
     t1.record(ctx.stream)
     torch.cuda.synchronize()
     launches = ctx.launches - l0
-    fam = {f: ctx.kernel_time(f) for f in ("step", "backward")}
+    fam = {f: ctx.kernel_time(f) for f in ("step", "backward", "window")}
     ctx.time_kernels()
     ms = t0.elapsed_time(t1) / args.steps
     e_ms = []
@@ -570,18 +571,22 @@ def run_batched(args, rank, world):
         if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     alu = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
-    fb = ff = bb = bf = 0.0
+    windowed = args.adjoint == "windowed"
+    fb = ff = bb = bf = wb = wf = 0.0
     for H, p in zip(Hs, ps_):
         K = p // 2
         panel = H.graph.n_atoms * 9 * s * 4
         blocks = H.graph.nnzb * 81
         fb += K * (3 * panel + blocks * 4)
         ff += K * 2 * blocks * s
-        bb += K * (6 * panel + blocks * 4 + blocks * 16)
-        bf += K * 4 * blocks * s
+        bb += K * (6 * panel + blocks * 4 + (0 if windowed else blocks * 16))
+        bf += K * (2 if windowed else 4) * blocks * s
+        wb += K * 2 * panel + (K / 4 + 1) * blocks * 16
+        wf += K * 2 * blocks * s
     kernels = {}
     for f, by, fl, kname in (("step", fb, ff, "cheb_step_bulk (batched)"),
-                             ("backward", bb, bf, "clenshaw_sddmm_bulk (batched)")):
+                             ("backward", bb, bf, "clenshaw_sddmm_bulk (batched)"),
+                             ("window", wb, wf, "sddmm_window (batched)")):
         tms, nl = fam[f]
         if nl == 0:
             continue
@@ -606,7 +611,7 @@ def run_batched(args, rank, world):
                        "atoms": int(sum(w.n_atoms for w in wks)), "probes": s,
                        "orders_p": [int(p) for p in ps], "kT": [float(w.kT) for w in wks],
                        "l2": "merged panels (%.0f MB each) larger than L2" % (sum(w.n_atoms for w in wks) * 9 * s * 4 / 1e6),
-                       "parallelism": f"replicas x{world}"},
+                       "parallelism": f"replicas x{world}", "adjoint": args.adjoint},
             "e2e": {"value": units * world / (statistics.median(e_ms) / 1e3), "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches,
@@ -644,9 +649,14 @@ def main():
                     help="probe count of the fcc10k workload (default 512; a profiling aid)")
     ap.add_argument("--atom-order", default="radial", choices=["radial", "morton"],
                     help="listing order of the fcc10k atoms (same cluster)")
-    ap.add_argument("--adjoint", default="fused", choices=["fused", "windowed"],
-                    help="outer products inside each backward step, or over windows of 4 steps")
+    ap.add_argument("--adjoint", default="auto", choices=["auto", "fused", "windowed"],
+                    help="outer products inside each backward step, or over windows of 4 steps "
+                         "(auto: fused for 512 probes, windowed for the 128-probe batch)")
     args = ap.parse_args()
+    if args.adjoint == "auto":
+        # measured on GB300: with 512 probes the fused step wins (every tile is read once); with
+        # 128 probes per cluster the per-tile lane reduction dominates and windows of 4 steps win
+        args.adjoint = "windowed" if args.workload == "batched64" else "fused"
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":

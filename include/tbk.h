@@ -265,8 +265,8 @@ int tbk_batched_fermi_level(tbk_ctx* ctx, int32_t n_clusters, const double* mome
    tbk_batched_moments; each cluster joins the sweep at its own order).  Host arrays: H, pos
    (device pointers, n_atoms x 3 each; open clusters), emin, emax, seeds, orders, mu, kT, G and
    forces (device pointers or NULL entries; either array may be NULL).  n_probes 128, 256 or 512
-   for the one-launch path; other shapes run the clusters one after another.  flags: 0 (mixed).
-   Synchronises the stream. */
+   for the one-launch path; other shapes run the clusters one after another.  flags: 0 (mixed),
+   optionally TBK_WINDOWED.  Synchronises the stream. */
 int tbk_batched_density_and_forces(tbk_ctx* ctx, int32_t n_clusters, const tbk_bsr* H,
                                    const tbk_model* model, const double* const* pos,
                                    const double* emin, const double* emax, const uint64_t* seeds,
@@ -281,7 +281,7 @@ int tbk_batched_density_and_forces(tbk_ctx* ctx, int32_t n_clusters, const tbk_b
    separate moment pass runs.  n_electrons: host, per cluster.  moments: device, laid out as
    tbk_batched_moments writes them, or NULL.  observables: host, 4 doubles {mu, Omega, E, N}
    per cluster.  G, forces as in tbk_batched_density_and_forces (either may be NULL).  n_probes
-   a multiple of 128; flags: 0 (mixed).  Synchronises the stream. */
+   a multiple of 128; flags: 0 (mixed), optionally TBK_WINDOWED.  Synchronises the stream. */
 int tbk_batched_energies_and_forces(tbk_ctx* ctx, int32_t n_clusters, const tbk_bsr* H,
                                     const tbk_model* model, const double* const* pos,
                                     const double* emin, const double* emax, const uint64_t* seeds,

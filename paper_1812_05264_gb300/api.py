@@ -269,7 +269,7 @@ def batched_fermi_level(ctx: Context, moments: list, emins, emaxs, n_electrons, 
 def batched_density_and_forces(ctx: Context, Hs: list, model: Model, positions: list, emins,
                                emaxs, seeds, n_probes: int, orders, mus, kTs,
                                jackson: bool = False, want_G: bool = False,
-                               max_panel_bytes: int = 0):
+                               max_panel_bytes: int = 0, windowed: bool = False):
     """a9-a11: (G list or None, forces list) of a batch, backward sweeps in one launch per step."""
     n = len(Hs)
     structs = (L.tbk_bsr * n)(*[h.struct() for h in Hs])
@@ -282,14 +282,15 @@ def batched_density_and_forces(ctx: Context, Hs: list, model: Model, positions: 
     L.call("tbk_batched_density_and_forces", ctx.handle, n, structs, C.byref(model.s), pp,
            arr(emins), arr(emaxs), (C.c_uint64 * n)(*map(int, seeds)), int(n_probes),
            (C.c_int32 * n)(*map(int, orders)), arr(mus), arr(kTs),
-           L.TBK_DAMP_JACKSON if jackson else L.TBK_DAMP_NONE, 0, int(max_panel_bytes), gp, fp)
+           L.TBK_DAMP_JACKSON if jackson else L.TBK_DAMP_NONE, L.TBK_WINDOWED if windowed else 0,
+           int(max_panel_bytes), gp, fp)
     return Gs, Fs
 
 
 def batched_energies_and_forces(ctx: Context, Hs: list, model: Model, positions: list, emins,
                                 emaxs, seeds, n_probes: int, orders, n_electrons, kTs,
                                 jackson: bool = False, want_G: bool = False,
-                                max_panel_bytes: int = 0):
+                                max_panel_bytes: int = 0, windowed: bool = False):
     """a5-a11 for a batch in one call: (moments list, observables (n, 4) array of
     (mu, Omega, E, N), G list or None, forces list)."""
     n = len(Hs)
@@ -306,8 +307,8 @@ def batched_energies_and_forces(ctx: Context, Hs: list, model: Model, positions:
     L.call("tbk_batched_energies_and_forces", ctx.handle, n, structs, C.byref(model.s), pp,
            arr(emins), arr(emaxs), (C.c_uint64 * n)(*map(int, seeds)), int(n_probes),
            (C.c_int32 * n)(*map(int, orders)), arr(n_electrons), arr(kTs),
-           L.TBK_DAMP_JACKSON if jackson else L.TBK_DAMP_NONE, 0, int(max_panel_bytes), _ptr(mom),
-           obs, gp, fp)
+           L.TBK_DAMP_JACKSON if jackson else L.TBK_DAMP_NONE, L.TBK_WINDOWED if windowed else 0,
+           int(max_panel_bytes), _ptr(mom), obs, gp, fp)
     moms = list(torch.split(mom, [int(p) for p in orders]))
     return moms, np.array(obs[:], dtype=np.float64).reshape(n, 4), Gs, Fs
 

@@ -380,7 +380,8 @@ template <int CW>
 __global__ void __launch_bounds__(32 * (CW + 1), CW == 4 ? 1 : 2)
 sddmm_window(const int n_atoms, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
              const WindowPanels wp, const int nw, const uint64_t seed, const int s, const double w,
-             double* __restrict__ Gacc, int* __restrict__ err) {
+             double* __restrict__ Gacc, int* __restrict__ err, const BatchRows batch,
+             const int32_t* __restrict__ kcl, const int k_lo) {
   using C = WinCfg<CW>;
   constexpr int D = C::D, P = C::P;
   extern __shared__ __align__(128) unsigned char smem[];
@@ -410,26 +411,45 @@ sddmm_window(const int n_atoms, const int32_t* __restrict__ row_ptr, const int32
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
+  // per atom: the probe stream and cluster-local row, and how many of the window's steps its
+  // cluster takes part in (a batch's cluster with K_c steps has pairs j = 0 .. K_c - 1 only: the
+  // panels of later steps were never formed on its rows)
+  auto atom_window = [&](int a, int& nwa, uint64_t& sd, int64_t& rloc) {
+    nwa = nw;
+    sd = seed;
+    rloc = (int64_t)9 * a;
+    if (batch.atom_cl) {
+      const int cl = __ldg(batch.atom_cl + a);
+      sd = __ldg(batch.seed + cl);
+      rloc = (int64_t)9 * (a - __ldg(batch.atom0 + cl));
+      if (kcl) nwa = min(nw, max(0, __ldg(kcl + cl) - k_lo));
+    }
+  };
 
   if (warp == CW) {
     // producer warp: lane 0 issues the copies; in the probe case all lanes write the probe block
     int it = 0, y_it = 0;
     bool ok = true;
     for (int a = blockIdx.x; a < n_atoms && ok; a += gridDim.x) {
+      int nwa;
+      uint64_t sd;
+      int64_t rloc;
+      atom_window(a, nwa, sd, rloc);
+      if (nwa == 0) continue;
       if (lane == 0) ok = mbar_wait(y_empty, (y_it & 1) ^ 1);
       ok = __shfl_sync(0xffffffffu, ok, 0);
       if (!ok) break;
       if (probe) {
         for (int e = lane; e < 9 * P; e += 32) {
           const int i = e / P, pr = e - i * P;
-          Yw[e] = tbk_probe_sign(seed, (int64_t)9 * a + i, pr);
+          Yw[e] = tbk_probe_sign(sd, rloc + i, pr);
         }
         __threadfence_block();
         __syncwarp();
         if (lane == 0) mbar_arrive(y_full);
       } else if (lane == 0) {
-        mbar_expect_tx(y_full, nw * C::XB);
-        for (int t = 0; t < nw; ++t)
+        mbar_expect_tx(y_full, nwa * C::XB);
+        for (int t = 0; t < nwa; ++t)
           bulk_g2s(smem_u32(Yw + t * 9 * P), wp.y[t] + (int64_t)9 * a * s, C::XB, y_full);
       }
       ++y_it;
@@ -437,7 +457,7 @@ sddmm_window(const int n_atoms, const int32_t* __restrict__ row_ptr, const int32
         const int k0 = __ldg(row_ptr + a), k1 = __ldg(row_ptr + a + 1);
         for (int q = k0; q < k1 && ok; ++q) {
           const int b = __ldg(col + q);
-          for (int t = 0; t < nw && ok; ++t) {
+          for (int t = 0; t < nwa && ok; ++t) {
             const int st = it % D;
             ok = mbar_wait(empty(st), ((it / D) & 1) ^ 1);
             if (!ok) break;
@@ -461,6 +481,11 @@ sddmm_window(const int n_atoms, const int32_t* __restrict__ row_ptr, const int32
   bool ok = true;
   const int pl = 4 * threadIdx.x;
   for (int a = blockIdx.x; a < n_atoms && ok; a += gridDim.x) {
+    int nwa;
+    uint64_t sd;
+    int64_t rloc;
+    atom_window(a, nwa, sd, rloc);
+    if (nwa == 0) continue;
     const int k0 = __ldg(row_ptr + a), k1 = __ldg(row_ptr + a + 1);
     ok = mbar_wait(y_full, y_it & 1);
     if (!ok) break;
@@ -468,7 +493,7 @@ sddmm_window(const int n_atoms, const int32_t* __restrict__ row_ptr, const int32
       float2 acc[81];
 #pragma unroll
       for (int e = 0; e < 81; ++e) acc[e] = make_float2(0.f, 0.f);
-      for (int t = 0; t < nw; ++t) {
+      for (int t = 0; t < nwa; ++t) {
         const int st = it % D;
         ok = mbar_wait(full(st), (it / D) & 1);
         if (!ok) break;
@@ -710,7 +735,8 @@ void launch_forces(tbk_ctx* ctx, const DevModel& M, const double* pos, int n_ato
 
 template <int CW>
 static void launch_window_cw(tbk_ctx* ctx, const HOp& op, const WindowPanels& wp, int nw, uint64_t seed,
-                             int s, double w, double* Gacc, int* err) {
+                             int s, double w, double* Gacc, int* err, const BatchRows& batch,
+                             const int32_t* kcl, int k_lo) {
   using C = WinCfg<CW>;
   TBK_CUDA(cudaFuncSetAttribute(sddmm_window<CW>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
   int occ = 0;
@@ -718,18 +744,20 @@ static void launch_window_cw(tbk_ctx* ctx, const HOp& op, const WindowPanels& wp
   TBK_CHECK_ARG(occ > 0, "windowed outer-product kernel does not fit on this device");
   const int G = std::max(1, std::min(op.n_atoms, occ * ctx->num_sms));
   sddmm_window<CW><<<G, C::THREADS, C::SMEM, ctx->stream>>>(op.n_atoms, op.row_ptr, op.col, wp, nw, seed,
-                                                             s, w, Gacc, err);
+                                                             s, w, Gacc, err, batch, kcl, k_lo);
   post_launch(ctx, "sddmm_window");
 }
 
-// Gacc_ab += w sum_t sum_probes y_t[a] x_t[b]^T over the stored blocks, 1 <= nw <= SDW steps.
+// Gacc_ab += w sum_t sum_probes y_t[a] x_t[b]^T over the stored blocks, 1 <= nw <= SDW steps
+// (t = 0 is step k_lo).  Batch: per-cluster probe streams, and with kcl (K per cluster) each
+// cluster's steps >= K_c are left out.
 void launch_window(tbk_ctx* ctx, const HOp& op, const WindowPanels& wp, int nw, uint64_t seed, int s,
-                   double w, double* Gacc, int* err) {
+                   double w, double* Gacc, int* err, const BatchRows& batch, const int32_t* kcl, int k_lo) {
   KernelTimerScope timer(ctx, TBK_KERNEL_WINDOW);
   TBK_CHECK_ARG(nw >= 1 && nw <= SDW && (wp.y[0] != nullptr || nw == 1), "bad outer-product window");
-  if (s == 512) launch_window_cw<4>(ctx, op, wp, nw, seed, s, w, Gacc, err);
-  else if (s == 256) launch_window_cw<2>(ctx, op, wp, nw, seed, s, w, Gacc, err);
-  else launch_window_cw<1>(ctx, op, wp, nw, seed, s, w, Gacc, err);
+  if (s == 512) launch_window_cw<4>(ctx, op, wp, nw, seed, s, w, Gacc, err, batch, kcl, k_lo);
+  else if (s == 256) launch_window_cw<2>(ctx, op, wp, nw, seed, s, w, Gacc, err, batch, kcl, k_lo);
+  else launch_window_cw<1>(ctx, op, wp, nw, seed, s, w, Gacc, err, batch, kcl, k_lo);
 }
 
 // ---- adjoint of the doubled moments (TMA-fed fused path) ------------------------------------
@@ -761,7 +789,6 @@ __global__ void ybar_init(int64_t n, int s, float ca, const float* __restrict__ 
 void adjoint_doubling(tbk_ctx* ctx, const HOp& op, uint64_t probe_seed, int s, int p,
                       const std::function<std::vector<double>()>& get_coefs, double* partials, int nctas,
                       int64_t max_panel_bytes, double* Gacc, int* err, bool windowed, const AdjBatch* bt) {
-  TBK_CHECK_ARG(!(bt && windowed), "batched adjoint: no windowed outer products");
   const int K = bt ? (bt->K.empty() ? 0 : bt->K[0]) : p / 2;
   if (K < 1) {
     if (get_coefs) get_coefs();
@@ -940,14 +967,14 @@ void adjoint_doubling(tbk_ctx* ctx, const HOp& op, uint64_t probe_seed, int s, i
             wp.y[t] = (const float*)Y(k + t);
             wp.x[t] = (const float*)YB(k + t + 1);
           }
-          launch_window(ctx, op, wp, nw, probe_seed, s, 2.0, Gacc, err);
+          launch_window(ctx, o, wp, nw, probe_seed, s, 2.0, Gacc, err, br, bt ? bt->d_K : nullptr, k);
         }
       } else if (windowed) {
         // G += y_0 ybar_1^T
         WindowPanels wp{};
         wp.y[0] = nullptr;
         wp.x[0] = (const float*)YB(1);
-        launch_window(ctx, op, wp, 1, probe_seed, s, 1.0, Gacc, err);
+        launch_window(ctx, o, wp, 1, probe_seed, s, 1.0, Gacc, err, br, bt ? bt->d_K : nullptr, 0);
       } else {
         launch_fused(ctx, o, YB(1), nullptr, nullptr, nullptr, make_float4(0.f, 0.f, 0.f, 0.f), probe_seed, s,
                      1.0, Gacc, err, br, nullptr, nullptr, nullptr);

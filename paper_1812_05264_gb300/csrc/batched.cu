@@ -446,7 +446,7 @@ static void batched_adjoint(tbk_ctx* ctx, int ncl, const tbk_bsr* H, const tbk_m
                             const uint64_t* seeds, int s, const int32_t* orders, const double* mu,
                             const double* n_electrons, const double* kT, int damping,
                             int64_t max_panel_bytes, double* moments, double* observables,
-                            double* const* G, double* const* forces) {
+                            double* const* G, double* const* forces, bool windowed) {
   HOp op;
   op.B = 9;
   op.prec = TBK_MIXED;
@@ -569,6 +569,7 @@ static void batched_adjoint(tbk_ctx* ctx, int ncl, const tbk_bsr* H, const tbk_m
   AdjBatch bt;
   bt.br = br;
   bt.cft = d_cft;
+  bt.d_K = d_ks;
   for (int ci = 0; ci < ncl; ++ci) {
     bt.K.push_back(ks[ci]);
     bt.n_at.push_back(n_at[ci]);
@@ -578,7 +579,7 @@ static void batched_adjoint(tbk_ctx* ctx, int ncl, const tbk_bsr* H, const tbk_m
   TBK_CUDA(cudaMemsetAsync(Gacc, 0, sizeof(double) * (size_t)bo * 81, ctx->stream));
   if (mu) {
     build_cft(mu);
-    adjoint_doubling(ctx, op, 0, s, 0, nullptr, nullptr, 0, max_panel_bytes, Gacc, err, false, &bt);
+    adjoint_doubling(ctx, op, 0, s, 0, nullptr, nullptr, 0, max_panel_bytes, Gacc, err, windowed, &bt);
   } else {
     // moments from the forward sweep: per (atom, warp) partials, reduced per cluster
     const int cw = bulk_consumer_warps(op, s);
@@ -641,7 +642,7 @@ static void batched_adjoint(tbk_ctx* ctx, int ncl, const tbk_bsr* H, const tbk_m
       build_cft(mus.data());
       return std::vector<double>();
     };
-    adjoint_doubling(ctx, op, 0, s, 0, after_forward, partials, 0, max_panel_bytes, Gacc, err, false, &bt);
+    adjoint_doubling(ctx, op, 0, s, 0, after_forward, partials, 0, max_panel_bytes, Gacc, err, windowed, &bt);
   }
   // ---- G (symmetrised, per-cluster scale) and forces on the merged pattern ----
   int32_t* tr = (int32_t*)scratch(ctx, WS_TRANSPOSE, sizeof(int32_t) * (size_t)bo);
@@ -689,7 +690,7 @@ extern "C" int tbk_batched_density_and_forces(
   TBK_CHECK_ARG(ctx && H && emin && emax && seeds && orders && mu && kT, "NULL argument");
   TBK_CHECK_ARG(n_clusters >= 1, "n_clusters must be >= 1");
   TBK_CHECK_ARG(G || forces, "nothing to compute: G and forces are both NULL");
-  TBK_CHECK_ARG(flags == 0, "batched adjoint runs in mixed precision; no flags are supported");
+  TBK_CHECK_ARG((flags & ~TBK_WINDOWED) == 0, "batched adjoint runs in mixed precision; unknown flag");
   TBK_CHECK_ARG(!forces || pos, "forces need positions");
   DeviceGuard dg(ctx);
   const int s = n_probes, ncl = n_clusters;
@@ -697,7 +698,7 @@ extern "C" int tbk_batched_density_and_forces(
     // same kernels, one cluster after the other
     for (int c = 0; c < ncl; ++c) {
       const int rc = tbk_density_and_forces(ctx, &H[c], model, pos ? pos[c] : nullptr, nullptr, emin[c],
-                                            emax[c], seeds[c], s, orders[c], mu[c], kT[c], damping, flags,
+                                            emax[c], seeds[c], s, orders[c], mu[c], kT[c], damping, 0,
                                             max_panel_bytes, G ? G[c] : nullptr,
                                             forces ? forces[c] : nullptr);
       if (rc != TBK_OK) throw Error(rc, std::string("cluster ") + std::to_string(c) + ": " + tbk_last_error());
@@ -705,7 +706,7 @@ extern "C" int tbk_batched_density_and_forces(
     return TBK_OK;
   }
   batched_adjoint(ctx, ncl, H, model, pos, emin, emax, seeds, s, orders, mu, nullptr, kT, damping,
-                  max_panel_bytes, nullptr, nullptr, G, forces);
+                  max_panel_bytes, nullptr, nullptr, G, forces, (flags & TBK_WINDOWED) != 0);
   TBK_API_END
 }
 
@@ -719,7 +720,7 @@ extern "C" int tbk_batched_energies_and_forces(
   TBK_CHECK_ARG(ctx && H && emin && emax && seeds && orders && n_electrons && kT && observables,
                 "NULL argument");
   TBK_CHECK_ARG(n_clusters >= 1, "n_clusters must be >= 1");
-  TBK_CHECK_ARG(flags == 0, "batched energies and forces run in mixed precision; no flags are supported");
+  TBK_CHECK_ARG((flags & ~TBK_WINDOWED) == 0, "batched energies and forces run in mixed precision; unknown flag");
   TBK_CHECK_ARG(!forces || pos, "forces need positions");
   TBK_CHECK_ARG(n_probes >= 128 && n_probes % 128 == 0, "batches need n_probes a multiple of 128");
   for (int c = 0; c < n_clusters; ++c)
@@ -745,6 +746,6 @@ extern "C" int tbk_batched_energies_and_forces(
     return TBK_OK;
   }
   batched_adjoint(ctx, ncl, H, model, pos, emin, emax, seeds, s, orders, nullptr, n_electrons, kT, damping,
-                  max_panel_bytes, moments, observables, G, forces);
+                  max_panel_bytes, moments, observables, G, forces, (flags & TBK_WINDOWED) != 0);
   TBK_API_END
 }

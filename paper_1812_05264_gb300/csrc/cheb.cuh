@@ -90,6 +90,7 @@ struct AdjBatch {
   const float4* cft = nullptr;  // device, (K_max + 1) x n_clusters: (probe, y_k, y_{k-1}, y_{k+1})
                                 // coefficients of the source g_k of step k, zero past K_c
   int64_t pstride = 0;          // doubles of moment partials per forward step (per atom and warp)
+  const int32_t* d_K = nullptr;  // device, K per sorted cluster (windowed outer products)
 };
 // Gacc += the unscaled gradient sum_k 2 y_k ybar_{k+1}^T + y_0 ybar_1^T on the pattern (scale 2/W
 // afterwards).  Single system: get_coefs() returns c_0 .. c_{p-1} once y_1 .. y_{p/2} exist

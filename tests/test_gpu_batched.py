@@ -186,3 +186,31 @@ def test_batched_spectral_bounds_equal_single_cluster_bounds(api, ctx):
     lo2, hi2 = api.batched_spectral_bounds(ctx, Hs, steps=20, margin=0.05, seed=7)
     for H, l_, h_ in zip(Hs, lo2, hi2):
         assert (l_, h_) == api.spectral_bounds(ctx, H, steps=20, margin=0.05, seed=7)
+
+
+def test_batched_windowed_outer_products_match_fused(api, ctx):
+    """Windowed outer products over a batch: each cluster's pairs stop at its own K (the rows of
+    steps it never formed are not read); G matches the fused kernel up to FP32 summation order,
+    and segment replays change no bit."""
+    sizes, kTs = [24, 41, 16], [0.5, 0.5, 0.1]
+    b = _batch(api, ctx, sizes, kTs)
+    orders = [61, 48, 7]
+    model = api.Solver(b[0][0], ctx).model
+    Hs, e0, e1, seeds = [x[1] for x in b], [x[2] for x in b], [x[3] for x in b], [x[0].probe_seed for x in b]
+    ne = [x[0].n_electrons for x in b]
+    pos = [torch.as_tensor(x[0].positions, dtype=torch.float64, device="cuda") for x in b]
+    m1, o1, G1, F1 = api.batched_energies_and_forces(ctx, Hs, model, pos, e0, e1, seeds, 128, orders, ne,
+                                                     kTs, want_G=True)
+    m2, o2, G2, F2 = api.batched_energies_and_forces(ctx, Hs, model, pos, e0, e1, seeds, 128, orders, ne,
+                                                     kTs, want_G=True, windowed=True)
+    assert np.array_equal(o1, o2)
+    for g1, g2, f1, f2 in zip(G1, G2, F1, F2):
+        gmax = g1.abs().max().item()
+        assert torch.allclose(g1, g2, rtol=0, atol=2e-6 * gmax)
+        assert torch.allclose(f1, f2, rtol=0, atol=1e-5)
+    panel = sum(sizes) * 9 * 128 * 4
+    # all stored: K_max + 2 + 7 panels = 39; the replay plan for K_max = 30 needs 2 x 4 + 8 + 9 = 25
+    _, _, G3, F3 = api.batched_energies_and_forces(ctx, Hs, model, pos, e0, e1, seeds, 128, orders, ne,
+                                                   kTs, want_G=True, windowed=True, max_panel_bytes=30 * panel)
+    for g2, g3, f2, f3 in zip(G2, G3, F2, F3):
+        assert torch.equal(g2, g3) and torch.equal(f2, f3)

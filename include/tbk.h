@@ -114,6 +114,12 @@ const char* tbk_last_error(void);
 /* Number of kernel launches this context has issued (for launch accounting). */
 int64_t tbk_launch_count(tbk_ctx* ctx);
 
+/* Test of the bounded waits: the next TMA-fed recurrence step launched on ctx gets a producer
+   that copies nothing, so its consumers' waits run out (each gives up after 2 s of wall time)
+   and the call that launched it returns TBK_ERR_TIMEOUT.  Nothing faults; the context stays
+   usable and the next calls compute normally.  Host-side only. */
+int tbk_test_stall_next_step(tbk_ctx* ctx);
+
 /* Kernel families that tbk_kernel_timer can bracket with CUDA events. */
 #define TBK_KERNEL_NONE 0
 #define TBK_KERNEL_STEP 1     /* one recurrence step y_{k+1} = 2 H^ y_k - y_{k-1} (Eq. cheb_rec) */

@@ -70,6 +70,7 @@ _U = C.c_uint64
 SIGNATURES = {
     "tbk_create": [C.POINTER(_P), C.c_int, _P],
     "tbk_destroy": [_P],
+    "tbk_test_stall_next_step": [_P],
     "tbk_kernel_timer": [_P, _I],
     "tbk_kernel_timer_read": [_P, _I, C.POINTER(_D), C.POINTER(_L)],
     "tbk_build_neighbors": [_P, _P, _I, _P, _D, _P, _P, _L, C.POINTER(_L)],

@@ -52,6 +52,7 @@ struct tbk_ctx {
   size_t slot_bytes[tbk::WS_NSLOTS] = {};
   void* pinned = nullptr;        // small pinned host buffer for scalar read-back
   size_t pinned_bytes = 0;
+  int stall_next_step = 0;       // test hook: the next TMA-fed step's producer issues no copies
   int timed_mask = 0;            // bit f set: launches of kernel family f are bracketed by events
   std::vector<cudaEvent_t> timer_events;  // (begin, end) pairs
   std::vector<int> timer_family;          // family of each pair

@@ -269,7 +269,7 @@ cheb_step_bulk(const int n_atoms, const int32_t* __restrict__ row_ptr, const int
                const float* __restrict__ hv, const float* __restrict__ yin, const float* yprev,
                float* yout, const float alpha, const float c_r, const uint64_t seed, const int s,
                const int direct, double* __restrict__ partials, int* __restrict__ err,
-               const BatchRows batch, const int per_task) {
+               const BatchRows batch, const int per_task, const int stall) {
   using C = BulkCfg<CW, D>;
   // every tile, the diagonal one included, streams through a ring of R = D + 1 stages; the
   // epilogue reads the row's own y_in values (for the moment partials) from global memory
@@ -295,7 +295,8 @@ cheb_step_bulk(const int n_atoms, const int32_t* __restrict__ row_ptr, const int
 
   if (warp == CW) {
     // ---------------- producer ----------------
-    if (lane == 0) {
+    // (stall: a test of the bounded waits; nothing is copied, the consumers give up and report)
+    if (lane == 0 && !stall) {
       int it = 0;
       bool ok = true;
       for (int task = blockIdx.x; task < n_tasks && ok; task += gridDim.x) {
@@ -550,7 +551,8 @@ static void launch_bulk(tbk_ctx* ctx, const HOp& op, const StepArgs& a, int G) {
   cheb_step_bulk<CW, BULK_D><<<G, C::THREADS, C::SMEM, ctx->stream>>>(
       op.n_atoms, op.row_ptr, op.col, (const float*)op.hv, (const float*)a.yin, (const float*)a.yprev,
       (float*)a.yout, (float)a.alpha, (float)a.c_r, a.seed, a.s, a.direct, a.partials, a.err,
-      a.batch, a.per_task);
+      a.batch, a.per_task, ctx->stall_next_step);
+  ctx->stall_next_step = 0;
   post_launch(ctx, "cheb_step_bulk");
 }
 

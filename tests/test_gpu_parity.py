@@ -424,3 +424,20 @@ def test_windowed_outer_products_match_fused(api, ctx, s, p):
     est = oracle_estimator(wk, H, res.emin, res.emax, p)
     _, F = oracle_estimator_forces(wk, rp, col, est, res.emin, res.emax, p)
     assert np.abs(F2.cpu().numpy() - F).max() < 1e-3
+
+
+def test_bounded_wait_reports_timeout_and_context_recovers(api, ctx):
+    """A recurrence step whose producer copies nothing: the consumers' waits give up after their
+    wall-time limit, the call returns TBK_ERR_TIMEOUT, nothing faults, and the same context then
+    computes the same moments as before."""
+    from paper_1812_05264_gb300 import _lib as L
+    wk = small_fcc(40, n_probes=128)
+    sv, pos, res = _gpu_run(api, ctx, wk, 30, fp64=False)
+    args = (ctx, res.H, res.emin, res.emax, wk.probe_seed, 128, 30, False)
+    m0 = api.chebyshev_moments(*args)
+    L.call("tbk_test_stall_next_step", ctx.handle)
+    with pytest.raises(L.TbkError) as e:
+        api.chebyshev_moments(*args)
+    assert e.value.code == L.TBK_ERR_TIMEOUT
+    m1 = api.chebyshev_moments(*args)
+    assert torch.equal(m0, m1)

@@ -138,8 +138,9 @@ def oracle_sample(wk_full, n_atoms: int = SAMPLE_ATOMS):
     return wk
 
 
-def oracle_step(wk):
-    """Exact estimator energies + forces for wk by the oracle (dense FP64); returns (units, s)."""
+def oracle_step(wk, want=False):
+    """Exact estimator energies + forces for wk by the oracle (dense FP64); returns (units, s, p)
+    and, with want, the bounds, mu, Omega, E and forces."""
     from oracle import chebyshev as och, hamiltonian as oham, neighbors as onb, physics as oph
     t0 = time.perf_counter()
     rp, col = onb.neighbor_csr(wk.positions, wk.cutoff, wk.box)
@@ -151,11 +152,13 @@ def oracle_step(wk):
     R = och.probes(H.shape[0], wk.n_probes, wk.probe_seed)
     mom = och.exact_moments(w, V, R, emin, emax, p)
     mu = och.estimator_mu(mom, emin, emax, wk.n_electrons, wk.kT)
-    och.estimator_observables(mom, emin, emax, mu, wk.kT)
+    Om, E, _ = och.estimator_observables(mom, emin, emax, mu, wk.kT)
     G = och.estimator_gradient(w, V, R, emin, emax, mu, wk.kT, p=p)
     a, b, dH = oham.sk_bond_grads(wk.positions, rp, col, wk.sk_V, wl.SK_R0, wl.SK_DECAY, wk.box)
-    oph.forces_from_blocks(G, a, b, dH, wk.n_atoms, 9)
+    F = oph.forces_from_blocks(G, a, b, dH, wk.n_atoms, 9)
     dt = time.perf_counter() - t0
+    if want:
+        return wk.n_atoms * wk.n_probes * p, dt, p, dict(emin=emin, emax=emax, mu=mu, Omega=Om, E=E, F=F)
     return wk.n_atoms * wk.n_probes * p, dt, p
 
 
@@ -370,6 +373,8 @@ def run_ours(args, rank, world):
         kernels[f] = r
     dom = max(kernels, key=lambda f: kernels[f]["share_of_step"])
     roof = dict(kernels[dom])
+    # (the fused schedule's y_0 launch is an outer product only)
+    n_products = (fam["step"][1] + fam["backward"][1]) / args.steps - (0 if windowed else 1)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -388,6 +393,10 @@ def run_ours(args, rank, world):
         "gpu_launches": launches,
         "roofline": roof,
         "kernels": {f: {k: v for k, v in r.items() if k != "peak_source"} for f, r in kernels.items()},
+        # the same rate counting the block products actually run (the doubling identities need
+        # K = p/2 forward and K - 1 backward products for p moments and their gradient)
+        "spmm_rate": {"value": wk.n_atoms * wk.n_probes * n_products * world / (ms / 1e3),
+                      "unit": "atom*vector*block-products/s", "block_products_per_step": n_products},
         "clocks": clk,
         "observables_per_atom": {"mu": obs[0], "Omega": obs[1] / wk.n_atoms,
                                  "E": obs[2] / wk.n_atoms, "N": obs[3] / wk.n_atoms},
@@ -395,7 +404,20 @@ def run_ours(args, rank, world):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         swk = oracle_sample(wk)
         if swk is not None:
-            u, dt, ps = oracle_step(swk)
+            u, dt, ps, ref = oracle_step(swk, want=True)
+            # the same estimator on the GPU (same probes, order and bounds): errors of the
+            # benchmarked precision against the FP64 oracle
+            ssv = api.Solver(swk, ctx)
+            spos = torch.as_tensor(swk.positions, dtype=torch.float64, device=f"cuda:{local}")
+            sres = ssv.energies_and_forces(spos, order=ps, bounds=(ref["emin"], ref["emax"]))
+            line["accuracy_vs_oracle"] = {
+                "sample": f"first {swk.n_atoms} atoms, {swk.n_probes} probes, p={ps}, "
+                          f"{'FP64' if fp64 else 'FP32 recurrence, FP64 moments'}",
+                "omega_per_atom_abs_eV": abs(sres.Omega - ref["Omega"]) / swk.n_atoms,
+                "energy_per_atom_abs_eV": abs(sres.E - ref["E"]) / swk.n_atoms,
+                "mu_abs_eV": abs(sres.mu - ref["mu"]),
+                "force_max_abs_eV_per_A": float(np.abs(sres.forces.cpu().numpy() - ref["F"]).max()),
+                "tolerances": {"energy_per_atom_eV": 1e-6 if fp64 else 1e-4, "force_eV_per_A": 1e-3}}
             line["cpu_baseline"] = {
                 "value": u / dt, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
                 "sample": (f"FP64 oracle (dense eigh, exact estimator, Daleckii-Krein forces) on "

@@ -53,6 +53,8 @@ typedef enum {
 #define TBK_TENSOR_CORES 16    /* mixed mode: recurrence steps on the tensor cores (tcgen05, TF32 x3) */
 #define TBK_WINDOWED 32        /* adjoint: outer products summed over windows of 4 steps by their own
                                   kernel instead of inside each backward step */
+#define TBK_FUSED_ADJOINT 64   /* adjoint: outer products inside each backward step, whatever
+                                  tbk_autotune chose */
 
 /* Damping of the Chebyshev series. */
 #define TBK_DAMP_NONE 0
@@ -119,6 +121,16 @@ int64_t tbk_launch_count(tbk_ctx* ctx);
    and the call that launched it returns TBK_ERR_TIMEOUT.  Nothing faults; the context stays
    usable and the next calls compute normally.  Host-side only. */
 int tbk_test_stall_next_step(tbk_ctx* ctx);
+
+/* tbk_autotune: time, on this operator (9x9 blocks, mixed precision) with n_probes a multiple
+   of 128, the probe chunk (128, 256 or 512 probes) per task of the TMA-fed recurrence step and
+   the adjoint's outer-product schedule (fused into each backward step, or windows of 4 steps),
+   and keep the faster of each in the context for every later call on an operator of the same
+   shape (rows, stored blocks) and probe count.  All choices give the same results up to FP32
+   summation order.  choice: host, 2 ints {probes per task, windowed (0/1)}.  Runs a few dozen
+   kernels on scratch panels; synchronises the stream. */
+int tbk_autotune(tbk_ctx* ctx, const tbk_bsr* H, double emin, double emax, int32_t n_probes,
+                 int32_t* choice);
 
 /* Kernel families that tbk_kernel_timer can bracket with CUDA events. */
 #define TBK_KERNEL_NONE 0
@@ -222,7 +234,8 @@ int tbk_fermi_level(tbk_ctx* ctx, const double* moments, int32_t order, double e
    G: device, nnzb * n_orb^2 FP64, or NULL.  forces: device, n_atoms x 3 FP64, or NULL;
    F_c = -sum_ab <G_ab, dH_ab/dR_c> needs model->kind == TBK_MODEL_SK and pos (device) / box as
    in tbk_assemble_H.  flags: TBK_MIXED or TBK_FP64, optionally | TBK_PLAIN_KERNEL |
-   TBK_WINDOWED (both ways give the same G up to FP32 summation order). */
+   TBK_WINDOWED or TBK_FUSED_ADJOINT (both ways give the same G up to FP32 summation order;
+   without either, the schedule tbk_autotune chose for this shape, else fused). */
 int tbk_density_and_forces(tbk_ctx* ctx, const tbk_bsr* H, const tbk_model* model,
                            const double* pos, const double* box, double emin, double emax,
                            uint64_t probe_seed, int32_t n_probes, int32_t order, double mu,
@@ -234,7 +247,8 @@ int tbk_density_and_forces(tbk_ctx* ctx, const tbk_bsr* H, const tbk_model* mode
    512 the forward sweep of the adjoint produces the moments as it goes, so no separate moment
    pass runs.  moments: device, order doubles, or NULL.  observables: host, 4 doubles {mu, Omega,
    E, N}.  G, forces as in tbk_density_and_forces (either may be NULL).  flags: TBK_MIXED or
-   TBK_FP64, optionally | TBK_PLAIN_KERNEL | TBK_WINDOWED.  Synchronises the stream. */
+   TBK_FP64, optionally | TBK_PLAIN_KERNEL | TBK_WINDOWED | TBK_FUSED_ADJOINT.  Synchronises
+   the stream. */
 int tbk_energies_and_forces(tbk_ctx* ctx, const tbk_bsr* H, const tbk_model* model,
                             const double* pos, const double* box, double emin, double emax,
                             uint64_t probe_seed, int32_t n_probes, int32_t order,

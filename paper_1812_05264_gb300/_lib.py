@@ -25,6 +25,7 @@ TBK_PLAIN_KERNEL = 4
 TBK_NO_GRAPH = 8
 TBK_TENSOR_CORES = 16
 TBK_WINDOWED = 32
+TBK_FUSED_ADJOINT = 64
 TBK_DAMP_NONE = 0
 TBK_DAMP_JACKSON = 1
 TBK_FN_FERMI = 0
@@ -71,6 +72,7 @@ SIGNATURES = {
     "tbk_create": [C.POINTER(_P), C.c_int, _P],
     "tbk_destroy": [_P],
     "tbk_test_stall_next_step": [_P],
+    "tbk_autotune": [_P, C.POINTER(tbk_bsr), _D, _D, _I, C.POINTER(_I)],
     "tbk_kernel_timer": [_P, _I],
     "tbk_kernel_timer_read": [_P, _I, C.POINTER(_D), C.POINTER(_L)],
     "tbk_build_neighbors": [_P, _P, _I, _P, _D, _P, _P, _L, C.POINTER(_L)],

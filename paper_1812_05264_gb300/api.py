@@ -137,6 +137,13 @@ def _box_arg(box):
     return arr, C.cast(arr, C.c_void_p)
 
 
+def _schedule_flag(windowed) -> int:
+    """None: the tuned schedule (else fused); True / False: windowed / fused outer products."""
+    if windowed is None:
+        return 0
+    return L.TBK_WINDOWED if windowed else L.TBK_FUSED_ADJOINT
+
+
 def build_neighbors(ctx: Context, pos: torch.Tensor, cutoff: float, box=None) -> Graph:
     """a1: CSR of all pairs with |r_j - r_i| <= cutoff (self included), ascending columns."""
     assert pos.is_cuda and pos.dtype == torch.float64 and pos.is_contiguous()
@@ -182,6 +189,14 @@ def batched_spectral_bounds(ctx: Context, Hs: list, steps: int = 64, margin: flo
     return list(lo), list(hi)
 
 
+def autotune(ctx: Context, H: BSR, emin: float, emax: float, n_probes: int) -> tuple[int, bool]:
+    """Time the recurrence step's probe chunk and the adjoint's schedule on this operator and keep
+    the faster in the context for its shape: (probes per task, windowed)."""
+    out = (C.c_int32 * 2)()
+    L.call("tbk_autotune", ctx.handle, C.byref(H.struct()), float(emin), float(emax), int(n_probes), out)
+    return int(out[0]), bool(out[1])
+
+
 def chebyshev_coefficients(ctx: Context, fn: int, order: int, emin: float, emax: float, mu: float,
                            kT: float, jackson: bool = False, device=None) -> torch.Tensor:
     """a4: damped Chebyshev coefficients of f, e f or g on [emin, emax]."""
@@ -221,7 +236,7 @@ def density_and_forces(ctx: Context, H: BSR, model: Model | None, pos: torch.Ten
                        emin: float, emax: float, seed: int, n_probes: int, order: int, mu: float,
                        kT: float, jackson: bool = False, fp64: bool = False, want_G: bool = True,
                        want_forces: bool = True, max_panel_bytes: int = 0, plain: bool = False,
-                       windowed: bool = False):
+                       windowed: bool | None = None):
     """a9-a10: (G, F) with G = dOmega^/dH (nnzb, b, b) and F = -dOmega^/dR (N, 3)."""
     dev = H.val.device
     G = torch.empty_like(H.val) if want_G else None
@@ -232,7 +247,7 @@ def density_and_forces(ctx: Context, H: BSR, model: Model | None, pos: torch.Ten
            C.c_uint64(seed), int(n_probes), int(order), float(mu), float(kT),
            L.TBK_DAMP_JACKSON if jackson else L.TBK_DAMP_NONE,
            (L.TBK_FP64 if fp64 else L.TBK_MIXED) | (L.TBK_PLAIN_KERNEL if plain else 0)
-           | (L.TBK_WINDOWED if windowed else 0),
+           | _schedule_flag(windowed),
            int(max_panel_bytes), _ptr(G), _ptr(F))
     return G, F
 
@@ -317,7 +332,7 @@ def energies_and_forces(ctx: Context, H: BSR, model: Model | None, pos: torch.Te
                         emin: float, emax: float, seed: int, n_probes: int, order: int,
                         n_electrons: float, kT: float, jackson: bool = False, fp64: bool = False,
                         want_G: bool = False, want_forces: bool = True, max_panel_bytes: int = 0,
-                        windowed: bool = False):
+                        windowed: bool | None = None):
     """a5-a10 in one call: (moments, (mu, Omega, E, N), G or None, forces or None)."""
     dev = H.val.device
     mom = torch.empty(order, dtype=torch.float64, device=dev)
@@ -329,7 +344,7 @@ def energies_and_forces(ctx: Context, H: BSR, model: Model | None, pos: torch.Te
            C.byref(model.s) if model is not None else None, _ptr(pos), bx, emin, emax,
            C.c_uint64(seed), int(n_probes), int(order), float(n_electrons), float(kT),
            L.TBK_DAMP_JACKSON if jackson else L.TBK_DAMP_NONE,
-           (L.TBK_FP64 if fp64 else L.TBK_MIXED) | (L.TBK_WINDOWED if windowed else 0),
+           (L.TBK_FP64 if fp64 else L.TBK_MIXED) | _schedule_flag(windowed),
            int(max_panel_bytes), _ptr(mom), obs, _ptr(G), _ptr(F))
     return mom, tuple(obs[:]), G, F
 

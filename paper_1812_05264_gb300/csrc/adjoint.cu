@@ -987,6 +987,17 @@ void adjoint_doubling(tbk_ctx* ctx, const HOp& op, uint64_t probe_seed, int s, i
 
 using namespace tbk;
 
+namespace tbk {
+// The adjoint's outer-product schedule: TBK_WINDOWED or TBK_FUSED_ADJOINT when given, else what
+// tbk_autotune measured for this shape, else fused.
+static bool windowed_schedule(const tbk_ctx* ctx, const HOp& op, int s, int flags) {
+  if (flags & TBK_WINDOWED) return true;
+  if (flags & TBK_FUSED_ADJOINT) return false;
+  const tbk_ctx::Tuned* t = find_tuned(ctx, op.n_rows, op.nnzb, s);
+  return t && t->windowed;
+}
+}  // namespace tbk
+
 extern "C" int tbk_density_and_forces(tbk_ctx* ctx, const tbk_bsr* H, const tbk_model* model,
                                       const double* pos, const double* box, double emin,
                                       double emax, uint64_t probe_seed, int32_t n_probes,
@@ -998,7 +1009,7 @@ extern "C" int tbk_density_and_forces(tbk_ctx* ctx, const tbk_bsr* H, const tbk_
   TBK_CHECK_ARG(G || forces, "nothing to compute: G and forces are both NULL");
   TBK_CHECK_ARG(order >= 1, "order must be >= 1");
   TBK_CHECK_ARG(n_probes >= 4 && n_probes % 4 == 0, "n_probes must be a positive multiple of 4");
-  TBK_CHECK_ARG((flags & ~(TBK_FP64 | TBK_PLAIN_KERNEL | TBK_WINDOWED)) == 0, "unknown flag");
+  TBK_CHECK_ARG((flags & ~(TBK_FP64 | TBK_PLAIN_KERNEL | TBK_WINDOWED | TBK_FUSED_ADJOINT)) == 0, "unknown flag");
   const int plain = (flags & TBK_PLAIN_KERNEL) ? 1 : 0;
   TBK_CHECK_ARG(kT > 0.0, "kT must be positive");
   DeviceGuard dg(ctx);
@@ -1036,7 +1047,7 @@ extern "C" int tbk_density_and_forces(tbk_ctx* ctx, const tbk_bsr* H, const tbk_
   double scale = 2.0 / (W * s);
   if (fused) {
     adjoint_doubling(ctx, op, probe_seed, s, p, [&]() { return c; }, nullptr, 0, max_panel_bytes, Gacc, err,
-                       (flags & TBK_WINDOWED) != 0, nullptr);
+                       windowed_schedule(ctx, op, s, flags), nullptr);
     scale = 2.0 / W;  // the 1/s of the moments is inside the source terms
   } else {
     // Panels y_1 .. y_{p-2} are needed in reverse order: all of them are kept when they fit the
@@ -1183,7 +1194,7 @@ extern "C" int tbk_energies_and_forces(tbk_ctx* ctx, const tbk_bsr* H, const tbk
   TBK_CHECK_ARG(ctx != nullptr && observables != nullptr, "NULL argument");
   TBK_CHECK_ARG(order >= 1, "order must be >= 1");
   TBK_CHECK_ARG(n_probes >= 4 && n_probes % 4 == 0, "n_probes must be a positive multiple of 4");
-  TBK_CHECK_ARG((flags & ~(TBK_FP64 | TBK_PLAIN_KERNEL | TBK_WINDOWED)) == 0, "unknown flag");
+  TBK_CHECK_ARG((flags & ~(TBK_FP64 | TBK_PLAIN_KERNEL | TBK_WINDOWED | TBK_FUSED_ADJOINT)) == 0, "unknown flag");
   TBK_CHECK_ARG(kT > 0.0 && n_electrons >= 0.0, "kT must be positive and n_electrons >= 0");
   DeviceGuard dg(ctx);
   const int prec = (flags & TBK_FP64) ? TBK_FP64 : TBK_MIXED;
@@ -1194,7 +1205,8 @@ extern "C" int tbk_energies_and_forces(tbk_ctx* ctx, const tbk_bsr* H, const tbk
   if (!H || !fused_eligible(shape, n_probes, plain)) {
     // the separate calls give the same results for the other shapes and precisions
     double* mom = moments ? moments : (double*)scratch(ctx, WS_SEGMENT, sizeof(double) * (size_t)order);
-    int rc = tbk_chebyshev_moments(ctx, H, emin, emax, probe_seed, n_probes, order, flags & ~TBK_WINDOWED, mom);
+    int rc = tbk_chebyshev_moments(ctx, H, emin, emax, probe_seed, n_probes, order,
+                                   flags & ~(TBK_WINDOWED | TBK_FUSED_ADJOINT), mom);
     if (rc != TBK_OK) throw Error(rc, tbk_last_error());
     rc = tbk_fermi_level(ctx, mom, order, emin, emax, n_electrons, 0.0, kT, damping, observables);
     if (rc != TBK_OK) throw Error(rc, tbk_last_error());
@@ -1258,7 +1270,7 @@ extern "C" int tbk_energies_and_forces(tbk_ctx* ctx, const tbk_bsr* H, const tbk
     return c;
   };
   adjoint_doubling(ctx, op, probe_seed, s, p, after_forward, partials, nctas, max_panel_bytes, Gacc, err,
-                   (flags & TBK_WINDOWED) != 0, nullptr);
+                   windowed_schedule(ctx, op, s, flags), nullptr);
   double* Gout = G ? G : Gsym;
   const int64_t tot = op.nnzb * BB;
   symmetrize<9><<<(unsigned)((tot + 255) / 256), 256, 0, ctx->stream>>>(op.nnzb, tr, Gacc, 2.0 / W, Gout);

@@ -53,6 +53,11 @@ struct tbk_ctx {
   void* pinned = nullptr;        // small pinned host buffer for scalar read-back
   size_t pinned_bytes = 0;
   int stall_next_step = 0;       // test hook: the next TMA-fed step's producer issues no copies
+  struct Tuned {                 // tbk_autotune's choices, per operator shape and probe count
+    int64_t n_rows, nnzb;
+    int s, cw, windowed;
+  };
+  std::vector<Tuned> tuned;
   int timed_mask = 0;            // bit f set: launches of kernel family f are bracketed by events
   std::vector<cudaEvent_t> timer_events;  // (begin, end) pairs
   std::vector<int> timer_family;          // family of each pair
@@ -74,6 +79,8 @@ struct DeviceGuard {
   ~DeviceGuard();
 };
 void sync(tbk_ctx* ctx);
+// The tuned choice for an operator of n_rows rows and nnzb blocks at s probes, or NULL.
+const tbk_ctx::Tuned* find_tuned(const tbk_ctx* ctx, int64_t n_rows, int64_t nnzb, int s);
 // Device bytes that slot s may grow to: what is free plus what s already holds, less a reserve
 // of 2 GiB + 3 % of the device for everything else.
 size_t panel_budget(tbk_ctx* ctx, Slot s);

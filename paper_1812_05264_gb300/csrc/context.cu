@@ -77,6 +77,12 @@ DeviceGuard::~DeviceGuard() {
 
 void sync(tbk_ctx* ctx) { TBK_CUDA(cudaStreamSynchronize(ctx->stream)); }
 
+const tbk_ctx::Tuned* find_tuned(const tbk_ctx* ctx, int64_t n_rows, int64_t nnzb, int s) {
+  for (const auto& t : ctx->tuned)
+    if (t.n_rows == n_rows && t.nnzb == nnzb && t.s == s) return &t;
+  return nullptr;
+}
+
 static void timer_record(tbk_ctx* ctx) {
   if (ctx->timer_used == ctx->timer_events.size()) {
     cudaEvent_t e;

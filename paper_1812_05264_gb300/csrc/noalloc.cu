@@ -70,6 +70,8 @@ extern "C" int tbk_chebyshev_moments_noalloc(tbk_ctx* ctx, const tbk_bsr* H, dou
   shape.B = H->n_orb;
   shape.prec = prec;
   shape.n_atoms = H->n_atoms;
+  shape.n_rows = n_rows;    // the grid follows any tuned choice for this shape, as the steps do
+  shape.nnzb = H->nnzb;
   const int nctas = step_grid_ctas(ctx, shape, s);
   // layout: flag | sums | partials | mapped H | panel A | panel B, each 256-byte aligned
   const size_t o_flag = 0;

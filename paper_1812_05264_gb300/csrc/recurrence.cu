@@ -486,6 +486,16 @@ static int bulk_warps(const HOp& op, int s) {
 
 int bulk_consumer_warps(const HOp& op, int s) { return bulk_warps(op, s); }
 
+// Consumer warps (probe chunk 128 cw per task) of the TMA-fed step for this operator: the tuned
+// choice when tbk_autotune measured this shape, else the widest chunk.  Per-task partial sums
+// (batches) keep the default layout.
+static int chosen_cw(const tbk_ctx* ctx, const HOp& op, int s, int per_task) {
+  const int cw = bulk_warps(op, s);
+  if (!cw || per_task) return cw;
+  const tbk_ctx::Tuned* t = find_tuned(ctx, op.n_rows, op.nnzb, s);
+  return t && t->cw >= 1 && t->cw <= cw && s % (128 * t->cw) == 0 ? t->cw : cw;
+}
+
 struct Occ {
   int simple = 0, bulk[5] = {0, 0, 0, 0, 0};
 };
@@ -525,7 +535,7 @@ int step_grid_ctas(tbk_ctx* ctx, const HOp& op, int s) {
   // then just takes more than one wave: every kernel loops over its tasks, none waits on another
   // CTA); the tensor-core step, when selected, runs on this same grid so that the per-CTA partial
   // sums line up
-  const int cw = bulk_warps(op, s);
+  const int cw = chosen_cw(ctx, op, s, 0);
   const int per_sm = cw && o.bulk[cw] > 0 ? o.bulk[cw] : o.simple;
   return std::max(1, per_sm * ctx->num_sms);
 }
@@ -564,7 +574,7 @@ void launch_step(tbk_ctx* ctx, const HOp& op, const StepArgs& a) {
     launch_step_tc(ctx, op, a, G);
     return;
   }
-  const int cw = bulk_warps(op, a.s);
+  const int cw = chosen_cw(ctx, op, a.s, a.per_task);
   if (cw && !a.cur_is_probe && a.err && !a.force_simple && occ_cache(ctx->device).bulk[cw] > 0) {
     if (cw == 4) launch_bulk<4>(ctx, op, a, G);
     else if (cw == 2) launch_bulk<2>(ctx, op, a, G);

@@ -441,3 +441,29 @@ def test_bounded_wait_reports_timeout_and_context_recovers(api, ctx):
     assert e.value.code == L.TBK_ERR_TIMEOUT
     m1 = api.chebyshev_moments(*args)
     assert torch.equal(m0, m1)
+
+
+def test_autotune_choice_keeps_the_results(api):
+    """tbk_autotune times the step's probe chunk and the adjoint's schedule and keeps its choice
+    for this operator shape in the context: moments, G and forces stay those of the default
+    choice up to FP32 summation order, and within the oracle's tolerances."""
+    ctx2 = api.Context()  # a context of its own, so that no other test sees the choice
+    wk = small_fcc(60, n_probes=512, kT=0.5)
+    rp, col, H = oracle_H(wk)
+    sv, pos, res = _gpu_run(api, ctx2, wk, 40, fp64=False)
+    args = (ctx2, res.H, sv.model, pos, None, res.emin, res.emax, wk.probe_seed, 512, 40, res.mu, wk.kT,
+            False, False)
+    m0 = api.chebyshev_moments(ctx2, res.H, res.emin, res.emax, wk.probe_seed, 512, 40, False)
+    G0, F0 = api.density_and_forces(*args)
+    chunk, windowed = api.autotune(ctx2, res.H, res.emin, res.emax, 512)
+    assert chunk in (128, 256, 512) and windowed in (False, True)
+    m1 = api.chebyshev_moments(ctx2, res.H, res.emin, res.emax, wk.probe_seed, 512, 40, False)
+    G1, F1 = api.density_and_forces(*args)
+    n = H.shape[0]
+    assert torch.allclose(m0, m1, rtol=0, atol=1e-9 * n)
+    assert torch.allclose(G0, G1, rtol=0, atol=2e-6 * G0.abs().max().item())
+    assert torch.allclose(F0, F1, rtol=0, atol=1e-5)
+    est = oracle_estimator(wk, H, res.emin, res.emax, 40)
+    _, F = oracle_estimator_forces(wk, rp, col, est, res.emin, res.emax, 40)
+    assert np.abs(F1.cpu().numpy() - F).max() < 1e-3
+    ctx2.close()

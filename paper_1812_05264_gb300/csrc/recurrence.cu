@@ -455,6 +455,197 @@ cheb_step_bulk(const int n_atoms, const int32_t* __restrict__ row_ptr, const int
   }
 }
 
+// ---- self-fed step for 128-probe tasks ---------------------------------------------------------
+//
+// The same step as cheb_step_bulk<1, D> with one warp per CTA and no producer warp: lane 0 keeps
+// R tiles in flight and, as soon as the warp has finished with a stage, refills it with the tile
+// R positions ahead in the CTA's tile sequence (its tasks' neighbour tiles, then the y_prev tile
+// of each task).  With 128 probes a task is quickly done, so a CTA that spends half its warps
+// and registers on a producer limits how many consumers an SM holds.
+template <int R>
+struct SelfCfg {
+  static constexpr int P = 128;
+  static constexpr int XB = 9 * P * 4;
+  static constexpr int HB = Layout<float, 9>::BS * 4;
+  static constexpr int SB = ((XB + HB + 127) / 128) * 128;
+  static constexpr int SMEM = R * SB + 8 * R;
+};
+
+template <int R>
+__global__ void __launch_bounds__(32)
+cheb_step_self(const int n_atoms, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+               const float* __restrict__ hv, const float* __restrict__ yin, const float* yprev,
+               float* yout, const float alpha, const float c_r, const uint64_t seed, const int s,
+               const int direct, double* __restrict__ partials, int* __restrict__ err,
+               const BatchRows batch, const int per_task, const int stall) {
+  using C = SelfCfg<R>;
+  extern __shared__ __align__(128) unsigned char smem[];
+  const uint32_t bar0 = smem_u32(smem + R * C::SB);
+  auto full = [&](int i) { return bar0 + 8u * i; };
+  const int lane = threadIdx.x;
+  const int n_chunks = s / C::P;
+  const int n_tasks = n_atoms * n_chunks;
+  const bool has_prev = yprev != nullptr;
+  if (lane == 0) {
+    for (int i = 0; i < R; ++i) mbar_init(full(i), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+  // producer cursor (lane 0): the next tile to issue, as (task, tile index within the task)
+  int p_task = blockIdx.x, p_q = 0, p_nt = 0, p_k0 = 0, issued = 0;
+  auto load_task = [&]() {
+    if (p_task < n_tasks) {
+      const int a = p_task / n_chunks;
+      p_k0 = __ldg(row_ptr + a);
+      p_nt = __ldg(row_ptr + a + 1) - p_k0 + (has_prev ? 1 : 0);
+    }
+  };
+  auto issue_next = [&]() {
+    if (stall || p_task >= n_tasks) return;
+    const int a = p_task / n_chunks, ch = p_task - a * n_chunks;
+    const bool is_prev = p_q == p_nt - (has_prev ? 1 : 0) && has_prev;
+    const int b = is_prev ? a : __ldg(col + p_k0 + p_q);
+    const int st = issued % R;
+    const uint32_t dst = smem_u32(smem + st * C::SB), bar = full(st);
+    const float* src = (is_prev ? yprev : yin) + (int64_t)9 * b * s + (int64_t)ch * C::P;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_expect_tx(bar, C::XB + (is_prev ? 0 : C::HB));
+    if (s == C::P) {
+      bulk_g2s(dst, src, C::XB, bar);  // the 9 rows are contiguous
+    } else {
+      for (int l = 0; l < 9; ++l) bulk_g2s(dst + l * C::P * 4, src + (int64_t)l * s, C::P * 4, bar);
+    }
+    if (!is_prev) bulk_g2s(dst + C::XB, hv + (int64_t)(p_k0 + p_q) * Layout<float, 9>::BS, C::HB, bar);
+    ++issued;
+    if (++p_q == p_nt) {
+      p_task += gridDim.x;
+      p_q = 0;
+      load_task();
+    }
+  };
+  if (lane == 0) {
+    load_task();
+    for (int j = 0; j < R; ++j) issue_next();
+  }
+  __syncwarp();
+
+  double sum0 = 0.0, sum1 = 0.0;
+  int it = 0;
+  bool ok = true;
+  const int pl = 4 * lane;
+  auto consumed = [&]() {
+    // the warp is done with stage it % R: refill it with the tile R positions ahead
+    __syncwarp();
+    if (lane == 0) issue_next();
+    ++it;
+  };
+  for (int task = blockIdx.x; task < n_tasks && ok; task += gridDim.x) {
+    const int a = task / n_chunks, ch = task - a * n_chunks;
+    const int k0 = __ldg(row_ptr + a), k1 = __ldg(row_ptr + a + 1);
+    float2 acc[9][2];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) acc[i][0] = acc[i][1] = make_float2(0.f, 0.f);
+    for (int q = 0; q < k1 - k0; ++q) {
+      const int st = it % R;
+      ok = mbar_wait(full(st), (it / R) & 1);
+      if (!ok) break;
+      const unsigned char* base = smem + st * C::SB;
+      spmm_tile_f2(reinterpret_cast<const float*>(base), reinterpret_cast<const float*>(base + C::XB), C::P,
+                   pl, acc);
+      consumed();
+    }
+    if (!ok) break;
+    float yp[9][4];
+    if (has_prev) {
+      const int st = it % R;
+      ok = mbar_wait(full(st), (it / R) & 1);
+      if (!ok) break;
+      const float* X = reinterpret_cast<const float*>(smem + st * C::SB);
+#pragma unroll
+      for (int l = 0; l < 9; ++l) {
+        const float4 t = *reinterpret_cast<const float4*>(X + l * C::P + pl);
+        yp[l][0] = t.x; yp[l][1] = t.y; yp[l][2] = t.z; yp[l][3] = t.w;
+      }
+      consumed();
+    }
+    const int p0 = ch * C::P + pl;
+    uint64_t sd = seed;
+    int64_t rloc = (int64_t)9 * a;
+    if (batch.atom_cl) {
+      const int cl = __ldg(batch.atom_cl + a);
+      sd = __ldg(batch.seed + cl);
+      rloc = (int64_t)9 * (a - __ldg(batch.atom0 + cl));
+    }
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      const int64_t row = (int64_t)9 * a + i;
+      float yo[4], r[4];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) yo[v] = alpha * ((v & 1) ? acc[i][v >> 1].y : acc[i][v >> 1].x);
+      if (c_r != 0.f || direct) {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) r[v] = tbk_probe_sign(sd, rloc + i, p0 + v);
+      }
+      if (c_r != 0.f) {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) yo[v] = fmaf(c_r, r[v], yo[v]);
+      }
+      if (has_prev) {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) yo[v] -= yp[i][v];
+      }
+      *reinterpret_cast<float4*>(yout + row * s + p0) = make_float4(yo[0], yo[1], yo[2], yo[3]);
+      if (partials) {
+        float xin[4];
+        if (direct) {
+#pragma unroll
+          for (int v = 0; v < 4; ++v) xin[v] = r[v];
+        } else {
+          const float4 t = __ldg(reinterpret_cast<const float4*>(yin + row * s + p0));
+          xin[0] = t.x; xin[1] = t.y; xin[2] = t.z; xin[3] = t.w;
+        }
+        float q0 = 0.f, q1 = 0.f;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          q0 = fmaf(yo[v], xin[v], q0);
+          q1 = fmaf(yo[v], yo[v], q1);
+        }
+        sum0 += (double)q0;
+        sum1 += (double)q1;
+      }
+    }
+    if (per_task && partials) {
+      for (int o = 16; o > 0; o >>= 1) {
+        sum0 += __shfl_xor_sync(0xffffffffu, sum0, o);
+        sum1 += __shfl_xor_sync(0xffffffffu, sum1, o);
+      }
+      if (lane == 0) {
+        partials[2 * (int64_t)a] = sum0;
+        partials[2 * (int64_t)a + 1] = sum1;
+      }
+      sum0 = sum1 = 0.0;
+    }
+  }
+  if (!ok) {
+    // let the copies in flight land before the CTA exits
+    if (lane == 0) {
+      atomicOr(err, 2);
+      for (int j = it; j < issued; ++j) mbar_wait(full(j % R), (j / R) & 1);
+    }
+    return;
+  }
+  if (partials && !per_task) {
+    for (int o = 16; o > 0; o >>= 1) {
+      sum0 += __shfl_xor_sync(0xffffffffu, sum0, o);
+      sum1 += __shfl_xor_sync(0xffffffffu, sum1, o);
+    }
+    if (lane == 0) {
+      partials[2 * blockIdx.x] = sum0;
+      partials[2 * blockIdx.x + 1] = sum1;
+    }
+  }
+}
+
 // ---- launch geometry ---------------------------------------------------------------------------
 
 template <typename T, int B, bool P>
@@ -462,6 +653,16 @@ static int occupancy_simple() {
   int n = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, cheb_step_kernel<T, B, P>, STEP_THREADS, 0);
   return n > 0 ? n : 1;
+}
+
+constexpr int SELF_R = 3;
+
+static int occupancy_self() {
+  using C = SelfCfg<SELF_R>;
+  cudaFuncSetAttribute(cheb_step_self<SELF_R>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+  int n = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, cheb_step_self<SELF_R>, 32, C::SMEM);
+  return n;
 }
 
 template <int CW, int D>
@@ -527,7 +728,7 @@ int step_grid_ctas(tbk_ctx* ctx, const HOp& op, int s) {
     m = std::min(m, std::min(occupancy_simple<double, 9, false>(), occupancy_simple<double, 9, true>()));
     m = std::min(m, std::min(occupancy_simple<double, 1, false>(), occupancy_simple<double, 1, true>()));
     o.simple = std::max(1, m);
-    o.bulk[1] = occupancy_bulk<1, BULK_D>();
+    o.bulk[1] = occupancy_self();  // 128-probe tasks run on the self-fed kernel
     o.bulk[2] = occupancy_bulk<2, BULK_D>();
     o.bulk[4] = occupancy_bulk<4, BULK_D>();
   }
@@ -566,6 +767,16 @@ static void launch_bulk(tbk_ctx* ctx, const HOp& op, const StepArgs& a, int G) {
   post_launch(ctx, "cheb_step_bulk");
 }
 
+static void launch_self(tbk_ctx* ctx, const HOp& op, const StepArgs& a, int G) {
+  using C = SelfCfg<SELF_R>;
+  cheb_step_self<SELF_R><<<G, 32, C::SMEM, ctx->stream>>>(
+      op.n_atoms, op.row_ptr, op.col, (const float*)op.hv, (const float*)a.yin, (const float*)a.yprev,
+      (float*)a.yout, (float)a.alpha, (float)a.c_r, a.seed, a.s, a.direct, a.partials, a.err,
+      a.batch, a.per_task, ctx->stall_next_step);
+  ctx->stall_next_step = 0;
+  post_launch(ctx, "cheb_step_self");
+}
+
 void launch_step(tbk_ctx* ctx, const HOp& op, const StepArgs& a) {
   KernelTimerScope timer(ctx, TBK_KERNEL_STEP);
   const int G = step_grid_ctas(ctx, op, a.s);
@@ -578,7 +789,7 @@ void launch_step(tbk_ctx* ctx, const HOp& op, const StepArgs& a) {
   if (cw && !a.cur_is_probe && a.err && !a.force_simple && occ_cache(ctx->device).bulk[cw] > 0) {
     if (cw == 4) launch_bulk<4>(ctx, op, a, G);
     else if (cw == 2) launch_bulk<2>(ctx, op, a, G);
-    else launch_bulk<1>(ctx, op, a, G);
+    else launch_self(ctx, op, a, G);
     return;
   }
   if (op.prec == TBK_MIXED) {

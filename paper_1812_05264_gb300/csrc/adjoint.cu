@@ -368,7 +368,8 @@ struct WindowPanels {
 
 template <int CW>
 struct WinCfg {
-  static constexpr int D = 8;  // tiles in flight: one 18 KB tile is consumed every ~0.2 us
+  // tiles in flight: 8 for the large tiles; 3 for 128 probes, so that six CTAs fit per SM
+  static constexpr int D = CW == 1 ? 3 : 8;
   static constexpr int P = 128 * CW;
   static constexpr int XB = 9 * P * 4;
   static constexpr int RED = 2 * CW * 96 * 4;
@@ -377,7 +378,7 @@ struct WinCfg {
 };
 
 template <int CW>
-__global__ void __launch_bounds__(32 * (CW + 1), CW == 4 ? 1 : 2)
+__global__ void __launch_bounds__(32 * (CW + 1), CW == 4 ? 1 : (CW == 2 ? 2 : 6))
 sddmm_window(const int n_atoms, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
              const WindowPanels wp, const int nw, const uint64_t seed, const int s, const double w,
              double* __restrict__ Gacc, int* __restrict__ err, const BatchRows batch,
@@ -490,9 +491,12 @@ sddmm_window(const int n_atoms, const int32_t* __restrict__ row_ptr, const int32
     ok = mbar_wait(y_full, y_it & 1);
     if (!ok) break;
     for (int q = k0; q < k1 && ok; ++q) {
-      float2 acc[81];
+      // 128 probes: scalar sums keep the kernel small enough for six CTAs per SM; wider tasks
+      // pair probes in f32x2 sums
+      using Acc = typename std::conditional<CW == 1, float, float2>::type;
+      Acc acc[81];
 #pragma unroll
-      for (int e = 0; e < 81; ++e) acc[e] = make_float2(0.f, 0.f);
+      for (int e = 0; e < 81; ++e) acc[e] = Acc{};
       for (int t = 0; t < nwa; ++t) {
         const int st = it % D;
         ok = mbar_wait(full(st), (it / D) & 1);
@@ -507,8 +511,15 @@ sddmm_window(const int n_atoms, const int32_t* __restrict__ row_ptr, const int32
           const float4 yv = *reinterpret_cast<const float4*>(Y + i * P + pl);
 #pragma unroll
           for (int l = 0; l < 9; ++l) {
-            acc[i * 9 + l] = __ffma2_rn(make_float2(yv.x, yv.y), make_float2(xv[l].x, xv[l].y), acc[i * 9 + l]);
-            acc[i * 9 + l] = __ffma2_rn(make_float2(yv.z, yv.w), make_float2(xv[l].z, xv[l].w), acc[i * 9 + l]);
+            if constexpr (CW == 1) {
+              float t = acc[i * 9 + l];
+              t = fmaf(yv.x, xv[l].x, t); t = fmaf(yv.y, xv[l].y, t);
+              t = fmaf(yv.z, xv[l].z, t); t = fmaf(yv.w, xv[l].w, t);
+              acc[i * 9 + l] = t;
+            } else {
+              acc[i * 9 + l] = __ffma2_rn(make_float2(yv.x, yv.y), make_float2(xv[l].x, xv[l].y), acc[i * 9 + l]);
+              acc[i * 9 + l] = __ffma2_rn(make_float2(yv.z, yv.w), make_float2(xv[l].z, xv[l].w), acc[i * 9 + l]);
+            }
           }
         }
         __syncwarp();
@@ -523,7 +534,10 @@ sddmm_window(const int n_atoms, const int32_t* __restrict__ row_ptr, const int32
       for (int blk = 0; blk < 3; ++blk) {
         float v[32];
 #pragma unroll
-        for (int e = 0; e < 32; ++e) v[e] = blk * 32 + e < 81 ? acc[blk * 32 + e].x + acc[blk * 32 + e].y : 0.f;
+        for (int e = 0; e < 32; ++e) {
+          if constexpr (CW == 1) v[e] = blk * 32 + e < 81 ? acc[blk * 32 + e] : 0.f;
+          else v[e] = blk * 32 + e < 81 ? acc[blk * 32 + e].x + acc[blk * 32 + e].y : 0.f;
+        }
         butterfly32(v, lane);
         if (blk == 0 && use > 0) ok = mbar_wait(red_empty(rb), (use - 1) & 1);
         R[warp * 96 + blk * 32 + lane] = v[0];

@@ -615,7 +615,8 @@ def run_batched(args, rank, world):
         wf += K * 2 * blocks * s
     kernels = {}
     for f, by, fl, kname in (("step", fb, ff, "cheb_step_bulk (batched)"),
-                             ("backward", bb, bf, "clenshaw_sddmm_bulk (batched)"),
+                             ("backward", bb, bf, "clenshaw_self (batched)" if windowed
+                              else "clenshaw_sddmm_bulk (batched)"),
                              ("window", wb, wf, "sddmm_window (batched)")):
         tms, nl = fam[f]
         if nl == 0:

@@ -18,7 +18,8 @@
  *    units of the positions (Angstrom).
  *  - Block-sparse matrices use BSR with square n_orb x n_orb blocks (n_orb = 1 or 9): row_ptr
  *    (int32, n_atoms + 1), col (int32, nnzb, ascending within a row, the diagonal block
- *    present), values FP64 row-major per block (nnzb * n_orb * n_orb).  Row i of a dense
+ *    present: a call that maps H to H^ fails with TBK_ERR_ARG on a row without it), values FP64
+ *    row-major per block (nnzb * n_orb * n_orb).  Row i of a dense
  *    vector block is orbital i = n_orb * atom + orbital-in-atom; probe panels are row-major
  *    (n_rows x s, probe index fastest).
  *  - The library allocates its own scratch (panels, partial sums, checkpoints) from the

@@ -568,6 +568,155 @@ sddmm_window(const int n_atoms, const int32_t* __restrict__ row_ptr, const int32
   if (!ok) atomicOr(err, 2);
 }
 
+// ---- self-fed adjoint step for 128 probes (windowed schedule) ---------------------------------
+//
+// clenshaw_sddmm_bulk<1, false> with one warp per CTA and no producer warp: lane 0 keeps R tiles
+// in flight (each row's neighbour tiles with their blocks, then its own-row source tiles) and
+// refills a stage as soon as the warp is done with it, so more consumer warps fit per SM.
+template <int R>
+struct ClenSelfCfg {
+  static constexpr int P = 128;
+  static constexpr int XB = 9 * P * 4;
+  static constexpr int HB = Layout<float, 9>::BS * 4;
+  static constexpr int SB = ((XB + HB + 127) / 128) * 128;
+  static constexpr int SMEM = R * SB + 8 * R;
+};
+
+template <int R>
+__global__ void __launch_bounds__(32)
+clenshaw_self(const int n_atoms, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+              const float* __restrict__ hv, const float* __restrict__ bin, const float* bprev, float* bout,
+              const float* __restrict__ ypan, const float4 cf, const uint64_t seed, const int s,
+              int* __restrict__ err, const BatchRows batch, const float4* __restrict__ cf_cl,
+              const float* __restrict__ ym1, const float* __restrict__ yp1) {
+  using C = ClenSelfCfg<R>;
+  extern __shared__ __align__(128) unsigned char smem[];
+  const uint32_t bar0 = smem_u32(smem + R * C::SB);
+  auto full = [&](int i) { return bar0 + 8u * i; };
+  const int lane = threadIdx.x;
+  enum { X_PREV = 0, X_Y = 1, X_YM1 = 2, X_YP1 = 3 };
+  const float* extra_src[4];
+  int extra_kind[4];
+  int n_extra = 0;
+  {
+    const bool any = cf_cl != nullptr;
+    if (bprev) { extra_src[n_extra] = bprev; extra_kind[n_extra++] = X_PREV; }
+    if (ypan && (any || cf.y != 0.f)) { extra_src[n_extra] = ypan; extra_kind[n_extra++] = X_Y; }
+    if (ym1 && (any || cf.z != 0.f)) { extra_src[n_extra] = ym1; extra_kind[n_extra++] = X_YM1; }
+    if (yp1 && (any || cf.w != 0.f)) { extra_src[n_extra] = yp1; extra_kind[n_extra++] = X_YP1; }
+  }
+  if (lane == 0) {
+    for (int i = 0; i < R; ++i) mbar_init(full(i), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+  int p_a = blockIdx.x, p_q = 0, p_k0 = 0, p_nb = 0, issued = 0;
+  auto load_row = [&]() {  // rows with no tile (no stored block, no source term) are skipped
+    for (; p_a < n_atoms; p_a += gridDim.x) {
+      p_k0 = __ldg(row_ptr + p_a);
+      p_nb = __ldg(row_ptr + p_a + 1) - p_k0;
+      if (p_nb + n_extra > 0) break;
+    }
+  };
+  auto issue_next = [&]() {
+    if (p_a >= n_atoms) return;
+    const bool own = p_q >= p_nb;
+    const int b = own ? p_a : __ldg(col + p_k0 + p_q);
+    const float* src = (own ? extra_src[p_q - p_nb] : bin) + (int64_t)9 * b * s;
+    const int st = issued % R;
+    const uint32_t dst = smem_u32(smem + st * C::SB), bar = full(st);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_expect_tx(bar, C::XB + (own ? 0 : C::HB));
+    bulk_g2s(dst, src, C::XB, bar);
+    if (!own) bulk_g2s(dst + C::XB, hv + (int64_t)(p_k0 + p_q) * Layout<float, 9>::BS, C::HB, bar);
+    ++issued;
+    if (++p_q == p_nb + n_extra) {
+      p_a += gridDim.x;
+      p_q = 0;
+      load_row();
+    }
+  };
+  if (lane == 0) {
+    load_row();
+    for (int j = 0; j < R; ++j) issue_next();
+  }
+  __syncwarp();
+  int it = 0;
+  bool ok = true;
+  const int pl = 4 * lane;
+  auto consumed = [&]() {
+    __syncwarp();
+    if (lane == 0) issue_next();
+    ++it;
+  };
+  for (int a = blockIdx.x; a < n_atoms && ok; a += gridDim.x) {
+    const int k0 = __ldg(row_ptr + a), k1 = __ldg(row_ptr + a + 1);
+    uint64_t sd = seed;
+    int64_t rloc = (int64_t)9 * a;
+    float4 cfa = cf;
+    if (batch.atom_cl) {
+      const int cl = __ldg(batch.atom_cl + a);
+      sd = __ldg(batch.seed + cl);
+      rloc = (int64_t)9 * (a - __ldg(batch.atom0 + cl));
+      if (cf_cl) cfa = cf_cl[cl];
+    }
+    float2 acc[9][2];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) acc[i][0] = acc[i][1] = make_float2(0.f, 0.f);
+    for (int q = 0; q < k1 - k0; ++q) {
+      const int st = it % R;
+      ok = mbar_wait(full(st), (it / R) & 1);
+      if (!ok) break;
+      const unsigned char* base = smem + st * C::SB;
+      spmm_tile_f2(reinterpret_cast<const float*>(base), reinterpret_cast<const float*>(base + C::XB), C::P,
+                   pl, acc);
+      consumed();
+    }
+    if (!ok) break;
+    float yo[9][4];
+#pragma unroll
+    for (int i = 0; i < 9; ++i)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) yo[i][v] = 2.f * ((v & 1) ? acc[i][v >> 1].y : acc[i][v >> 1].x);
+    if (cfa.x != 0.f) {
+#pragma unroll
+      for (int i = 0; i < 9; ++i)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) yo[i][v] = fmaf(cfa.x, tbk_probe_sign(sd, rloc + i, pl + v), yo[i][v]);
+    }
+    for (int e = 0; e < n_extra; ++e) {
+      const int st = it % R;
+      ok = mbar_wait(full(st), (it / R) & 1);
+      if (!ok) break;
+      const float* X = reinterpret_cast<const float*>(smem + st * C::SB);
+      const int kd = extra_kind[e];
+      const float ce = kd == X_PREV ? -1.f : (kd == X_Y ? cfa.y : (kd == X_YM1 ? cfa.z : cfa.w));
+      if (ce != 0.f) {  // a zero coefficient skips the tile (its rows may never have been formed)
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+          const float4 t = *reinterpret_cast<const float4*>(X + i * C::P + pl);
+          yo[i][0] = fmaf(ce, t.x, yo[i][0]); yo[i][1] = fmaf(ce, t.y, yo[i][1]);
+          yo[i][2] = fmaf(ce, t.z, yo[i][2]); yo[i][3] = fmaf(ce, t.w, yo[i][3]);
+        }
+      }
+      consumed();
+    }
+    if (!ok) break;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      const int64_t row = (int64_t)9 * a + i;
+      *reinterpret_cast<float4*>(bout + row * s + pl) = make_float4(yo[i][0], yo[i][1], yo[i][2], yo[i][3]);
+    }
+  }
+  if (!ok && lane == 0) {
+    // let the copies in flight land before the CTA exits
+    atomicOr(err, 2);
+    for (int j = it; j < issued; ++j) mbar_wait(full(j % R), (j / R) & 1);
+  }
+}
+
+constexpr int CLEN_SELF_R = 3;
+
 // tr[k] = index of block (b, a) for block k = (a, b) (the pattern is symmetric).
 __global__ void transpose_map(int n_atoms, const int32_t* __restrict__ row_ptr,
                               const int32_t* __restrict__ col, int32_t* __restrict__ tr, int* err) {
@@ -687,7 +836,23 @@ void launch_fused(tbk_ctx* ctx, const HOp& op, const void* bin, const void* bpre
   using F = std::false_type;
   if (s == 512) Gacc ? go(std::integral_constant<int, 4>(), T()) : go(std::integral_constant<int, 4>(), F());
   else if (s == 256) Gacc ? go(std::integral_constant<int, 2>(), T()) : go(std::integral_constant<int, 2>(), F());
-  else Gacc ? go(std::integral_constant<int, 1>(), T()) : go(std::integral_constant<int, 1>(), F());
+  else if (Gacc) go(std::integral_constant<int, 1>(), T());
+  else {
+    // the adjoint step alone at 128 probes: the self-fed single-warp kernel
+    using C = ClenSelfCfg<CLEN_SELF_R>;
+    static int occ_dev[64] = {0};
+    int& occ = occ_dev[ctx->device & 63];
+    if (!occ) {
+      TBK_CUDA(cudaFuncSetAttribute(clenshaw_self<CLEN_SELF_R>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
+      TBK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, clenshaw_self<CLEN_SELF_R>, 32, C::SMEM));
+      TBK_CHECK_ARG(occ > 0, "self-fed adjoint kernel does not fit on this device");
+    }
+    const int G = std::max(1, std::min(op.n_atoms, occ * ctx->num_sms));
+    clenshaw_self<CLEN_SELF_R><<<G, 32, C::SMEM, ctx->stream>>>(
+        op.n_atoms, op.row_ptr, op.col, (const float*)op.hv, (const float*)bin, (const float*)bprev,
+        (float*)bout, (const float*)ypan, cf, seed, s, err, batch, cf_cl, (const float*)ym1, (const float*)yp1);
+    post_launch(ctx, "clenshaw_self");
+  }
 }
 
 static void launch_sddmm(tbk_ctx* ctx, const HOp& op, const void* y, int y_is_probe, uint64_t seed,
@@ -1034,7 +1199,9 @@ extern "C" int tbk_density_and_forces(tbk_ctx* ctx, const tbk_bsr* H, const tbk_
     TBK_CHECK_ARG(M.kind == TBK_MODEL_SK, "forces need the Slater-Koster model");
     TBK_CHECK_ARG(pos != nullptr, "pos is NULL");
   }
-  HOp op = prepare_hop(ctx, H, emin, emax, prec, WS_HHAT);
+  int* err = (int*)scratch(ctx, WS_FLAGS, 64);
+  TBK_CUDA(cudaMemsetAsync(err, 0, sizeof(int), ctx->stream));
+  HOp op = prepare_hop(ctx, H, emin, emax, prec, WS_HHAT, err);
   const int p = order, s = n_probes, BB = op.B * op.B;
   const bool fused = fused_eligible(op, s, plain);
   const double W = emax - emin;
@@ -1047,8 +1214,6 @@ extern "C" int tbk_density_and_forces(tbk_ctx* ctx, const tbk_bsr* H, const tbk_
 
   // transpose map of the pattern
   int32_t* tr = (int32_t*)scratch(ctx, WS_TRANSPOSE, sizeof(int32_t) * (size_t)op.nnzb);
-  int* err = (int*)scratch(ctx, WS_FLAGS, 64);
-  TBK_CUDA(cudaMemsetAsync(err, 0, sizeof(int), ctx->stream));
   transpose_map<<<ceil_div(op.n_atoms, 16), dim3(8, 16), 0, ctx->stream>>>(op.n_atoms, op.row_ptr, op.col, tr, err);
   post_launch(ctx, "transpose_map");
 
@@ -1183,6 +1348,7 @@ extern "C" int tbk_density_and_forces(tbk_ctx* ctx, const tbk_bsr* H, const tbk_
   int herr = 0;
   TBK_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   sync(ctx);
+  check_diagonal_flag(herr);
   if (herr & 2) throw Error(TBK_ERR_TIMEOUT, "a bounded wait in the recurrence kernel expired");
   TBK_CHECK_ARG(herr == 0, "the block pattern is not symmetric");
   TBK_API_END
@@ -1237,14 +1403,14 @@ extern "C" int tbk_energies_and_forces(tbk_ctx* ctx, const tbk_bsr* H, const tbk
     TBK_CHECK_ARG(M.kind == TBK_MODEL_SK, "forces need the Slater-Koster model");
     TBK_CHECK_ARG(pos != nullptr, "pos is NULL");
   }
-  HOp op = prepare_hop(ctx, H, emin, emax, prec, WS_HHAT);
+  // err: bit 4 = a row has no diagonal block, bit 2 = a bounded wait expired, bit 1 = the pattern
+  // is not symmetric; err[1] bit 1 = a panel outgrew ||r|| (the spectrum is not inside [emin, emax])
+  int* err = (int*)scratch(ctx, WS_FLAGS, 64);
+  TBK_CUDA(cudaMemsetAsync(err, 0, 2 * sizeof(int), ctx->stream));
+  HOp op = prepare_hop(ctx, H, emin, emax, prec, WS_HHAT, err);
   const int p = order, s = n_probes, BB = op.B * op.B;
   const double W = emax - emin;
   int32_t* tr = (int32_t*)scratch(ctx, WS_TRANSPOSE, sizeof(int32_t) * (size_t)op.nnzb);
-  // err: bit 2 = a bounded wait expired, bit 1 = the pattern is not symmetric; err[1] bit 1 = a
-  // panel outgrew ||r|| (the spectrum is not inside [emin, emax])
-  int* err = (int*)scratch(ctx, WS_FLAGS, 64);
-  TBK_CUDA(cudaMemsetAsync(err, 0, 2 * sizeof(int), ctx->stream));
   launch_transpose_map(ctx, op.n_atoms, op.row_ptr, op.col, tr, err);
   double* Gacc = (double*)scratch(ctx, WS_GACC, sizeof(double) * (size_t)op.nnzb * BB * 2);
   double* Gsym = Gacc + (size_t)op.nnzb * BB;
@@ -1270,6 +1436,7 @@ extern "C" int tbk_energies_and_forces(tbk_ctx* ctx, const tbk_bsr* H, const tbk
     TBK_CUDA(cudaMemcpyAsync(h, res, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
     TBK_CUDA(cudaMemcpyAsync(herr, err, sizeof(herr), cudaMemcpyDeviceToHost, ctx->stream));
     sync(ctx);
+    check_diagonal_flag(herr[0]);
     if ((herr[0] | herr[1]) & 2) throw Error(TBK_ERR_TIMEOUT, "a bounded wait in the recurrence kernel expired");
     TBK_CHECK_ARG(herr[0] == 0, "the block pattern is not symmetric");
     if (herr[1])
@@ -1296,6 +1463,7 @@ extern "C" int tbk_energies_and_forces(tbk_ctx* ctx, const tbk_bsr* H, const tbk
   int herr = 0;
   TBK_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   sync(ctx);
+  check_diagonal_flag(herr);
   if (herr & 2) throw Error(TBK_ERR_TIMEOUT, "a bounded wait in the recurrence kernel expired");
   TBK_CHECK_ARG(herr == 0, "the block pattern is not symmetric");
   TBK_API_END

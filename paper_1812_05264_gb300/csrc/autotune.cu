@@ -54,15 +54,15 @@ extern "C" int tbk_autotune(tbk_ctx* ctx, const tbk_bsr* H, double emin, double 
   TBK_CHECK_ARG(n_probes >= 128 && n_probes % 128 == 0, "n_probes must be a multiple of 128");
   DeviceGuard dg(ctx);
   const int s = n_probes;
-  HOp op = prepare_hop(ctx, H, emin, emax, TBK_MIXED, WS_HHAT);
+  int* err = (int*)scratch(ctx, WS_FLAGS, 64);
+  TBK_CUDA(cudaMemsetAsync(err, 0, sizeof(int), ctx->stream));
+  HOp op = prepare_hop(ctx, H, emin, emax, TBK_MIXED, WS_HHAT, err);
   const int cw_max = bulk_consumer_warps(op, s);
   TBK_CHECK_ARG(cw_max > 0, "no TMA-fed step for this operator");
   const size_t panel = (size_t)op.n_rows * s * 4;
   void* A = scratch(ctx, WS_PANEL0, panel);
   void* B = scratch(ctx, WS_PANEL1, panel);
   void* Cp = scratch(ctx, WS_PANEL2, panel);
-  int* err = (int*)scratch(ctx, WS_FLAGS, 64);
-  TBK_CUDA(cudaMemsetAsync(err, 0, sizeof(int), ctx->stream));
   const uint64_t seed = 0x7E57;
   launch_scaled_probe(ctx, op, A, 1.0, seed, s);
   launch_scaled_probe(ctx, op, B, 0.5, seed + 1, s);
@@ -115,11 +115,12 @@ extern "C" int tbk_autotune(tbk_ctx* ctx, const tbk_bsr* H, double emin, double 
     }
     windowed = t_sched[1] < t_sched[0] ? 1 : 0;
   }
-  set_choice(ctx, op, s, best_cw, windowed);
   int herr = 0;
   TBK_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   sync(ctx);
+  check_diagonal_flag(herr);
   if (herr & 2) throw Error(TBK_ERR_TIMEOUT, "a bounded wait expired while tuning");
+  set_choice(ctx, op, s, best_cw, windowed);
   choice[0] = 128 * best_cw;
   choice[1] = windowed;
   TBK_API_END

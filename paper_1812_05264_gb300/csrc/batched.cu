@@ -28,9 +28,11 @@ __global__ void merge_cluster(int n, const int32_t* __restrict__ row_ptr, const 
                               const double* __restrict__ H, double shift, double inv, int a_off,
                               int b_off, int cl, int last, int32_t* __restrict__ m_row_ptr,
                               int32_t* __restrict__ m_col, float* __restrict__ m_hv,
-                              int32_t* __restrict__ atom_cl) {
+                              int32_t* __restrict__ atom_cl, int* __restrict__ err) {
+  // blockDim (8, 16): the 8 lanes of a row are 8 consecutive lanes of one warp
   const int a = blockIdx.x * blockDim.y + threadIdx.y;
   if (a >= n) return;
+  bool has_diag = false;
   if (threadIdx.x == 0) {
     m_row_ptr[a_off + a] = b_off + row_ptr[a];
     atom_cl[a_off + a] = cl;
@@ -40,6 +42,7 @@ __global__ void merge_cluster(int n, const int32_t* __restrict__ row_ptr, const 
     const int b = col[k];
     m_col[b_off + k] = a_off + b;
     const bool diag = b == a;
+    has_diag |= diag;
     float* out = m_hv + (int64_t)(b_off + k) * Layout<float, 9>::BS;
     for (int l = 0; l < 9; ++l)          // column l
       for (int i = 0; i < 12; ++i) {     // row i (padded to 12)
@@ -52,6 +55,7 @@ __global__ void merge_cluster(int n, const int32_t* __restrict__ row_ptr, const 
         out[l * 12 + i] = (float)v;
       }
   }
+  if (!__any_sync(0xFFu << (8 * (threadIdx.y & 3)), has_diag) && threadIdx.x == 0) atomicOr(err, ERR_NO_DIAGONAL);
 }
 
 // y0 = r for every merged row (cluster probe streams).
@@ -253,7 +257,7 @@ extern "C" int tbk_batched_moments(tbk_ctx* ctx, int32_t n_clusters, const tbk_b
       const double shift = 0.5 * (emax[c] + emin[c]), inv = 2.0 / (emax[c] - emin[c]);
       merge_cluster<<<ceil_div(n_at[ci], 16), dim3(8, 16), 0, ctx->stream>>>(
           n_at[ci], H[c].row_ptr, H[c].col, H[c].val, shift, inv, a_off[ci], (int)b_off[ci], ci,
-          ci == n_clusters - 1, m_row_ptr, m_col, m_hv, atom_cl);
+          ci == n_clusters - 1, m_row_ptr, m_col, m_hv, atom_cl, flag);
       post_launch(ctx, "merge_cluster");
     }
     char* A = panels;
@@ -354,6 +358,7 @@ extern "C" int tbk_batched_moments(tbk_ctx* ctx, int32_t n_clusters, const tbk_b
   int hflag = 0;
   TBK_CUDA(cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   sync(ctx);
+  check_diagonal_flag(hflag);
   if (hflag & 2) throw Error(TBK_ERR_TIMEOUT, "a bounded wait in the recurrence kernel expired");
   if (hflag) throw Error(TBK_ERR_SPECTRUM, "a Chebyshev panel of some cluster grew beyond ||r||");
   TBK_API_END
@@ -512,12 +517,16 @@ static void batched_adjoint(tbk_ctx* ctx, int ncl, const tbk_bsr* H, const tbk_m
   int32_t* m_col = (int32_t*)scratch(ctx, WS_CELLS2, sizeof(int32_t) * (size_t)bo + 64);
   float* m_hv = (float*)scratch(ctx, WS_HHAT, sizeof(float) * (size_t)bo * Layout<float, 9>::BS);
   double* m_pos = (double*)scratch(ctx, WS_CELLS3, sizeof(double) * 3 * (size_t)ao + 64);
+  // err: bit 4 = a row has no diagonal block, bit 2 = a bounded wait expired, bit 1 = a pattern is
+  // not symmetric; err[1] bit 1 = a panel outgrew ||r|| (the spectrum is not inside [emin, emax])
+  int* err = (int*)scratch(ctx, WS_FLAGS, 64);
+  TBK_CUDA(cudaMemsetAsync(err, 0, 2 * sizeof(int), ctx->stream));
   for (int ci = 0; ci < ncl; ++ci) {
     const int c = idx[ci];
     const double shift = 0.5 * (emax[c] + emin[c]), inv = 2.0 / (emax[c] - emin[c]);
     merge_cluster<<<ceil_div(n_at[ci], 16), dim3(8, 16), 0, ctx->stream>>>(
         n_at[ci], H[c].row_ptr, H[c].col, H[c].val, shift, inv, a_off[ci], (int)b_off[ci], ci,
-        ci == ncl - 1, m_row_ptr, m_col, m_hv, atom_cl);
+        ci == ncl - 1, m_row_ptr, m_col, m_hv, atom_cl, err);
     post_launch(ctx, "merge_cluster");
     if (forces)
       TBK_CUDA(cudaMemcpyAsync(m_pos + 3 * (size_t)a_off[ci], pos[c], sizeof(double) * 3 * n_at[ci],
@@ -530,10 +539,6 @@ static void batched_adjoint(tbk_ctx* ctx, int ncl, const tbk_bsr* H, const tbk_m
   br.atom_cl = atom_cl;
   br.seed = d_seed;
   br.atom0 = d_atom0;
-  // err: bit 2 = a bounded wait expired, bit 1 = a pattern is not symmetric; err[1] bit 1 = a
-  // panel outgrew ||r|| (the spectrum is not inside [emin, emax])
-  int* err = (int*)scratch(ctx, WS_FLAGS, 64);
-  TBK_CUDA(cudaMemsetAsync(err, 0, 2 * sizeof(int), ctx->stream));
   // (not WS_NODES: coefficients() keeps its cosine table there)
   float4* d_cft = (float4*)scratch(ctx, WS_LANCZOS, sizeof(float4) * (size_t)(Kmax + 1) * ncl + 64);
   // ---- the source coefficients of every step from c_k = d_k beta_k[g](mu) of every cluster ----
@@ -626,6 +631,7 @@ static void batched_adjoint(tbk_ctx* ctx, int ncl, const tbk_bsr* H, const tbk_m
       TBK_CUDA(cudaMemcpyAsync(h.data(), res, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, ctx->stream));
       TBK_CUDA(cudaMemcpyAsync(herr, err, sizeof(herr), cudaMemcpyDeviceToHost, ctx->stream));
       sync(ctx);
+      check_diagonal_flag(herr[0]);
       if ((herr[0] | herr[1]) & 2) throw Error(TBK_ERR_TIMEOUT, "a bounded wait in a recurrence kernel expired");
       TBK_CHECK_ARG(herr[0] == 0, "a block pattern is not symmetric");
       if (herr[1])
@@ -666,6 +672,7 @@ static void batched_adjoint(tbk_ctx* ctx, int ncl, const tbk_bsr* H, const tbk_m
   int herr = 0;
   TBK_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   sync(ctx);
+  check_diagonal_flag(herr);
   if (herr & 2) throw Error(TBK_ERR_TIMEOUT, "a bounded wait in a recurrence kernel expired");
   TBK_CHECK_ARG(herr == 0, "a block pattern is not symmetric");
 }

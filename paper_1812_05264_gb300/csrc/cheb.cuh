@@ -28,8 +28,18 @@ struct HOp {
   const void* hv = nullptr;          // mapped blocks, Layout<T,B>
 };
 
-// Validate a tbk_bsr and build H^ in scratch slot `slot` with precision `prec`.
-HOp prepare_hop(tbk_ctx* ctx, const tbk_bsr* H, double emin, double emax, int prec, Slot slot);
+// Error-word bit set by the kernels that map H when a row stores no diagonal block (a, a): the
+// shift of H^ = (2H - (emax + emin) I) / W lives on the diagonal blocks, so such a pattern is
+// rejected rather than mapped wrongly.
+constexpr int ERR_NO_DIAGONAL = 4;
+inline void check_diagonal_flag(int herr) {
+  if (herr & ERR_NO_DIAGONAL)
+    throw Error(TBK_ERR_ARG, "a row of H stores no diagonal block; every row must hold its block (a, a)");
+}
+
+// Validate a tbk_bsr and build H^ in scratch slot `slot` with precision `prec`; a row without
+// its diagonal block sets ERR_NO_DIAGONAL in *err (device).
+HOp prepare_hop(tbk_ctx* ctx, const tbk_bsr* H, double emin, double emax, int prec, Slot slot, int* err);
 
 // One fused step over all rows and probes:
 //   y_out = alpha * (H^ y_in) + c_r * r - y_prev
@@ -76,7 +86,7 @@ void launch_scaled_probe(tbk_ctx* ctx, const HOp& op, void* panel, double c, uin
 // Allocation-free building blocks: bytes of the mapped operator, building it into caller
 // memory, and the per-step partial-sum reduction into moments (flag bit 1 = spectrum error).
 size_t mapped_h_bytes(const tbk_bsr* H, int prec);
-HOp prepare_hop_into(tbk_ctx* ctx, const tbk_bsr* H, double emin, double emax, int prec, void* dst);
+HOp prepare_hop_into(tbk_ctx* ctx, const tbk_bsr* H, double emin, double emax, int prec, void* dst, int* err);
 void launch_moment_reduction(tbk_ctx* ctx, const double* partials, int nctas, int K, int order, int s,
                              int64_t n_rows, int direct, double* sums, double* moments, int* flag);
 

@@ -93,7 +93,7 @@ extern "C" int tbk_chebyshev_moments_noalloc(tbk_ctx* ctx, const tbk_bsr* H, dou
   void* Bp = K >= 2 ? (void*)(base + o_pb) : nullptr;
   // the array keeps the previous call's contents: the error flag must start at zero
   TBK_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), ctx->stream));
-  HOp op = prepare_hop_into(ctx, H, emin, emax, prec, base + o_hhat);
+  HOp op = prepare_hop_into(ctx, H, emin, emax, prec, base + o_hhat, flag);
   void *cur = nullptr, *prev = nullptr;
   for (int j = 1; j <= K; ++j) {
     StepArgs a;
@@ -128,6 +128,7 @@ extern "C" int tbk_chebyshev_moments_noalloc(tbk_ctx* ctx, const tbk_bsr* H, dou
   int hflag = 0;
   TBK_CUDA(cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   sync(ctx);
+  check_diagonal_flag(hflag);
   if (hflag & 2) throw Error(TBK_ERR_TIMEOUT, "a bounded wait in the recurrence kernel expired");
   if (hflag)
     throw Error(TBK_ERR_SPECTRUM, "a Chebyshev panel grew beyond ||r||: the spectrum of H is not "

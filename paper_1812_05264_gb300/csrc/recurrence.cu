@@ -46,12 +46,15 @@ __device__ __forceinline__ void st16(T* p, const T* x) {
 template <typename T, int B>
 __global__ void map_h_kernel(int n_atoms, const int32_t* __restrict__ row_ptr,
                              const int32_t* __restrict__ col, const double* __restrict__ H,
-                             double shift, double inv_half_w, T* __restrict__ out) {
+                             double shift, double inv_half_w, T* __restrict__ out, int* __restrict__ err) {
   constexpr int RS = Layout<T, B>::RS, BS = Layout<T, B>::BS;
+  // blockDim (8, 16): the 8 lanes of a row are 8 consecutive lanes of one warp
   const int a = blockIdx.x * blockDim.y + threadIdx.y;
   if (a >= n_atoms) return;
+  bool has_diag = false;
   for (int k = row_ptr[a] + threadIdx.x; k < row_ptr[a + 1]; k += blockDim.x) {
     const bool diag = col[k] == a;
+    has_diag |= diag;
     for (int i = 0; i < B; ++i)
       for (int j = 0; j < RS; ++j) {
         // stored element (major index i, minor index j): H^[i][j] row-major, H^[j][i] column-major
@@ -65,9 +68,10 @@ __global__ void map_h_kernel(int n_atoms, const int32_t* __restrict__ row_ptr,
         out[(int64_t)k * BS + i * RS + j] = (T)v;
       }
   }
+  if (!__any_sync(0xFFu << (8 * (threadIdx.y & 3)), has_diag) && threadIdx.x == 0) atomicOr(err, ERR_NO_DIAGONAL);
 }
 
-HOp prepare_hop(tbk_ctx* ctx, const tbk_bsr* H, double emin, double emax, int prec, Slot slot) {
+HOp prepare_hop(tbk_ctx* ctx, const tbk_bsr* H, double emin, double emax, int prec, Slot slot, int* err) {
   TBK_CHECK_ARG(H != nullptr, "H is NULL");
   TBK_CHECK_ARG(H->n_orb == 1 || H->n_orb == 9, "n_orb must be 1 or 9");
   TBK_CHECK_ARG(H->n_atoms >= 1 && H->nnzb >= H->n_atoms, "empty or inconsistent matrix");
@@ -90,7 +94,7 @@ HOp prepare_hop(tbk_ctx* ctx, const tbk_bsr* H, double emin, double emax, int pr
   {                                                                                            \
     TT* out = (TT*)scratch(ctx, slot, sizeof(TT) * (size_t)op.nnzb * Layout<TT, BB>::BS);      \
     map_h_kernel<TT, BB><<<grid, blk, 0, ctx->stream>>>(op.n_atoms, op.row_ptr, op.col, H->val, \
-                                                        shift, inv, out);                      \
+                                                        shift, inv, out, err);                 \
     post_launch(ctx, "map_h_kernel");                                                          \
     op.hv = out;                                                                               \
   }
@@ -493,11 +497,12 @@ cheb_step_self(const int n_atoms, const int32_t* __restrict__ row_ptr, const int
   __syncwarp();
   // producer cursor (lane 0): the next tile to issue, as (task, tile index within the task)
   int p_task = blockIdx.x, p_q = 0, p_nt = 0, p_k0 = 0, issued = 0;
-  auto load_task = [&]() {
-    if (p_task < n_tasks) {
+  auto load_task = [&]() {  // tasks with no tile (an empty row, no y_{k-1}) are skipped
+    for (; p_task < n_tasks; p_task += gridDim.x) {
       const int a = p_task / n_chunks;
       p_k0 = __ldg(row_ptr + a);
       p_nt = __ldg(row_ptr + a + 1) - p_k0 + (has_prev ? 1 : 0);
+      if (p_nt > 0) break;
     }
   };
   auto issue_next = [&]() {
@@ -885,7 +890,7 @@ size_t mapped_h_bytes(const tbk_bsr* H, int prec) {
   return (size_t)H->nnzb * bs * (prec == TBK_MIXED ? 4 : 8);
 }
 
-HOp prepare_hop_into(tbk_ctx* ctx, const tbk_bsr* H, double emin, double emax, int prec, void* dst) {
+HOp prepare_hop_into(tbk_ctx* ctx, const tbk_bsr* H, double emin, double emax, int prec, void* dst, int* err) {
   TBK_CHECK_ARG(H != nullptr, "H is NULL");
   TBK_CHECK_ARG(H->n_orb == 1 || H->n_orb == 9, "n_orb must be 1 or 9");
   TBK_CHECK_ARG(H->n_atoms >= 1 && H->nnzb >= H->n_atoms, "empty or inconsistent matrix");
@@ -907,14 +912,14 @@ HOp prepare_hop_into(tbk_ctx* ctx, const tbk_bsr* H, double emin, double emax, i
   const int grid = ceil_div(op.n_atoms, 16);
   if (prec == TBK_MIXED) {
     if (op.B == 9)
-      map_h_kernel<float, 9><<<grid, blk, 0, ctx->stream>>>(op.n_atoms, op.row_ptr, op.col, H->val, shift, inv, (float*)dst);
+      map_h_kernel<float, 9><<<grid, blk, 0, ctx->stream>>>(op.n_atoms, op.row_ptr, op.col, H->val, shift, inv, (float*)dst, err);
     else
-      map_h_kernel<float, 1><<<grid, blk, 0, ctx->stream>>>(op.n_atoms, op.row_ptr, op.col, H->val, shift, inv, (float*)dst);
+      map_h_kernel<float, 1><<<grid, blk, 0, ctx->stream>>>(op.n_atoms, op.row_ptr, op.col, H->val, shift, inv, (float*)dst, err);
   } else {
     if (op.B == 9)
-      map_h_kernel<double, 9><<<grid, blk, 0, ctx->stream>>>(op.n_atoms, op.row_ptr, op.col, H->val, shift, inv, (double*)dst);
+      map_h_kernel<double, 9><<<grid, blk, 0, ctx->stream>>>(op.n_atoms, op.row_ptr, op.col, H->val, shift, inv, (double*)dst, err);
     else
-      map_h_kernel<double, 1><<<grid, blk, 0, ctx->stream>>>(op.n_atoms, op.row_ptr, op.col, H->val, shift, inv, (double*)dst);
+      map_h_kernel<double, 1><<<grid, blk, 0, ctx->stream>>>(op.n_atoms, op.row_ptr, op.col, H->val, shift, inv, (double*)dst, err);
   }
   post_launch(ctx, "map_h_kernel");
   return op;
@@ -947,7 +952,9 @@ extern "C" int tbk_chebyshev_moments(tbk_ctx* ctx, const tbk_bsr* H, double emin
   DeviceGuard dg(ctx);
   const int prec = (flags & TBK_FP64) ? TBK_FP64 : TBK_MIXED;
   const int direct = (flags & TBK_MOMENTS_DIRECT) ? 1 : 0;
-  HOp op = prepare_hop(ctx, H, emin, emax, prec, WS_HHAT);
+  int* flag = (int*)scratch(ctx, WS_FLAGS, 64);
+  TBK_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), ctx->stream));
+  HOp op = prepare_hop(ctx, H, emin, emax, prec, WS_HHAT, flag);
   const int s = n_probes;
   const size_t esz = prec == TBK_MIXED ? 4 : 8;
   const size_t panel = (size_t)op.n_rows * s * esz;
@@ -955,8 +962,6 @@ extern "C" int tbk_chebyshev_moments(tbk_ctx* ctx, const tbk_bsr* H, double emin
   const int nctas = step_grid_ctas(ctx, op, s);
   double* partials = (double*)scratch(ctx, WS_PARTIALS, sizeof(double) * 2 * (size_t)std::max(1, K) * nctas);
   double* sums = (double*)scratch(ctx, WS_MISC, sizeof(double) * 2 * (size_t)std::max(1, K) + 64);
-  int* flag = (int*)scratch(ctx, WS_FLAGS, 64);
-  TBK_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), ctx->stream));
   void* A = K >= 1 ? scratch(ctx, WS_PANEL0, panel) : nullptr;
   void* Bp = K >= 2 ? scratch(ctx, WS_PANEL1, panel) : nullptr;
   void *cur = nullptr, *prev = nullptr;
@@ -999,6 +1004,7 @@ extern "C" int tbk_chebyshev_moments(tbk_ctx* ctx, const tbk_bsr* H, double emin
   int hflag = 0;
   TBK_CUDA(cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   sync(ctx);
+  check_diagonal_flag(hflag);
   if (hflag & 2) throw Error(TBK_ERR_TIMEOUT, "a bounded wait in the recurrence kernel expired");
   if (hflag)
     throw Error(TBK_ERR_SPECTRUM, "a Chebyshev panel grew beyond ||r||: the spectrum of H is not "

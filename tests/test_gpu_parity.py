@@ -426,6 +426,43 @@ def test_windowed_outer_products_match_fused(api, ctx, s, p):
     assert np.abs(F2.cpu().numpy() - F).max() < 1e-3
 
 
+def test_row_without_its_diagonal_block_is_rejected(api, ctx):
+    """H^ = (2H - (emax + emin) I) / W keeps its shift on the diagonal blocks, so a pattern in which
+    an atom's row stores no block at all is refused with TBK_ERR_ARG by every call that maps H
+    (the self-fed 128-probe kernels among those that run on it first skip the empty row and stay
+    in bounds), and the context then computes as before."""
+    from paper_1812_05264_gb300 import _lib as L
+    wk = small_fcc(30, n_probes=128, kT=0.5)
+    sv, pos, res = _gpu_run(api, ctx, wk, 20, fp64=False)
+    p = 41
+    m0 = api.chebyshev_moments(ctx, res.H, res.emin, res.emax, wk.probe_seed, 128, p)
+    j, g = 7, res.H.graph
+    rpc, colc, val = g.row_ptr.cpu().long(), g.col.cpu().long(), res.H.val.cpu()
+    rows = torch.repeat_interleave(torch.arange(g.n_atoms), rpc[1:] - rpc[:-1])
+    keep = (rows != j) & (colc != j)
+    counts = torch.bincount(rows[keep], minlength=g.n_atoms)
+    assert counts[j] == 0
+    rp2 = torch.cat([torch.zeros(1, dtype=torch.long), counts.cumsum(0)]).int()
+    H2 = api.BSR(api.Graph(g.n_atoms, int(keep.sum()), rp2.cuda(), colc[keep].int().cuda()), 9,
+                 val[keep].contiguous().cuda())
+    e0, e1 = res.emin, res.emax
+    calls = [
+        lambda: api.chebyshev_moments(ctx, H2, e0, e1, wk.probe_seed, 128, p),
+        lambda: api.chebyshev_moments(ctx, H2, e0, e1, wk.probe_seed, 128, p, plain=True),
+        lambda: api.density_and_forces(ctx, H2, None, None, None, e0, e1, wk.probe_seed, 128, p,
+                                       res.mu, wk.kT, want_forces=False, windowed=True),
+        lambda: api.density_and_forces(ctx, H2, None, None, None, e0, e1, wk.probe_seed, 128, p,
+                                       res.mu, wk.kT, want_forces=False, windowed=False),
+        lambda: api.batched_moments(ctx, [res.H, H2], [e0, e0], [e1, e1], [1, 2], 128, [p, p]),
+    ]
+    for call in calls:
+        with pytest.raises(L.TbkError) as e:
+            call()
+        assert e.value.code == L.TBK_ERR_ARG and "diagonal" in str(e.value)
+    m1 = api.chebyshev_moments(ctx, res.H, res.emin, res.emax, wk.probe_seed, 128, p)
+    assert torch.equal(m0, m1)
+
+
 def test_bounded_wait_reports_timeout_and_context_recovers(api, ctx):
     """A recurrence step whose producer copies nothing: the consumers' waits give up after their
     wall-time limit, the call returns TBK_ERR_TIMEOUT, nothing faults, and the same context then

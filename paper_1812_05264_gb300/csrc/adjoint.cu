@@ -246,6 +246,7 @@ clenshaw_sddmm_bulk(const int n_atoms, const int32_t* __restrict__ row_ptr,
 
   int it = 0, y_it = 0;
   bool ok = true;
+  uint32_t rdy = 0;  // stage it % R was found ready by the early test
   const int pl = 4 * threadIdx.x;
   for (int a = blockIdx.x; a < n_atoms && ok; a += gridDim.x) {
     const int k0 = __ldg(row_ptr + a), k1 = __ldg(row_ptr + a + 1);
@@ -268,8 +269,11 @@ clenshaw_sddmm_bulk(const int n_atoms, const int32_t* __restrict__ row_ptr,
     for (int i = 0; i < 9; ++i) acc[i][0] = acc[i][1] = make_float2(0.f, 0.f);
     for (int q = 0; q < k1 - k0; ++q) {
       const int st = it % R;
-      ok = mbar_wait(full(st), (it / R) & 1);
-      if (!ok) break;
+      if (!rdy) {
+        ok = mbar_wait(full(st), (it / R) & 1);
+        if (!ok) break;
+      }
+      rdy = mbar_test(full((it + 1) % R), ((it + 1) / R) & 1);
       const unsigned char* base = smem + st * C::SB;
       const float* X = reinterpret_cast<const float*>(base);
       if (has_out) spmm_tile_f2(X, reinterpret_cast<const float*>(base + C::XB), C::P, pl, acc);
@@ -315,8 +319,11 @@ clenshaw_sddmm_bulk(const int n_atoms, const int32_t* __restrict__ row_ptr,
     }
     for (int e = 0; e < n_extra; ++e) {
       const int st = it % R;
-      ok = mbar_wait(full(st), (it / R) & 1);
-      if (!ok) break;
+      if (!rdy) {
+        ok = mbar_wait(full(st), (it / R) & 1);
+        if (!ok) break;
+      }
+      rdy = mbar_test(full((it + 1) % R), ((it + 1) / R) & 1);
       const float* X = reinterpret_cast<const float*>(smem + st * C::SB);
       const int kd = extra_kind[e];
       const float ce = kd == X_PREV ? -1.f : (kd == X_Y ? cfa.y : (kd == X_YM1 ? cfa.z : cfa.w));
@@ -643,6 +650,7 @@ clenshaw_self(const int n_atoms, const int32_t* __restrict__ row_ptr, const int3
   __syncwarp();
   int it = 0;
   bool ok = true;
+  uint32_t rdy = 0;  // stage it % R was found ready by the early test
   const int pl = 4 * lane;
   auto consumed = [&]() {
     __syncwarp();
@@ -665,8 +673,11 @@ clenshaw_self(const int n_atoms, const int32_t* __restrict__ row_ptr, const int3
     for (int i = 0; i < 9; ++i) acc[i][0] = acc[i][1] = make_float2(0.f, 0.f);
     for (int q = 0; q < k1 - k0; ++q) {
       const int st = it % R;
-      ok = mbar_wait(full(st), (it / R) & 1);
-      if (!ok) break;
+      if (!rdy) {
+        ok = mbar_wait(full(st), (it / R) & 1);
+        if (!ok) break;
+      }
+      rdy = mbar_test(full((it + 1) % R), ((it + 1) / R) & 1);
       const unsigned char* base = smem + st * C::SB;
       spmm_tile_f2(reinterpret_cast<const float*>(base), reinterpret_cast<const float*>(base + C::XB), C::P,
                    pl, acc);
@@ -686,8 +697,11 @@ clenshaw_self(const int n_atoms, const int32_t* __restrict__ row_ptr, const int3
     }
     for (int e = 0; e < n_extra; ++e) {
       const int st = it % R;
-      ok = mbar_wait(full(st), (it / R) & 1);
-      if (!ok) break;
+      if (!rdy) {
+        ok = mbar_wait(full(st), (it / R) & 1);
+        if (!ok) break;
+      }
+      rdy = mbar_test(full((it + 1) % R), ((it + 1) / R) & 1);
       const float* X = reinterpret_cast<const float*>(smem + st * C::SB);
       const int kd = extra_kind[e];
       const float ce = kd == X_PREV ? -1.f : (kd == X_Y ? cfa.y : (kd == X_YM1 ? cfa.z : cfa.w));

@@ -338,6 +338,7 @@ cheb_step_bulk(const int n_atoms, const int32_t* __restrict__ row_ptr, const int
   double sum0 = 0.0, sum1 = 0.0;
   int it = 0;
   bool ok = true;
+  uint32_t rdy = 0;  // stage it % R was found ready by the early test
   for (int task = blockIdx.x; task < n_tasks && ok; task += gridDim.x) {
     const int a = task / n_chunks, ch = task - a * n_chunks;
     const int k0 = __ldg(row_ptr + a), k1 = __ldg(row_ptr + a + 1);
@@ -347,8 +348,11 @@ cheb_step_bulk(const int n_atoms, const int32_t* __restrict__ row_ptr, const int
     for (int i = 0; i < 9; ++i) acc[i][0] = acc[i][1] = make_float2(0.f, 0.f);
     for (int q = 0; q < k1 - k0; ++q) {
       const int st = it % R;
-      ok = mbar_wait(full(st), (it / R) & 1);
-      if (!ok) break;
+      if (!rdy) {
+        ok = mbar_wait(full(st), (it / R) & 1);
+        if (!ok) break;
+      }
+      rdy = mbar_test(full((it + 1) % R), ((it + 1) / R) & 1);
       const unsigned char* base = smem + st * C::SB;
       const float* X = reinterpret_cast<const float*>(base);
       const float* Hs = reinterpret_cast<const float*>(base + C::XB);
@@ -362,8 +366,11 @@ cheb_step_bulk(const int n_atoms, const int32_t* __restrict__ row_ptr, const int
     float yp[9][4];
     if (has_prev) {
       const int st = it % R;
-      ok = mbar_wait(full(st), (it / R) & 1);
-      if (!ok) break;
+      if (!rdy) {
+        ok = mbar_wait(full(st), (it / R) & 1);
+        if (!ok) break;
+      }
+      rdy = mbar_test(full((it + 1) % R), ((it + 1) / R) & 1);
       const float* X = reinterpret_cast<const float*>(smem + st * C::SB);
 #pragma unroll
       for (int l = 0; l < 9; ++l) {
@@ -537,6 +544,7 @@ cheb_step_self(const int n_atoms, const int32_t* __restrict__ row_ptr, const int
   double sum0 = 0.0, sum1 = 0.0;
   int it = 0;
   bool ok = true;
+  uint32_t rdy = 0;  // stage it % R was found ready by the early test
   const int pl = 4 * lane;
   auto consumed = [&]() {
     // the warp is done with stage it % R: refill it with the tile R positions ahead
@@ -552,8 +560,11 @@ cheb_step_self(const int n_atoms, const int32_t* __restrict__ row_ptr, const int
     for (int i = 0; i < 9; ++i) acc[i][0] = acc[i][1] = make_float2(0.f, 0.f);
     for (int q = 0; q < k1 - k0; ++q) {
       const int st = it % R;
-      ok = mbar_wait(full(st), (it / R) & 1);
-      if (!ok) break;
+      if (!rdy) {
+        ok = mbar_wait(full(st), (it / R) & 1);
+        if (!ok) break;
+      }
+      rdy = mbar_test(full((it + 1) % R), ((it + 1) / R) & 1);
       const unsigned char* base = smem + st * C::SB;
       spmm_tile_f2(reinterpret_cast<const float*>(base), reinterpret_cast<const float*>(base + C::XB), C::P,
                    pl, acc);
@@ -563,8 +574,11 @@ cheb_step_self(const int n_atoms, const int32_t* __restrict__ row_ptr, const int
     float yp[9][4];
     if (has_prev) {
       const int st = it % R;
-      ok = mbar_wait(full(st), (it / R) & 1);
-      if (!ok) break;
+      if (!rdy) {
+        ok = mbar_wait(full(st), (it / R) & 1);
+        if (!ok) break;
+      }
+      rdy = mbar_test(full((it + 1) % R), ((it + 1) / R) & 1);
       const float* X = reinterpret_cast<const float*>(smem + st * C::SB);
 #pragma unroll
       for (int l = 0; l < 9; ++l) {

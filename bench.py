@@ -354,8 +354,9 @@ def run_ours(args, rank, world):
         # G += sum_j y_j ybar_{j+1}^T (j = 0 .. K-1, K pairs a step): reads both panels of every
         # pair, reads and writes the FP64 accumulator once per window
         "window": (lambda n: args.steps * (K * 2 * panel + nwin * nnzb * B2 * 16),
-                   lambda n: args.steps * K * blk, "sddmm_window", "sddmm_window_fcc10000.md",
-                   "adjoint.cu"),
+                   lambda n: args.steps * K * blk,
+                   "sddmm_window_g" if wk.n_probes >= 256 else "sddmm_window",
+                   "sddmm_window_fcc10000.md", "adjoint.cu"),
     }
     kernels = {}
     for f, (tms, nl) in fam.items():
@@ -500,12 +501,13 @@ def adjoint_only(args, ctx, solver, wk, pos):
     mu = api.fermi_level(ctx, mom, emin, emax, wk.n_electrons, wk.kT)[0]
     args_ = (ctx, H, solver.model, pos, solver.box, emin, emax, wk.probe_seed, wk.n_probes, p, mu,
              wk.kT, wk.jackson, not wk.mixed)
+    sched = {"auto": None, "fused": False, "windowed": True}[args.adjoint]
     for _ in range(args.warmup):
-        api.density_and_forces(*args_)
+        api.density_and_forces(*args_, windowed=sched)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(ctx.stream)
     for _ in range(args.steps):
-        api.density_and_forces(*args_)
+        api.density_and_forces(*args_, windowed=sched)
     e1.record(ctx.stream)
     torch.cuda.synchronize()
     print(json.dumps({"only": "adjoint", "workload": wk.name, "order": p,

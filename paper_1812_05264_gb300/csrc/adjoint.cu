@@ -156,7 +156,7 @@ __device__ __forceinline__ void sddmm_rows3(int g, const float* Y, const float* 
 // four consumer warps per SM, whose interleaving hides the latency of the outer product's
 // reductions.
 template <int CW, bool SD>
-__global__ void __launch_bounds__(32 * (CW + 1), SD ? 3 : 1)
+__global__ void __launch_bounds__(32 * (CW + 1), SD || CW == 4 ? 3 : 1)
 clenshaw_sddmm_bulk(const int n_atoms, const int32_t* __restrict__ row_ptr,
                     const int32_t* __restrict__ col, const float* __restrict__ hv,
                     const float* __restrict__ bin, const float* bprev, float* bout,
@@ -575,6 +575,209 @@ sddmm_window(const int n_atoms, const int32_t* __restrict__ row_ptr, const int32
   if (!ok) atomicOr(err, 2);
 }
 
+// ---- outer products of a window for 256 or 512 probes ------------------------------------------
+//
+// The same sums as sddmm_window with the work split so that a lane keeps 27 accumulators instead
+// of 81 probe pairs: consumer warp (g, c) takes rows 3g .. 3g+2 of the block (27 entries) over
+// probe chunk c (128 probes, 4 per lane), for g < 3 and c < NC = P / 128.  The producer warp
+// stages the window's own-row tiles once per block row and streams the neighbour tiles through a
+// D-stage ring read by all 3 NC warps.  Per block, each warp reduces its 27 sums over the lanes
+// (one butterfly for all the window's steps) and warp (g, 0) adds the NC chunk partials in a
+// fixed order and writes the 27 totals to the FP64 accumulator: one writer per entry, so the
+// result does not depend on timing.
+template <int NC>
+struct WinGCfg {
+  static constexpr int P = 128 * NC;
+  static constexpr int NWARP = 3 * NC;  // consumer warps
+  static constexpr int THREADS = 32 * (NWARP + 1);
+  static constexpr int XB = 9 * P * 4;
+  static constexpr int D = NC == 4 ? 6 : 8;
+  static constexpr int RED = 2 * 3 * NC * 32 * 4;  // [2 buffers][3 groups][NC chunks][32 lanes]
+  static constexpr int NBAR = 2 * D + 2 + 12;
+  static constexpr int SMEM = (SDW + D) * XB + RED + 8 * NBAR;
+};
+
+template <int NC>
+__global__ void __launch_bounds__(32 * (3 * NC + 1), 1)
+sddmm_window_g(const int n_atoms, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+               const WindowPanels wp, const int nw, const uint64_t seed, const int s, const double w,
+               double* __restrict__ Gacc, int* __restrict__ err, const BatchRows batch,
+               const int32_t* __restrict__ kcl, const int k_lo) {
+  using C = WinGCfg<NC>;
+  constexpr int D = C::D, P = C::P, NWARP = C::NWARP;
+  extern __shared__ __align__(128) unsigned char smem[];
+  float* Yw = reinterpret_cast<float*>(smem);                       // SDW own-row tiles
+  unsigned char* ring = smem + SDW * C::XB;                          // D neighbour tiles
+  float* red = reinterpret_cast<float*>(smem + (SDW + D) * C::XB);   // [2][3][NC][32]
+  const uint32_t bar0 = smem_u32(smem + (SDW + D) * C::XB + C::RED);
+  auto full = [&](int i) { return bar0 + 8u * i; };
+  auto empty = [&](int i) { return bar0 + 8u * (D + i); };
+  const uint32_t y_full = bar0 + 8u * (2 * D), y_empty = bar0 + 8u * (2 * D + 1);
+  auto red_full = [&](int b, int g) { return bar0 + 8u * (2 * D + 2 + 3 * b + g); };
+  auto red_empty = [&](int b, int g) { return bar0 + 8u * (2 * D + 8 + 3 * b + g); };
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const bool probe = wp.y[0] == nullptr;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < D; ++i) {
+      mbar_init(full(i), 1);
+      mbar_init(empty(i), NWARP);
+    }
+    mbar_init(y_full, 1);
+    mbar_init(y_empty, NWARP);
+    for (int b = 0; b < 2; ++b)
+      for (int g = 0; g < 3; ++g) {
+        mbar_init(red_full(b, g), NC);
+        mbar_init(red_empty(b, g), 1);
+      }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  auto atom_window = [&](int a, int& nwa, uint64_t& sd, int64_t& rloc) {
+    nwa = nw;
+    sd = seed;
+    rloc = (int64_t)9 * a;
+    if (batch.atom_cl) {
+      const int cl = __ldg(batch.atom_cl + a);
+      sd = __ldg(batch.seed + cl);
+      rloc = (int64_t)9 * (a - __ldg(batch.atom0 + cl));
+      if (kcl) nwa = min(nw, max(0, __ldg(kcl + cl) - k_lo));
+    }
+  };
+
+  if (warp == NWARP) {
+    // producer warp: lane 0 issues the copies; in the probe case all lanes write the probe block
+    int it = 0, y_it = 0;
+    bool ok = true;
+    for (int a = blockIdx.x; a < n_atoms && ok; a += gridDim.x) {
+      int nwa;
+      uint64_t sd;
+      int64_t rloc;
+      atom_window(a, nwa, sd, rloc);
+      if (nwa == 0) continue;
+      if (lane == 0) ok = mbar_wait(y_empty, (y_it & 1) ^ 1);
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      if (!ok) break;
+      if (probe) {
+        for (int e = lane; e < 9 * P; e += 32) {
+          const int i = e / P, pr = e - i * P;
+          Yw[e] = tbk_probe_sign(sd, rloc + i, pr);
+        }
+        __threadfence_block();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(y_full);
+      } else if (lane == 0) {
+        mbar_expect_tx(y_full, nwa * C::XB);
+        for (int t = 0; t < nwa; ++t)
+          bulk_g2s(smem_u32(Yw + t * 9 * P), wp.y[t] + (int64_t)9 * a * s, C::XB, y_full);
+      }
+      ++y_it;
+      if (lane == 0) {
+        const int k0 = __ldg(row_ptr + a), k1 = __ldg(row_ptr + a + 1);
+        for (int q = k0; q < k1 && ok; ++q) {
+          const int b = __ldg(col + q);
+          for (int t = 0; t < nwa && ok; ++t) {
+            const int st = it % D;
+            ok = mbar_wait(empty(st), ((it / D) & 1) ^ 1);
+            if (!ok) break;
+            mbar_expect_tx(full(st), C::XB);
+            bulk_g2s(smem_u32(ring + st * C::XB), wp.x[t] + (int64_t)9 * b * s, C::XB, full(st));
+            ++it;
+          }
+        }
+      }
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+    }
+    if (!ok && lane == 0) {
+      atomicOr(err, 2);
+      for (int j = (it > D ? it - D : 0); j < it; ++j) mbar_wait(full(j % D), (j / D) & 1);
+      if (y_it > 0 && !probe) mbar_wait(y_full, (y_it - 1) & 1);
+    }
+    return;
+  }
+
+  const int g = warp / NC, c = warp - g * NC;
+  const int pl = 128 * c + 4 * lane;  // this lane's 4 probes
+  int it = 0, y_it = 0, r_it = 0;
+  bool ok = true;
+  for (int a = blockIdx.x; a < n_atoms && ok; a += gridDim.x) {
+    int nwa;
+    uint64_t sd;
+    int64_t rloc;
+    atom_window(a, nwa, sd, rloc);
+    if (nwa == 0) continue;
+    const int k0 = __ldg(row_ptr + a), k1 = __ldg(row_ptr + a + 1);
+    ok = mbar_wait(y_full, y_it & 1);
+    ok = __all_sync(0xffffffffu, ok);
+    if (!ok) break;
+    for (int q = k0; q < k1; ++q) {
+      float acc[27];
+#pragma unroll
+      for (int e = 0; e < 27; ++e) acc[e] = 0.f;
+      for (int t = 0; t < nwa; ++t) {
+        const int st = it % D;
+        ok = mbar_wait(full(st), (it / D) & 1);
+        ok = __all_sync(0xffffffffu, ok);
+        if (!ok) break;
+        const float* X = reinterpret_cast<const float*>(ring + st * C::XB);
+        const float* Y = Yw + t * 9 * P + 3 * g * P;
+        float4 yv[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) yv[i] = *reinterpret_cast<const float4*>(Y + i * P + pl);
+#pragma unroll
+        for (int l = 0; l < 9; ++l) {
+          const float4 xv = *reinterpret_cast<const float4*>(X + l * P + pl);
+#pragma unroll
+          for (int i = 0; i < 3; ++i) {
+            float u = acc[i * 9 + l];
+            u = fmaf(yv[i].x, xv.x, u); u = fmaf(yv[i].y, xv.y, u);
+            u = fmaf(yv[i].z, xv.z, u); u = fmaf(yv[i].w, xv.w, u);
+            acc[i * 9 + l] = u;
+          }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(empty(st));
+        ++it;
+      }
+      if (!ok) break;
+      // lanes -> lane e holds this chunk's sum of entry 27 g + e
+      float v[32];
+#pragma unroll
+      for (int e = 0; e < 32; ++e) v[e] = e < 27 ? acc[e] : 0.f;
+      butterfly32(v, lane);
+      const int rb = r_it & 1, use = r_it >> 1;
+      if (use > 0) {
+        ok = mbar_wait(red_empty(rb, g), (use - 1) & 1);
+        ok = __all_sync(0xffffffffu, ok);
+        if (!ok) break;
+      }
+      float* R = red + (rb * 3 + g) * NC * 32;
+      R[c * 32 + lane] = v[0];
+      __syncwarp();
+      if (lane == 0) mbar_arrive(red_full(rb, g));
+      if (c == 0) {
+        // fixed-order sum over the chunks, one writer per entry
+        ok = mbar_wait(red_full(rb, g), use & 1);
+        ok = __all_sync(0xffffffffu, ok);
+        if (!ok) break;
+        if (lane < 27) {
+          float tsum = R[lane];
+#pragma unroll
+          for (int cc = 1; cc < NC; ++cc) tsum += R[cc * 32 + lane];
+          atomicAdd(Gacc + (int64_t)q * 81 + 27 * g + lane, w * (double)tsum);
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(red_empty(rb, g));
+      }
+      ++r_it;
+    }
+    if (!ok) break;
+    __syncwarp();
+    if (lane == 0) mbar_arrive(y_empty);
+    ++y_it;
+  }
+  if (!ok) atomicOr(err, 2);
+}
+
 // ---- self-fed adjoint step for 128 probes (windowed schedule) ---------------------------------
 //
 // clenshaw_sddmm_bulk<1, false> with one warp per CTA and no producer warp: lane 0 keeps R tiles
@@ -944,12 +1147,27 @@ static void launch_window_cw(tbk_ctx* ctx, const HOp& op, const WindowPanels& wp
 // Gacc_ab += w sum_t sum_probes y_t[a] x_t[b]^T over the stored blocks, 1 <= nw <= SDW steps
 // (t = 0 is step k_lo).  Batch: per-cluster probe streams, and with kcl (K per cluster) each
 // cluster's steps >= K_c are left out.
+template <int NC>
+static void launch_window_g(tbk_ctx* ctx, const HOp& op, const WindowPanels& wp, int nw, uint64_t seed,
+                            int s, double w, double* Gacc, int* err, const BatchRows& batch,
+                            const int32_t* kcl, int k_lo) {
+  using C = WinGCfg<NC>;
+  TBK_CUDA(cudaFuncSetAttribute(sddmm_window_g<NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
+  int occ = 0;
+  TBK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, sddmm_window_g<NC>, C::THREADS, C::SMEM));
+  TBK_CHECK_ARG(occ > 0, "windowed outer-product kernel does not fit on this device");
+  const int G = std::max(1, std::min(op.n_atoms, occ * ctx->num_sms));
+  sddmm_window_g<NC><<<G, C::THREADS, C::SMEM, ctx->stream>>>(op.n_atoms, op.row_ptr, op.col, wp, nw, seed,
+                                                               s, w, Gacc, err, batch, kcl, k_lo);
+  post_launch(ctx, "sddmm_window_g");
+}
+
 void launch_window(tbk_ctx* ctx, const HOp& op, const WindowPanels& wp, int nw, uint64_t seed, int s,
                    double w, double* Gacc, int* err, const BatchRows& batch, const int32_t* kcl, int k_lo) {
   KernelTimerScope timer(ctx, TBK_KERNEL_WINDOW);
   TBK_CHECK_ARG(nw >= 1 && nw <= SDW && (wp.y[0] != nullptr || nw == 1), "bad outer-product window");
-  if (s == 512) launch_window_cw<4>(ctx, op, wp, nw, seed, s, w, Gacc, err, batch, kcl, k_lo);
-  else if (s == 256) launch_window_cw<2>(ctx, op, wp, nw, seed, s, w, Gacc, err, batch, kcl, k_lo);
+  if (s == 512) launch_window_g<4>(ctx, op, wp, nw, seed, s, w, Gacc, err, batch, kcl, k_lo);
+  else if (s == 256) launch_window_g<2>(ctx, op, wp, nw, seed, s, w, Gacc, err, batch, kcl, k_lo);
   else launch_window_cw<1>(ctx, op, wp, nw, seed, s, w, Gacc, err, batch, kcl, k_lo);
 }
 

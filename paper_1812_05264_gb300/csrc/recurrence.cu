@@ -348,10 +348,9 @@ cheb_step_bulk(const int n_atoms, const int32_t* __restrict__ row_ptr, const int
     for (int i = 0; i < 9; ++i) acc[i][0] = acc[i][1] = make_float2(0.f, 0.f);
     for (int q = 0; q < k1 - k0; ++q) {
       const int st = it % R;
-      if (!rdy) {
-        ok = mbar_wait(full(st), (it / R) & 1);
-        if (!ok) break;
-      }
+      if (!rdy) ok = mbar_wait(full(st), (it / R) & 1);
+      ok = __all_sync(0xffffffffu, ok);  // one decision per warp: the warps meet at a barrier below
+      if (!ok) break;
       rdy = mbar_test(full((it + 1) % R), ((it + 1) / R) & 1);
       const unsigned char* base = smem + st * C::SB;
       const float* X = reinterpret_cast<const float*>(base);
@@ -366,10 +365,9 @@ cheb_step_bulk(const int n_atoms, const int32_t* __restrict__ row_ptr, const int
     float yp[9][4];
     if (has_prev) {
       const int st = it % R;
-      if (!rdy) {
-        ok = mbar_wait(full(st), (it / R) & 1);
-        if (!ok) break;
-      }
+      if (!rdy) ok = mbar_wait(full(st), (it / R) & 1);
+      ok = __all_sync(0xffffffffu, ok);  // one decision per warp: the warps meet at a barrier below
+      if (!ok) break;
       rdy = mbar_test(full((it + 1) % R), ((it + 1) / R) & 1);
       const float* X = reinterpret_cast<const float*>(smem + st * C::SB);
 #pragma unroll

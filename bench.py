@@ -201,9 +201,10 @@ def run_reference(args, rank, world):
 # our arm
 # ---------------------------------------------------------------------------------------------
 
-def traffic_from_profile(kernel_file: str, src_name: str):
+def traffic_from_profile(kernel_file: str, src_name: str, workload: str):
     """Per-launch DRAM bytes of a kernel from its committed ncu summary, if that summary was taken
-    on the current source of the file that holds the kernel (matching sha256 prefix); else None."""
+    on this workload and on the current source of the file that holds the kernel (matching
+    sha256 prefix); else None."""
     import hashlib
     src = os.path.join(ROOT, "paper_1812_05264_gb300", "csrc", src_name)
     sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
@@ -215,7 +216,7 @@ def traffic_from_profile(kernel_file: str, src_name: str):
         if ": " in ln and ln.strip().startswith("- "):
             k, v = ln.strip()[2:].split(": ", 1)
             vals[k.strip()] = v.strip()
-    if vals.get(f"{src_name} sha256[:16]") != sha:
+    if vals.get(f"{src_name} sha256[:16]") != sha or vals.get("workload") != workload:
         return None
     try:
         return float(vals["dram bytes per launch (full size)"])
@@ -341,22 +342,26 @@ def run_ours(args, rank, world):
     # algorithmic bytes and flops (2 per FMA) of each family over the timed steps
     hb, blk = nnzb * B2 * esz, 2 * nnzb * B2 * wk.n_probes
     windowed = args.adjoint == "windowed" or (args.adjoint == "auto" and bool(tuned and tuned[1]))
+    # the kernels that ran: 128-probe tasks take the self-fed kernels; the profiles under
+    # profiles/ are of the TMA-fed step and the fused adjoint step
+    chunk = tuned[0] if tuned else wk.n_probes
+    step_k = "cheb_step_self" if chunk == 128 or wk.n_probes == 128 else "cheb_step_bulk"
+    bwd_k = "clenshaw_self" if windowed and wk.n_probes == 128 else "clenshaw_sddmm_bulk"
     alg = {
         # y_{k+1} = 2 H^ y_k - y_{k-1}: reads y_k, y_{k-1}, the H^ blocks, writes y_{k+1}
-        "step": (lambda n: n * (3 * panel + hb), lambda n: n * blk, "cheb_step_bulk",
-                 "cheb_step_bulk_fcc10000.md", "recurrence.cu"),
+        "step": (lambda n: n * (3 * panel + hb), lambda n: n * blk, step_k,
+                 "cheb_step_bulk_fcc10000.md" if step_k == "cheb_step_bulk" else None, "recurrence.cu"),
         # ybar_k = g_k + 2 H^ ybar_{k+1} - ybar_{k+2}: reads ybar_{k+1}, ybar_{k+2}, y_k, y_{k-1},
         # y_{k+1}, the H^ blocks, writes ybar_k; fused: and G += 2 y_k ybar_{k+1}^T (the same
         # tiles, as many FMAs again, the FP64 accumulator read and written once)
         "backward": (lambda n: n * (6 * panel + hb + (0 if windowed else nnzb * B2 * 16)),
-                     lambda n: n * blk * (1 if windowed else 2), "clenshaw_sddmm_bulk",
-                     "clenshaw_sddmm_bulk_fcc10000.md", "adjoint.cu"),
+                     lambda n: n * blk * (1 if windowed else 2), bwd_k,
+                     None if windowed else "clenshaw_sddmm_bulk_fcc10000.md", "adjoint.cu"),
         # G += sum_j y_j ybar_{j+1}^T (j = 0 .. K-1, K pairs a step): reads both panels of every
         # pair, reads and writes the FP64 accumulator once per window
         "window": (lambda n: args.steps * (K * 2 * panel + nwin * nnzb * B2 * 16),
                    lambda n: args.steps * K * blk,
-                   "sddmm_window_g" if wk.n_probes >= 256 else "sddmm_window",
-                   "sddmm_window_fcc10000.md", "adjoint.cu"),
+                   "sddmm_window_g" if wk.n_probes >= 256 else "sddmm_window", None, "adjoint.cu"),
     }
     kernels = {}
     for f, (tms, nl) in fam.items():
@@ -374,7 +379,7 @@ def run_ours(args, rank, world):
             r = {"bound": "hbm", "achieved": by / sec / 1e9, "peak": hbm, "unit": "GB/s",
                  "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
         r["frac"] = r["achieved"] / r["peak"]
-        r.update(kernel=kname, traffic=traffic_from_profile(prof, src),
+        r.update(kernel=kname, traffic=traffic_from_profile(prof, src, wk.name) if prof else None,
                  algorithmic_bytes_per_launch=by * args.steps / nl,
                  algorithmic_flops_per_launch=fl * args.steps / nl,
                  avg_launch_ms=tms / nl, launches_timed=nl, share_of_step=tms / (ms * args.steps))
@@ -616,7 +621,7 @@ def run_batched(args, rank, world):
         wb += K * 2 * panel + (K / 4 + 1) * blocks * 16
         wf += K * 2 * blocks * s
     kernels = {}
-    for f, by, fl, kname in (("step", fb, ff, "cheb_step_bulk (batched)"),
+    for f, by, fl, kname in (("step", fb, ff, ("cheb_step_self" if s == 128 else "cheb_step_bulk") + " (batched)"),
                              ("backward", bb, bf, "clenshaw_self (batched)" if windowed
                               else "clenshaw_sddmm_bulk (batched)"),
                              ("window", wb, wf, "sddmm_window (batched)")):

@@ -137,6 +137,14 @@ def exact_moments(eps, V, R, emin, emax, p):
     return cheb_T(mapped(eps, emin, emax), p) @ w
 
 
+def exact_probe_moments(eps, V, R, emin, emax, p):
+    """mu_k^(i) = r_i^T C_k(H^) r_i for k < p (rows) and each probe i (columns), exactly: with
+    c_i = V^T r_i, mu_k^(i) = sum_n c_in^2 C_k(x_n).  Their mean over i is exact_moments; their
+    spread is the sampling error of Sec. II.C.2."""
+    C = V.T @ R
+    return cheb_T(mapped(eps, emin, emax), p) @ (C * C)
+
+
 def estimator_observables(moments, emin, emax, mu, T, use_jackson=False):
     """(Omega^, E^, N^) = sum_k g_k c_k mu_k with c = beta[g], alpha[eps f], alpha[f]."""
     p = len(moments)

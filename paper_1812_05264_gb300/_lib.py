@@ -81,6 +81,7 @@ SIGNATURES = {
     "tbk_batched_spectral_bounds": [_P, _I, C.POINTER(tbk_bsr), _I, _D, _U, C.POINTER(_D), C.POINTER(_D)],
     "tbk_chebyshev_coefficients": [_P, _I, _I, _D, _D, _D, _D, _I, _P],
     "tbk_chebyshev_moments": [_P, C.POINTER(tbk_bsr), _D, _D, _U, _I, _I, _I, _P],
+    "tbk_chebyshev_probe_moments": [_P, C.POINTER(tbk_bsr), _D, _D, _U, _I, _I, _I, _P, _P],
     "tbk_chebyshev_moments_noalloc": [_P, C.POINTER(tbk_bsr), _D, _D, _U, _I, _I, _I, _P],
     "tbk_energies_and_forces": [_P, C.POINTER(tbk_bsr), C.POINTER(tbk_model), _P, _P, _D, _D, _U,
                                 _I, _I, _D, _D, _I, _I, _L, _P, C.POINTER(_D), _P, _P],

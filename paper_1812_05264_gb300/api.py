@@ -220,6 +220,21 @@ def chebyshev_moments(ctx: Context, H: BSR, emin: float, emax: float, seed: int,
     return out
 
 
+def chebyshev_probe_moments(ctx: Context, H: BSR, emin: float, emax: float, seed: int, n_probes: int,
+                            order: int, fp64: bool = False, direct: bool = False,
+                            plain: bool = False) -> tuple[torch.Tensor, torch.Tensor]:
+    """a7 per probe: (moments (order,), per_probe (order, n_probes)) with per_probe[k, i] =
+    r_i^T C_k(H^) r_i; the mean over i is moments[k]."""
+    dev = H.val.device
+    mom = torch.empty(order, dtype=torch.float64, device=dev)
+    per = torch.empty((order, n_probes), dtype=torch.float64, device=dev)
+    flags = ((L.TBK_FP64 if fp64 else L.TBK_MIXED) | (L.TBK_MOMENTS_DIRECT if direct else 0)
+             | (L.TBK_PLAIN_KERNEL if plain else 0))
+    L.call("tbk_chebyshev_probe_moments", ctx.handle, C.byref(H.struct()), emin, emax, C.c_uint64(seed),
+           int(n_probes), int(order), flags, _ptr(mom), _ptr(per))
+    return mom, per
+
+
 def fermi_level(ctx: Context, moments: torch.Tensor, emin: float, emax: float,
                 n_electrons: float | None, kT: float, jackson: bool = False,
                 mu: float | None = None) -> tuple[float, float, float, float]:

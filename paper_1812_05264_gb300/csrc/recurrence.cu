@@ -895,6 +895,78 @@ __global__ void finish_moments(const double* __restrict__ sums, int K, int order
   }
 }
 
+// ---- per-probe moments -------------------------------------------------------------------------
+//
+// After step j, PD_BLOCKS row blocks each sum, for every probe i, the products of the new panel
+// y_j with itself and with y_{j-1} (the probe block r for j = 1) over their rows:
+//   part[(rb s + i) 2 + 0] = sum_rows y_j y_j   (direct: sum_rows r y_j),
+//   part[(rb s + i) 2 + 1] = sum_rows y_j y_{j-1}.
+// FP32 panels: products are summed in FP32 over runs of 32 rows, then in FP64.  A second kernel
+// adds the row blocks in a fixed order, so the result does not depend on timing.
+constexpr int PD_BLOCKS = 304;
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+probe_dots(int64_t n_rows, int s, int64_t rows_per_block, const T* __restrict__ y,
+           const T* __restrict__ x, uint64_t seed, int direct, double* __restrict__ part) {
+  const int64_t r0 = (int64_t)blockIdx.x * rows_per_block;
+  const int64_t r1 = r0 + rows_per_block < n_rows ? r0 + rows_per_block : n_rows;
+  for (int i = threadIdx.x; i < s; i += blockDim.x) {
+    double d0 = 0.0, d1 = 0.0;
+    for (int64_t b = r0; b < r1; b += 32) {
+      const int64_t e = b + 32 < r1 ? b + 32 : r1;
+      T t0 = T(0), t1 = T(0);
+      for (int64_t row = b; row < e; ++row) {
+        const T v = y[row * s + i];
+        if (direct) {
+          t0 += v * (T)tbk_probe_sign(seed, row, i);
+        } else {
+          const T u = x ? x[row * s + i] : (T)tbk_probe_sign(seed, row, i);
+          t0 += v * v;
+          t1 += v * u;
+        }
+      }
+      d0 += (double)t0;
+      d1 += (double)t1;
+    }
+    part[((int64_t)blockIdx.x * s + i) * 2] = d0;
+    part[((int64_t)blockIdx.x * s + i) * 2 + 1] = d1;
+  }
+}
+
+// dots[i 2 + c] = sum over the row blocks, in order, of part[(rb s + i) 2 + c]
+__global__ void probe_dots_reduce(int nrb, int s, const double* __restrict__ part, double* __restrict__ dots) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= s) return;
+  double a = 0.0, b = 0.0;
+  for (int rb = 0; rb < nrb; ++rb) {
+    a += part[((int64_t)rb * s + i) * 2];
+    b += part[((int64_t)rb * s + i) * 2 + 1];
+  }
+  dots[2 * i] = a;
+  dots[2 * i + 1] = b;
+}
+
+// per_probe[k s + i] = r_i^T C_k(H^) r_i from the dots of steps j = 1 .. K (dots[((j-1) s + i) 2
+// + c]): mu_0 = n_rows; direct: mu_k = (r . y_k); doubling: mu_1 = y_1 . r, mu_2k = 2 y_k . y_k -
+// mu_0, mu_2k-1 = 2 y_k . y_{k-1} - mu_1 (the identities the summed moments use).
+__global__ void probe_moments_finish(const double* __restrict__ dots, int K, int order, int s,
+                                     int64_t n_rows, int direct, double* __restrict__ per_probe) {
+  const int64_t n = (int64_t)order * s;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+    const int k = (int)(t / s), i = (int)(t - (int64_t)k * s);
+    auto d = [&](int j, int c) { return dots[((int64_t)(j - 1) * s + i) * 2 + c]; };
+    const double mu0 = (double)n_rows;
+    double v;
+    if (k == 0) v = mu0;
+    else if (direct) v = d(k, 0);
+    else if (k == 1) v = d(1, 1);
+    else if ((k & 1) == 0) v = 2.0 * d(k / 2, 0) - mu0;
+    else v = 2.0 * d((k + 1) / 2, 1) - d(1, 1);
+    per_probe[t] = v;
+  }
+}
+
 // ---- building blocks that allocate nothing (for the static-scratch entry point) --------------
 
 size_t mapped_h_bytes(const tbk_bsr* H, int prec) {
@@ -951,17 +1023,15 @@ void launch_moment_reduction(tbk_ctx* ctx, const double* partials, int nctas, in
 
 using namespace tbk;
 
-extern "C" int tbk_chebyshev_moments(tbk_ctx* ctx, const tbk_bsr* H, double emin, double emax,
-                                     uint64_t probe_seed, int32_t n_probes, int32_t order,
-                                     int32_t flags, double* moments) {
-  TBK_API_BEGIN
-  TBK_CHECK_ARG(ctx != nullptr, "ctx is NULL");
-  TBK_CHECK_ARG(moments != nullptr, "moments is NULL");
+namespace tbk {
+// The moments sweep of tbk_chebyshev_moments; with per_probe, every step is followed by the
+// per-probe dot products of its panels.
+static void moments_sweep(tbk_ctx* ctx, const tbk_bsr* H, double emin, double emax, uint64_t probe_seed,
+                          int32_t n_probes, int32_t order, int32_t flags, double* moments, double* per_probe) {
   TBK_CHECK_ARG(order >= 1, "order must be >= 1");
   TBK_CHECK_ARG(n_probes >= 4 && n_probes % 4 == 0, "n_probes must be a positive multiple of 4");
   TBK_CHECK_ARG((flags & ~(TBK_FP64 | TBK_MOMENTS_DIRECT | TBK_PLAIN_KERNEL | TBK_TENSOR_CORES)) == 0,
                 "unknown flag");
-  DeviceGuard dg(ctx);
   const int prec = (flags & TBK_FP64) ? TBK_FP64 : TBK_MIXED;
   const int direct = (flags & TBK_MOMENTS_DIRECT) ? 1 : 0;
   int* flag = (int*)scratch(ctx, WS_FLAGS, 64);
@@ -976,6 +1046,12 @@ extern "C" int tbk_chebyshev_moments(tbk_ctx* ctx, const tbk_bsr* H, double emin
   double* sums = (double*)scratch(ctx, WS_MISC, sizeof(double) * 2 * (size_t)std::max(1, K) + 64);
   void* A = K >= 1 ? scratch(ctx, WS_PANEL0, panel) : nullptr;
   void* Bp = K >= 2 ? scratch(ctx, WS_PANEL1, panel) : nullptr;
+  // per-probe dots: row-block partials of one step, then K x s x 2 reduced dots
+  const int64_t rpb = (op.n_rows + PD_BLOCKS - 1) / PD_BLOCKS;
+  const int nrb = (int)((op.n_rows + rpb - 1) / rpb);
+  double* pd_part = per_probe ? (double*)scratch(ctx, WS_PANEL2, sizeof(double) * 2 * (size_t)nrb * s) : nullptr;
+  double* pd_dots = per_probe ? (double*)scratch(ctx, WS_SEGMENT, sizeof(double) * 2 * (size_t)std::max(1, K) * s)
+                              : nullptr;
   void *cur = nullptr, *prev = nullptr;
   for (int j = 1; j <= K; ++j) {
     StepArgs a;
@@ -1006,6 +1082,19 @@ extern "C" int tbk_chebyshev_moments(tbk_ctx* ctx, const tbk_bsr* H, double emin
       std::swap(cur, prev);  // y_{j} now lives where y_{j-2} was
     }
     launch_step(ctx, op, a);
+    if (per_probe) {
+      // y_j at a.yout; y_{j-1} at a.yin (the probe block for j = 1)
+      if (prec == TBK_MIXED)
+        probe_dots<float><<<nrb, 256, 0, ctx->stream>>>(op.n_rows, s, rpb, (const float*)a.yout,
+                                                        (const float*)a.yin, probe_seed, direct, pd_part);
+      else
+        probe_dots<double><<<nrb, 256, 0, ctx->stream>>>(op.n_rows, s, rpb, (const double*)a.yout,
+                                                         (const double*)a.yin, probe_seed, direct, pd_part);
+      post_launch(ctx, "probe_dots");
+      probe_dots_reduce<<<ceil_div(s, 256), 256, 0, ctx->stream>>>(nrb, s, pd_part,
+                                                                    pd_dots + (size_t)(j - 1) * 2 * s);
+      post_launch(ctx, "probe_dots_reduce");
+    }
   }
   if (K >= 1) {
     reduce_partials<<<K, 256, 0, ctx->stream>>>(partials, nctas, sums);
@@ -1013,6 +1102,12 @@ extern "C" int tbk_chebyshev_moments(tbk_ctx* ctx, const tbk_bsr* H, double emin
   }
   finish_moments<<<1, 256, 0, ctx->stream>>>(sums, K, order, s, op.n_rows, direct, moments, flag);
   post_launch(ctx, "finish_moments");
+  if (per_probe) {
+    const int64_t n = (int64_t)order * s;
+    probe_moments_finish<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, ctx->stream>>>(
+        pd_dots, K, order, s, op.n_rows, direct, per_probe);
+    post_launch(ctx, "probe_moments_finish");
+  }
   int hflag = 0;
   TBK_CUDA(cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   sync(ctx);
@@ -1021,5 +1116,29 @@ extern "C" int tbk_chebyshev_moments(tbk_ctx* ctx, const tbk_bsr* H, double emin
   if (hflag)
     throw Error(TBK_ERR_SPECTRUM, "a Chebyshev panel grew beyond ||r||: the spectrum of H is not "
                                   "inside [emin, emax]");
+}
+}  // namespace tbk
+
+extern "C" int tbk_chebyshev_moments(tbk_ctx* ctx, const tbk_bsr* H, double emin, double emax,
+                                     uint64_t probe_seed, int32_t n_probes, int32_t order,
+                                     int32_t flags, double* moments) {
+  TBK_API_BEGIN
+  TBK_CHECK_ARG(ctx != nullptr, "ctx is NULL");
+  TBK_CHECK_ARG(moments != nullptr, "moments is NULL");
+  DeviceGuard dg(ctx);
+  moments_sweep(ctx, H, emin, emax, probe_seed, n_probes, order, flags, moments, nullptr);
+  TBK_API_END
+}
+
+extern "C" int tbk_chebyshev_probe_moments(tbk_ctx* ctx, const tbk_bsr* H, double emin, double emax,
+                                           uint64_t probe_seed, int32_t n_probes, int32_t order,
+                                           int32_t flags, double* moments, double* per_probe) {
+  TBK_API_BEGIN
+  TBK_CHECK_ARG(ctx != nullptr, "ctx is NULL");
+  TBK_CHECK_ARG(per_probe != nullptr, "per_probe is NULL");
+  DeviceGuard dg(ctx);
+  double* mom = moments;
+  if (!mom) mom = (double*)scratch(ctx, WS_COEF, sizeof(double) * (size_t)std::max(1, order));
+  moments_sweep(ctx, H, emin, emax, probe_seed, n_probes, order, flags, mom, per_probe);
   TBK_API_END
 }

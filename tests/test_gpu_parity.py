@@ -426,6 +426,29 @@ def test_windowed_outer_products_match_fused(api, ctx, s, p):
     assert np.abs(F2.cpu().numpy() - F).max() < 1e-3
 
 
+@pytest.mark.parametrize("s,fp64,direct", [(16, True, False), (16, True, True), (128, False, False),
+                                            (512, False, True), (512, False, False)])
+def test_probe_moments_vs_oracle(api, ctx, s, fp64, direct):
+    """a7 per probe: r_i^T C_k(H^) r_i for every probe against the oracle's exact values (plain,
+    self-fed and TMA-fed steps); the sweep's summed moments equal tbk_chebyshev_moments, the mean
+    over the probes equals them to rounding, and a second call repeats every bit."""
+    wk = small_fcc(40, n_probes=s)
+    rp, col, H = oracle_H(wk)
+    sv, pos, res = _gpu_run(api, ctx, wk, 20, fp64=fp64)
+    p, n = 61, H.shape[0]
+    args = (ctx, res.H, res.emin, res.emax, wk.probe_seed, s, p)
+    mom, per = api.chebyshev_probe_moments(*args, fp64=fp64, direct=direct)
+    assert per.shape == (p, s)
+    assert torch.equal(mom, api.chebyshev_moments(*args, fp64=fp64, direct=direct))
+    w, V = np.linalg.eigh(H)
+    exact = och.exact_probe_moments(w, V, och.probes(n, s, wk.probe_seed), res.emin, res.emax, p)
+    assert np.abs(per.cpu().numpy() - exact).max() < (1e-11 if fp64 else 2e-5) * n
+    assert np.allclose(per.mean(dim=1).cpu().numpy(), mom.cpu().numpy(), rtol=0,
+                       atol=(1e-12 if fp64 else 1e-6) * n)
+    _, again = api.chebyshev_probe_moments(*args, fp64=fp64, direct=direct)
+    assert torch.equal(per, again)
+
+
 def test_row_without_its_diagonal_block_is_rejected(api, ctx):
     """H^ = (2H - (emax + emin) I) / W keeps its shift on the diagonal blocks, so a pattern in which
     an atom's row stores no block at all is refused with TBK_ERR_ARG by every call that maps H

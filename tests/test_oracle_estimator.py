@@ -108,6 +108,46 @@ def test_moments_match_dense_matrix_recurrence():
     assert mu[0] == pytest.approx(H.shape[0])              # Rademacher: r^T r = n exactly
 
 
+def test_probe_moments_match_dense_recurrence_per_probe():
+    """Each probe's moments from the eigen route against r_i . y_k of the matrix recurrence run on
+    that probe alone; their mean is exact_moments and mu_0 is n for every +-1 probe."""
+    _, _, _, _, H = _small_sk()
+    w, Vv = np.linalg.eigh(H)
+    emin, emax = w.min() - 1.0, w.max() + 1.0
+    s, p = 6, 25
+    R = ch.probes(H.shape[0], s, 23)
+    per = ch.exact_probe_moments(w, Vv, R, emin, emax, p)
+    assert per.shape == (p, s)
+    Hh = (2 * H - (emax + emin) * np.eye(H.shape[0])) / (emax - emin)
+    for i in range(s):
+        r = R[:, i]
+        y0, y1 = r, Hh @ r
+        ref = [r @ y0, r @ y1]
+        for _ in range(2, p):
+            y0, y1 = y1, 2 * Hh @ y1 - y0
+            ref.append(r @ y1)
+        assert np.allclose(per[:, i], ref, rtol=1e-11, atol=1e-9)
+    assert np.all(per[0] == pytest.approx(H.shape[0]))
+    assert np.allclose(per.mean(axis=1), ch.exact_moments(w, Vv, R, emin, emax, p), rtol=1e-13, atol=1e-10)
+
+
+def test_probe_spread_gives_the_hutchinson_error():
+    """The standard deviation over probes of the single-probe estimates, / sqrt(s), estimates the
+    exact standard error 2 sum_{j!=k} A_jk^2 / s of the trace estimate (Sec. II.C.2)."""
+    pos, rp, col, V, H = _small_sk(n=55, jitter=0.0)
+    w, Vv = np.linalg.eigh(H)
+    T, p, s = 0.5, 300, 2048
+    mu = physics.chemical_potential(w, 11.0 * pos.shape[0], T)
+    emin, emax = w.min() - 0.5, w.max() + 0.5
+    _, _, bg = ch.fd_coefficients(p, emin, emax, mu, T)
+    R = ch.probes(H.shape[0], s, 91)
+    per = ch.exact_probe_moments(w, Vv, R, emin, emax, p)
+    omega_i = bg @ per                       # one estimate per probe
+    se = omega_i.std(ddof=1) / np.sqrt(s)
+    A = Vv @ np.diag(ch.poly_values(bg, ch.mapped(w, emin, emax))) @ Vv.T
+    assert se == pytest.approx(ch.hutchinson_sigma(A, s), rel=0.1)
+
+
 def test_estimator_exact_for_diagonal_H():
     """Diagonal H: r_j^2 = 1 makes the probe estimate exact for any s."""
     rng = np.random.default_rng(5)

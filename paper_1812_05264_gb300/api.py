@@ -454,12 +454,14 @@ class FreeEnergy(torch.autograd.Function):
     """A^(R) = Omega^ + mu^ N_e of the probe estimate; backward returns -F (bounds held fixed).
 
     At fixed electron count dA^/dR = dOmega^/dR at fixed mu (the polynomial coefficients satisfy
-    d beta[g]/d mu = -alpha[f] exactly), which the adjoint kernel evaluates.
+    d beta[g]/d mu = -alpha[f] exactly), which the adjoint kernel evaluates.  ``bounds`` (emin,
+    emax) fixes the spectral interval instead of taking it from Lanczos at ``pos``: with it, A^ is
+    the smooth function of the positions whose gradient the backward pass returns.
     """
 
     @staticmethod
-    def forward(fctx, pos: torch.Tensor, solver: Solver):
-        res = solver.energies(pos.detach().contiguous())
+    def forward(fctx, pos: torch.Tensor, solver: Solver, bounds=None):
+        res = solver.energies(pos.detach().contiguous(), bounds=bounds)
         fctx.solver = solver
         fctx.res = res
         fctx.save_for_backward(pos)
@@ -470,4 +472,4 @@ class FreeEnergy(torch.autograd.Function):
     def backward(fctx, grad):
         (pos,) = fctx.saved_tensors
         res = fctx.solver.forces(pos.detach().contiguous(), fctx.res)
-        return -res.forces * grad, None
+        return -res.forces * grad, None, None

@@ -223,6 +223,38 @@ def test_autograd_free_energy(api, ctx):
     assert torch.allclose(pos.grad, -r2.forces)
 
 
+def test_autograd_forces_match_central_finite_differences(api, ctx):
+    """Forces from the adjoint kernel through torch.autograd against central differences
+    (dx = 1e-4 A) of A^ = Omega^ + mu^ N_e on 8 random atoms.  FP64 recurrence; the spectral
+    bounds, probes and order are held fixed, as in the analytic derivative (Sec. II.D).  No pair
+    distance of the jittered fcc cluster is near the 4.0 A cutoff (shells at 3.61 and 4.42 A), so
+    the pattern does not change under the displacements."""
+    wk = small_fcc(60, n_probes=16, order=150, kT=0.5)
+    s = api.Solver(wk, ctx)
+    pos0 = _dev(wk.positions)
+    r0 = s.energies(pos0, fp64=True)
+    bounds = (r0.emin - 0.5, r0.emax + 0.5)
+    pos = pos0.clone().requires_grad_(True)
+    A = api.FreeEnergy.apply(pos, s, bounds)
+    A.backward()
+    grad = pos.grad.cpu().numpy()
+    ne = wk.n_electrons
+
+    def a_hat(p):
+        r = s.energies(p, fp64=True, bounds=bounds)
+        return r.Omega + r.mu * ne
+
+    rng = np.random.default_rng(1812)
+    h = 1e-4
+    for a in rng.choice(wk.n_atoms, 8, replace=False):
+        for c in range(3):
+            pp, pm = pos0.clone(), pos0.clone()
+            pp[a, c] += h
+            pm[a, c] -= h
+            fd = (a_hat(pp) - a_hat(pm)) / (2 * h)
+            assert grad[a, c] == pytest.approx(fd, abs=1e-5, rel=1e-5)
+
+
 # ---- error paths ------------------------------------------------------------------------------
 
 def test_too_narrow_bounds_raise_spectrum_error(api, ctx):

@@ -64,3 +64,12 @@ def test_errors_without_a_device_are_reported_not_raised(lib):
     rc = lib.tbk_chebyshev_moments(None, None, 0.0, 1.0, 0, 8, 10, 0, None)
     assert rc == _lib.TBK_ERR_ARG
     assert b"NULL" in lib.tbk_last_error()
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    """No fallback: without the built library the binding raises instead of computing anything."""
+    code = ("from paper_1812_05264_gb300 import _lib\n"
+            f"_lib.load({str(tmp_path / 'libtbk.so')!r})\n")
+    r = subprocess.run(["python", "-c", code], cwd=ROOT, capture_output=True, text=True)
+    assert r.returncode != 0
+    assert "libtbk.so not found" in r.stderr

@@ -1243,7 +1243,26 @@ void adjoint_doubling(tbk_ctx* ctx, const HOp& op, uint64_t probe_seed, int s, i
     const int r = std::max(2, (int)std::ceil(std::sqrt(2.0 * npan)));
     return ((r + SDW - 1) / SDW) * SDW;
   };
-  if ((size_t)(npan + 2 + NX) * panel > budget && npan > 2) {
+  // A batch's step t runs on the clusters with K_c >= t, a prefix of the merged rows, so its
+  // all-stored plan can keep every y_j compactly: panel j holds the rows of the clusters still
+  // running at step j - 1 (backward step j - 1 reads y_j on those rows, with a zero coefficient
+  // for the clusters that stop there).  poff: byte offsets of P(0 .. npan) and E = y_{npan+1}.
+  bool prefix = false;
+  std::vector<size_t> poff;
+  size_t prefix_tail = 0;
+  if (bt) {
+    const size_t row_bytes = (size_t)op.B * s * 4;
+    poff.resize((size_t)npan + 2);
+    size_t o = 0;
+    for (int i = 0; i <= npan + 1; ++i) {
+      poff[i] = o;
+      o += (size_t)active(std::max(i - 1, 0)) * row_bytes;
+      o = (o + 255) & ~(size_t)255;
+    }
+    prefix_tail = o;
+    prefix = o + (size_t)NX * panel <= budget;
+  }
+  if (!prefix && (size_t)(npan + 2 + NX) * panel > budget && npan > 2) {
     seg = seg_plan();
     const size_t need = (size_t)(2 * ((npan + seg - 1) / seg) + seg + 2 + NX) * panel;
     if (need > budget)
@@ -1254,6 +1273,7 @@ void adjoint_doubling(tbk_ctx* ctx, const HOp& op, uint64_t probe_seed, int s, i
   // P(0 .. seg): segment panels (P(i) = y_{t0 - 1 + i}); checkpoints (y_{t0-2}, y_{t0-1}); E = y_{t1+1};
   // NB ybar panels; the probe panel of a batch
   auto plan_bytes = [&]() {
+    if (prefix) return prefix_tail + (size_t)NX * panel;
     return panel * ((size_t)seg + 1 + (nseg <= 1 ? 0 : 2 * (size_t)nseg) + 1 + NX);
   };
   char* base = nullptr;
@@ -1262,13 +1282,19 @@ void adjoint_doubling(tbk_ctx* ctx, const HOp& op, uint64_t probe_seed, int s, i
   } catch (const Error& e) {
     // the device could not map the all-stored plan after all: replay segments instead
     if (e.code != TBK_ERR_OOM || nseg > 1 || npan <= 2) throw;
+    prefix = false;
     seg = seg_plan();
     nseg = (npan + seg - 1) / seg;
     base = (char*)scratch(ctx, WS_CHECKPOINTS, plan_bytes());
   }
   const bool all_stored = nseg <= 1;
   const size_t n_seg_pan = (size_t)seg + 1, n_ckpt = all_stored ? 0 : 2 * (size_t)nseg;
-  auto P = [&](size_t i) { return (void*)(base + i * panel); };
+  // P(0 .. npan + 1) of the prefix plan at poff, the full-size panels after them
+  auto P = [&](size_t i) -> void* {
+    if (!prefix) return base + i * panel;
+    if (i <= (size_t)npan + 1) return base + poff[i];
+    return base + prefix_tail + (i - ((size_t)npan + 2)) * panel;
+  };
   auto CK = [&](int sg, int which) { return P(n_seg_pan + 2 * (size_t)sg + which); };
   void* E = P(n_seg_pan + n_ckpt);
   auto YB = [&](int j) { return P(n_seg_pan + n_ckpt + 1 + (size_t)(j % NB)); };

@@ -361,7 +361,7 @@ def run_ours(args, rank, world):
         # pair, reads and writes the FP64 accumulator once per window
         "window": (lambda n: args.steps * (K * 2 * panel + nwin * nnzb * B2 * 16),
                    lambda n: args.steps * K * blk,
-                   "sddmm_window_g" if wk.n_probes >= 256 else "sddmm_window", None, "adjoint.cu"),
+                   "sddmm_window_g", None, "adjoint.cu"),
     }
     kernels = {}
     for f, (tms, nl) in fam.items():
@@ -624,7 +624,7 @@ def run_batched(args, rank, world):
     for f, by, fl, kname in (("step", fb, ff, ("cheb_step_self" if s == 128 else "cheb_step_bulk") + " (batched)"),
                              ("backward", bb, bf, "clenshaw_self (batched)" if windowed
                               else "clenshaw_sddmm_bulk (batched)"),
-                             ("window", wb, wf, "sddmm_window (batched)")):
+                             ("window", wb, wf, "sddmm_window_g (batched)")):
         tms, nl = fam[f]
         if nl == 0:
             continue

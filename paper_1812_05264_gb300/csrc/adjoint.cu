@@ -151,7 +151,7 @@ __device__ __forceinline__ void sddmm_rows3(int g, const float* Y, const float* 
     atomicAdd(Gacc + k * 81 + 27 * g + lane, w * (double)v[0]);
 }
 
-// SD = false: the Clenshaw step alone (the outer products are left to sddmm_window); the own-row
+// SD = false: the Clenshaw step alone (the outer products are left to sddmm_window_g); the own-row
 // tile y_j then streams through the ring like the other source terms.  SD = true: three CTAs of
 // four consumer warps per SM, whose interleaving hides the latency of the outer product's
 // reductions.
@@ -358,13 +358,6 @@ clenshaw_sddmm_bulk(const int n_atoms, const int32_t* __restrict__ row_ptr,
 //
 // Gacc_ab += w sum_{t < nw} sum_probes y_{k_t}[a] ybar_{k_t + 1}[b]^T for every stored block (a, b).
 // Summing nw steps before the cross-lane reduction spreads its cost over nw block products.
-// One CTA task is one block row a: the producer warp stages the nw own-row tiles y_{k_t}[a] (or
-// writes the probe block when y[0] is NULL, nw = 1) and streams the nw neighbour tiles
-// ybar_{k_t+1}[b] of every block through a D-stage ring.  Consumer thread t owns probes
-// 4t .. 4t+3 of all 81 entries, accumulated as (even probe, odd probe) pairs with FFMA2.  Per
-// block, a reduce-scatter over the lanes and a fixed-order sum over the warps (in shared memory)
-// give one total per entry, added to the FP64 accumulator by one thread: the result does not
-// depend on timing.
 
 constexpr int SDW = 4;  // steps per window
 
@@ -373,232 +366,30 @@ struct WindowPanels {
   const float* x[SDW];  // ybar_{k_t + 1} panels
 };
 
-template <int CW>
-struct WinCfg {
-  // tiles in flight: 8 for the large tiles; 3 for 128 probes, so that six CTAs fit per SM
-  static constexpr int D = CW == 1 ? 3 : 8;
-  static constexpr int P = 128 * CW;
-  static constexpr int XB = 9 * P * 4;
-  static constexpr int RED = 2 * CW * 96 * 4;
-  static constexpr int SMEM = (SDW + D) * XB + RED + 8 * (2 * D + 6);
-  static constexpr int THREADS = 32 * (CW + 1);
-};
-
-template <int CW>
-__global__ void __launch_bounds__(32 * (CW + 1), CW == 4 ? 1 : (CW == 2 ? 2 : 6))
-sddmm_window(const int n_atoms, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
-             const WindowPanels wp, const int nw, const uint64_t seed, const int s, const double w,
-             double* __restrict__ Gacc, int* __restrict__ err, const BatchRows batch,
-             const int32_t* __restrict__ kcl, const int k_lo) {
-  using C = WinCfg<CW>;
-  constexpr int D = C::D, P = C::P;
-  extern __shared__ __align__(128) unsigned char smem[];
-  float* Yw = reinterpret_cast<float*>(smem);                       // SDW own-row tiles
-  unsigned char* ring = smem + SDW * C::XB;                          // D neighbour tiles
-  float* red = reinterpret_cast<float*>(smem + (SDW + D) * C::XB);   // [2][CW][96]
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (SDW + D) * C::XB + C::RED);
-  const uint32_t bar0 = smem_u32(bars);
-  auto full = [&](int i) { return bar0 + 8u * i; };
-  auto empty = [&](int i) { return bar0 + 8u * (D + i); };
-  const uint32_t y_full = bar0 + 8u * (2 * D), y_empty = bar0 + 8u * (2 * D + 1);
-  auto red_full = [&](int b) { return bar0 + 8u * (2 * D + 2 + b); };
-  auto red_empty = [&](int b) { return bar0 + 8u * (2 * D + 4 + b); };
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const bool probe = wp.y[0] == nullptr;
-  if (threadIdx.x == 0) {
-    for (int i = 0; i < D; ++i) {
-      mbar_init(full(i), 1);
-      mbar_init(empty(i), CW);
-    }
-    mbar_init(y_full, 1);
-    mbar_init(y_empty, CW);
-    for (int b = 0; b < 2; ++b) {
-      mbar_init(red_full(b), CW);
-      mbar_init(red_empty(b), 1);
-    }
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  __syncthreads();
-  // per atom: the probe stream and cluster-local row, and how many of the window's steps its
-  // cluster takes part in (a batch's cluster with K_c steps has pairs j = 0 .. K_c - 1 only: the
-  // panels of later steps were never formed on its rows)
-  auto atom_window = [&](int a, int& nwa, uint64_t& sd, int64_t& rloc) {
-    nwa = nw;
-    sd = seed;
-    rloc = (int64_t)9 * a;
-    if (batch.atom_cl) {
-      const int cl = __ldg(batch.atom_cl + a);
-      sd = __ldg(batch.seed + cl);
-      rloc = (int64_t)9 * (a - __ldg(batch.atom0 + cl));
-      if (kcl) nwa = min(nw, max(0, __ldg(kcl + cl) - k_lo));
-    }
-  };
-
-  if (warp == CW) {
-    // producer warp: lane 0 issues the copies; in the probe case all lanes write the probe block
-    int it = 0, y_it = 0;
-    bool ok = true;
-    for (int a = blockIdx.x; a < n_atoms && ok; a += gridDim.x) {
-      int nwa;
-      uint64_t sd;
-      int64_t rloc;
-      atom_window(a, nwa, sd, rloc);
-      if (nwa == 0) continue;
-      if (lane == 0) ok = mbar_wait(y_empty, (y_it & 1) ^ 1);
-      ok = __shfl_sync(0xffffffffu, ok, 0);
-      if (!ok) break;
-      if (probe) {
-        for (int e = lane; e < 9 * P; e += 32) {
-          const int i = e / P, pr = e - i * P;
-          Yw[e] = tbk_probe_sign(sd, rloc + i, pr);
-        }
-        __threadfence_block();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(y_full);
-      } else if (lane == 0) {
-        mbar_expect_tx(y_full, nwa * C::XB);
-        for (int t = 0; t < nwa; ++t)
-          bulk_g2s(smem_u32(Yw + t * 9 * P), wp.y[t] + (int64_t)9 * a * s, C::XB, y_full);
-      }
-      ++y_it;
-      if (lane == 0) {
-        const int k0 = __ldg(row_ptr + a), k1 = __ldg(row_ptr + a + 1);
-        for (int q = k0; q < k1 && ok; ++q) {
-          const int b = __ldg(col + q);
-          for (int t = 0; t < nwa && ok; ++t) {
-            const int st = it % D;
-            ok = mbar_wait(empty(st), ((it / D) & 1) ^ 1);
-            if (!ok) break;
-            mbar_expect_tx(full(st), C::XB);
-            bulk_g2s(smem_u32(ring + st * C::XB), wp.x[t] + (int64_t)9 * b * s, C::XB, full(st));
-            ++it;
-          }
-        }
-      }
-      ok = __shfl_sync(0xffffffffu, ok, 0);
-    }
-    if (!ok && lane == 0) {
-      atomicOr(err, 2);
-      for (int j = (it > D ? it - D : 0); j < it; ++j) mbar_wait(full(j % D), (j / D) & 1);
-      if (y_it > 0 && !probe) mbar_wait(y_full, (y_it - 1) & 1);
-    }
-    return;
-  }
-
-  int it = 0, y_it = 0, r_it = 0;
-  bool ok = true;
-  const int pl = 4 * threadIdx.x;
-  for (int a = blockIdx.x; a < n_atoms && ok; a += gridDim.x) {
-    int nwa;
-    uint64_t sd;
-    int64_t rloc;
-    atom_window(a, nwa, sd, rloc);
-    if (nwa == 0) continue;
-    const int k0 = __ldg(row_ptr + a), k1 = __ldg(row_ptr + a + 1);
-    ok = mbar_wait(y_full, y_it & 1);
-    if (!ok) break;
-    for (int q = k0; q < k1 && ok; ++q) {
-      // 128 probes: scalar sums keep the kernel small enough for six CTAs per SM; wider tasks
-      // pair probes in f32x2 sums
-      using Acc = typename std::conditional<CW == 1, float, float2>::type;
-      Acc acc[81];
-#pragma unroll
-      for (int e = 0; e < 81; ++e) acc[e] = Acc{};
-      for (int t = 0; t < nwa; ++t) {
-        const int st = it % D;
-        ok = mbar_wait(full(st), (it / D) & 1);
-        if (!ok) break;
-        const float* X = reinterpret_cast<const float*>(ring + st * C::XB);
-        const float* Y = Yw + t * 9 * P;
-        float4 xv[9];
-#pragma unroll
-        for (int l = 0; l < 9; ++l) xv[l] = *reinterpret_cast<const float4*>(X + l * P + pl);
-#pragma unroll
-        for (int i = 0; i < 9; ++i) {
-          const float4 yv = *reinterpret_cast<const float4*>(Y + i * P + pl);
-#pragma unroll
-          for (int l = 0; l < 9; ++l) {
-            if constexpr (CW == 1) {
-              float t = acc[i * 9 + l];
-              t = fmaf(yv.x, xv[l].x, t); t = fmaf(yv.y, xv[l].y, t);
-              t = fmaf(yv.z, xv[l].z, t); t = fmaf(yv.w, xv[l].w, t);
-              acc[i * 9 + l] = t;
-            } else {
-              acc[i * 9 + l] = __ffma2_rn(make_float2(yv.x, yv.y), make_float2(xv[l].x, xv[l].y), acc[i * 9 + l]);
-              acc[i * 9 + l] = __ffma2_rn(make_float2(yv.z, yv.w), make_float2(xv[l].z, xv[l].w), acc[i * 9 + l]);
-            }
-          }
-        }
-        __syncwarp();
-        if (lane == 0) mbar_arrive(empty(st));
-        ++it;
-      }
-      if (!ok) break;
-      // lanes -> one partial per entry and warp (entries padded to 3 x 32)
-      const int rb = r_it & 1, use = r_it >> 1;
-      float* R = red + rb * CW * 96;
-#pragma unroll
-      for (int blk = 0; blk < 3; ++blk) {
-        float v[32];
-#pragma unroll
-        for (int e = 0; e < 32; ++e) {
-          if constexpr (CW == 1) v[e] = blk * 32 + e < 81 ? acc[blk * 32 + e] : 0.f;
-          else v[e] = blk * 32 + e < 81 ? acc[blk * 32 + e].x + acc[blk * 32 + e].y : 0.f;
-        }
-        butterfly32(v, lane);
-        if (blk == 0 && use > 0) ok = mbar_wait(red_empty(rb), (use - 1) & 1);
-        R[warp * 96 + blk * 32 + lane] = v[0];
-      }
-      if (!ok) break;
-      __syncwarp();
-      if (lane == 0) mbar_arrive(red_full(rb));
-      if (warp == 0) {
-        // fixed-order sum over the warps, one writer per entry
-        ok = mbar_wait(red_full(rb), use & 1);
-        if (!ok) break;
-        for (int e = lane; e < 81; e += 32) {
-          float tsum = R[e];
-#pragma unroll
-          for (int v = 1; v < CW; ++v) tsum += R[v * 96 + e];
-          atomicAdd(Gacc + (int64_t)q * 81 + e, w * (double)tsum);
-        }
-        __syncwarp();
-        if (lane == 0) mbar_arrive(red_empty(rb));
-      }
-      ++r_it;
-    }
-    if (!ok) break;
-    __syncwarp();
-    if (lane == 0) mbar_arrive(y_empty);
-    ++y_it;
-  }
-  if (!ok) atomicOr(err, 2);
-}
-
-// ---- outer products of a window for 256 or 512 probes ------------------------------------------
-//
-// The same sums as sddmm_window with the work split so that a lane keeps 27 accumulators instead
-// of 81 probe pairs: consumer warp (g, c) takes rows 3g .. 3g+2 of the block (27 entries) over
-// probe chunk c (128 probes, 4 per lane), for g < 3 and c < NC = P / 128.  The producer warp
-// stages the window's own-row tiles once per block row and streams the neighbour tiles through a
-// D-stage ring read by all 3 NC warps.  Per block, each warp reduces its 27 sums over the lanes
-// (one butterfly for all the window's steps) and warp (g, 0) adds the NC chunk partials in a
-// fixed order and writes the 27 totals to the FP64 accumulator: one writer per entry, so the
-// result does not depend on timing.
+// One CTA task is one block row a.  Consumer warp (g, c) takes rows 3g .. 3g+2 of the block (27
+// entries, one scalar sum each per lane) over probe chunk c (128 probes, 4 per lane), for g < 3
+// and c < NC = P / 128.  The producer warp stages the window's own-row tiles y_{k_t}[a] once per
+// block row (or writes the probe block when y[0] is NULL, nw = 1) and streams the neighbour tiles
+// ybar_{k_t+1}[b] of every block through a D-stage ring read by all 3 NC warps.  Per block, each
+// warp reduces its 27 sums over the lanes (one butterfly for all the window's steps) and warp
+// (g, 0) adds the NC chunk partials in a fixed order and writes the 27 totals to the FP64
+// accumulator: one writer per entry, so the result does not depend on timing.  (One warp holding
+// all 81 entries, the earlier form, kept 6 consumer warps per SM at 128 probes: 2.80 ms per window
+// on the 64-cluster batch against 2.02 ms.)
 template <int NC>
 struct WinGCfg {
   static constexpr int P = 128 * NC;
   static constexpr int NWARP = 3 * NC;  // consumer warps
   static constexpr int THREADS = 32 * (NWARP + 1);
   static constexpr int XB = 9 * P * 4;
-  static constexpr int D = NC == 4 ? 6 : 8;
+  static constexpr int D = NC == 4 ? 6 : (NC == 1 ? 4 : 8);
   static constexpr int RED = 2 * 3 * NC * 32 * 4;  // [2 buffers][3 groups][NC chunks][32 lanes]
   static constexpr int NBAR = 2 * D + 2 + 12;
   static constexpr int SMEM = (SDW + D) * XB + RED + 8 * NBAR;
 };
 
 template <int NC>
-__global__ void __launch_bounds__(32 * (3 * NC + 1), 1)
+__global__ void __launch_bounds__(32 * (3 * NC + 1), NC == 1 ? 5 : 1)
 sddmm_window_g(const int n_atoms, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
                const WindowPanels wp, const int nw, const uint64_t seed, const int s, const double w,
                double* __restrict__ Gacc, int* __restrict__ err, const BatchRows batch,
@@ -1129,24 +920,6 @@ void launch_forces(tbk_ctx* ctx, const DevModel& M, const double* pos, int n_ato
   post_launch(ctx, "gather_forces");
 }
 
-template <int CW>
-static void launch_window_cw(tbk_ctx* ctx, const HOp& op, const WindowPanels& wp, int nw, uint64_t seed,
-                             int s, double w, double* Gacc, int* err, const BatchRows& batch,
-                             const int32_t* kcl, int k_lo) {
-  using C = WinCfg<CW>;
-  TBK_CUDA(cudaFuncSetAttribute(sddmm_window<CW>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
-  int occ = 0;
-  TBK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, sddmm_window<CW>, C::THREADS, C::SMEM));
-  TBK_CHECK_ARG(occ > 0, "windowed outer-product kernel does not fit on this device");
-  const int G = std::max(1, std::min(op.n_atoms, occ * ctx->num_sms));
-  sddmm_window<CW><<<G, C::THREADS, C::SMEM, ctx->stream>>>(op.n_atoms, op.row_ptr, op.col, wp, nw, seed,
-                                                             s, w, Gacc, err, batch, kcl, k_lo);
-  post_launch(ctx, "sddmm_window");
-}
-
-// Gacc_ab += w sum_t sum_probes y_t[a] x_t[b]^T over the stored blocks, 1 <= nw <= SDW steps
-// (t = 0 is step k_lo).  Batch: per-cluster probe streams, and with kcl (K per cluster) each
-// cluster's steps >= K_c are left out.
 template <int NC>
 static void launch_window_g(tbk_ctx* ctx, const HOp& op, const WindowPanels& wp, int nw, uint64_t seed,
                             int s, double w, double* Gacc, int* err, const BatchRows& batch,
@@ -1168,7 +941,7 @@ void launch_window(tbk_ctx* ctx, const HOp& op, const WindowPanels& wp, int nw, 
   TBK_CHECK_ARG(nw >= 1 && nw <= SDW && (wp.y[0] != nullptr || nw == 1), "bad outer-product window");
   if (s == 512) launch_window_g<4>(ctx, op, wp, nw, seed, s, w, Gacc, err, batch, kcl, k_lo);
   else if (s == 256) launch_window_g<2>(ctx, op, wp, nw, seed, s, w, Gacc, err, batch, kcl, k_lo);
-  else launch_window_cw<1>(ctx, op, wp, nw, seed, s, w, Gacc, err, batch, kcl, k_lo);
+  else launch_window_g<1>(ctx, op, wp, nw, seed, s, w, Gacc, err, batch, kcl, k_lo);
 }
 
 // ---- adjoint of the doubled moments (TMA-fed fused path) ------------------------------------

@@ -723,7 +723,9 @@ clenshaw_self(const int n_atoms, const int32_t* __restrict__ row_ptr, const int3
   }
 }
 
-constexpr int CLEN_SELF_R = 3;
+// two stages: ~21 warps per SM instead of 14 (shared memory sets the limit); measured 11 % faster
+// on the batch than three stages
+constexpr int CLEN_SELF_R = 2;
 
 // tr[k] = index of block (b, a) for block k = (a, b) (the pattern is symmetric).
 __global__ void transpose_map(int n_atoms, const int32_t* __restrict__ row_ptr,

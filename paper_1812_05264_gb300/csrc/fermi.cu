@@ -46,20 +46,29 @@ __device__ __forceinline__ double damp_factor(int k, int p, int damping) {
   return ((p - k + 1) * cos(q * k) + sin(q * k) / tan(q)) / (p + 1);
 }
 
+// h_j = h(e_j) at the M quadrature nodes, once (the coefficient blocks all read them).
+__global__ void node_values(int fn, int M, double emin, double emax, double mu, double kT,
+                            double* __restrict__ hv) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= M) return;
+  const double e = node_energy(j, M, emin, emax);
+  double h;
+  if (fn == TBK_FN_FREE) h = free_fn(e, mu, kT);
+  else {
+    h = fermi_fn(e, mu, kT);
+    if (fn == TBK_FN_ENERGY) h *= e;
+  }
+  hv[j] = h;
+}
+
 // One block per coefficient k.
-__global__ void coeff_kernel(int fn, int p, int M, double emin, double emax, double mu, double kT,
-                             int damping, const double* __restrict__ tab, double* __restrict__ out) {
+__global__ void coeff_kernel(int p, int M, int damping, const double* __restrict__ tab,
+                             const double* __restrict__ hv, double* __restrict__ out) {
   __shared__ double red[32];
   const int k = blockIdx.x;
   double s = 0.0, c = 0.0;
   for (int j = threadIdx.x; j < M; j += blockDim.x) {
-    const double e = node_energy(j, M, emin, emax);
-    double h;
-    if (fn == TBK_FN_FREE) h = free_fn(e, mu, kT);
-    else {
-      h = fermi_fn(e, mu, kT);
-      if (fn == TBK_FN_ENERGY) h *= e;
-    }
+    const double h = hv[j];
     const int64_t m = ((int64_t)k * (2 * j + 1)) % (4 * (int64_t)M);
     const double y = h * tab[m] - c, t = s + y;
     c = (t - s) - y;
@@ -181,8 +190,9 @@ void fermi_enqueue_batched(tbk_ctx* ctx, int n, const FermiJob* d_jobs, int M_ma
   post_launch(ctx, "fermi_batched");
 }
 
-const double* make_cos_table(tbk_ctx* ctx, int M) {
-  double* tab = (double*)scratch(ctx, WS_NODES, sizeof(double) * 4 * (size_t)M);
+// cos table of 4M doubles in WS_NODES, followed by `extra` doubles of room for the caller.
+const double* make_cos_table(tbk_ctx* ctx, int M, size_t extra = 0) {
+  double* tab = (double*)scratch(ctx, WS_NODES, sizeof(double) * (4 * (size_t)M + extra));
   cos_table<<<ceil_div(4 * (int64_t)M, 256), 256, 0, ctx->stream>>>(M, tab);
   post_launch(ctx, "cos_table");
   return tab;
@@ -196,8 +206,11 @@ void coefficients(tbk_ctx* ctx, int fn, int p, double emin, double emax, double 
   TBK_CHECK_ARG(kT > 0.0 && std::isfinite(kT), "kT must be positive");
   TBK_CHECK_ARG(emax > emin, "need emax > emin");
   const int M = quad_nodes(p);
-  const double* tab = make_cos_table(ctx, M);
-  coeff_kernel<<<p, 256, 0, ctx->stream>>>(fn, p, M, emin, emax, mu, kT, damping, tab, out);
+  const double* tab = make_cos_table(ctx, M, (size_t)M);
+  double* hv = const_cast<double*>(tab) + 4 * (size_t)M;
+  node_values<<<ceil_div(M, 256), 256, 0, ctx->stream>>>(fn, M, emin, emax, mu, kT, hv);
+  post_launch(ctx, "node_values");
+  coeff_kernel<<<p, 256, 0, ctx->stream>>>(p, M, damping, tab, hv, out);
   post_launch(ctx, "coeff_kernel");
 }
 

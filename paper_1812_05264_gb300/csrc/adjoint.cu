@@ -389,7 +389,7 @@ struct WinGCfg {
 };
 
 template <int NC>
-__global__ void __launch_bounds__(32 * (3 * NC + 1), NC == 1 ? 5 : 1)
+__global__ void __launch_bounds__(32 * (3 * NC + 1), NC == 1 ? 6 : 1)
 sddmm_window_g(const int n_atoms, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
                const WindowPanels wp, const int nw, const uint64_t seed, const int s, const double w,
                double* __restrict__ Gacc, int* __restrict__ err, const BatchRows batch,

@@ -389,7 +389,7 @@ struct WinGCfg {
 };
 
 template <int NC>
-__global__ void __launch_bounds__(32 * (3 * NC + 1), NC == 1 ? 6 : 1)
+__global__ void __launch_bounds__(32 * (3 * NC + 1), NC == 1 ? 5 : 1)
 sddmm_window_g(const int n_atoms, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
                const WindowPanels wp, const int nw, const uint64_t seed, const int s, const double w,
                double* __restrict__ Gacc, int* __restrict__ err, const BatchRows batch,
@@ -504,11 +504,11 @@ sddmm_window_g(const int n_atoms, const int32_t* __restrict__ row_ptr, const int
       float acc[27];
 #pragma unroll
       for (int e = 0; e < 27; ++e) acc[e] = 0.f;
-      for (int t = 0; t < nwa; ++t) {
+      auto tile = [&](int t) {  // step t of the window for this block; false: a wait expired
         const int st = it % D;
         ok = mbar_wait(full(st), (it / D) & 1);
         ok = __all_sync(0xffffffffu, ok);
-        if (!ok) break;
+        if (!ok) return false;
         const float* X = reinterpret_cast<const float*>(ring + st * C::XB);
         const float* Y = Yw + t * 9 * P + 3 * g * P;
         float4 yv[3];
@@ -528,6 +528,15 @@ sddmm_window_g(const int n_atoms, const int32_t* __restrict__ row_ptr, const int
         __syncwarp();
         if (lane == 0) mbar_arrive(empty(st));
         ++it;
+        return true;
+      };
+      if (nwa == SDW) {  // a full window: the step loop unrolled
+#pragma unroll
+        for (int t = 0; t < SDW; ++t)
+          if (!tile(t)) break;
+      } else {
+        for (int t = 0; t < nwa; ++t)
+          if (!tile(t)) break;
       }
       if (!ok) break;
       // lanes -> lane e holds this chunk's sum of entry 27 g + e

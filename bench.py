@@ -44,6 +44,23 @@ METRIC = "atom*vector*Chebyshev-steps/s"
 UNIT = "atom*vector*steps/s"
 
 
+def replica_times(*times_ms: float, device: str = "cpu") -> list:
+    """Max over the ranks of each time: N replicas of the step make one job that lasts as long as
+    its slowest rank.  One process: the local values."""
+    import torch
+    import torch.distributed as td
+    if not (td.is_available() and td.is_initialized()) or td.get_world_size() == 1:
+        return list(times_ms)
+    t = torch.tensor(list(times_ms), dtype=torch.float64, device=device)
+    td.all_reduce(t, op=td.ReduceOp.MAX)
+    return t.tolist()
+
+
+def job_rate(units_per_rank: float, world: int, ms: float) -> float:
+    """Whole-job throughput: the units of every rank over the slowest rank's time per step."""
+    return units_per_rank * world / (ms / 1e3)
+
+
 def make_workload(name: str, rank: int = 0, atom_order: str = "radial", probes: int | None = None):
     if name == "fcc10k":
         return wl.fcc_cu(10000, kT=0.025, n_probes=probes or 512, seed=5264, probe_seed=52640 + rank,
@@ -318,14 +335,9 @@ def run_ours(args, rank, world):
         d2h = (out.numel() * 8 if out is not None else 0) + 4 * 8
         e_ms.append(s0.elapsed_time(s1))
     clk = clocks.stop()
-    if dist:
-        tt = torch.tensor([ms, statistics.median(e_ms)], dtype=torch.float64, device=f"cuda:{local}")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        ms, e_med = tt.tolist()
-    else:
-        e_med = statistics.median(e_ms)
+    ms, e_med = replica_times(ms, statistics.median(e_ms), device=f"cuda:{local}")
     units = wk.n_atoms * wk.n_probes * p
-    value = units * world / (ms / 1e3)
+    value = job_rate(units, world, ms)
     # roofline of the dominant kernel from its own launches inside the timed steps
     n_rows = wk.n_atoms * wk.n_orb
     panel = n_rows * wk.n_probes * esz
@@ -402,7 +414,7 @@ def run_ours(args, rank, world):
                    "adjoint": ("windowed" if windowed else "fused") + (" (tuned)" if args.adjoint == "auto" else ""),
                    "autotune": None if tuned is None else {"probes_per_task": tuned[0], "windowed": tuned[1]},
                    "order_rule": "fixed by --order (profiling run)" if args.order else "exp(-6.4 p kT/W) = 1e-7"},
-        "e2e": {"value": units * world / (e_med / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+        "e2e": {"value": job_rate(units, world, e_med), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "roofline": roof,
@@ -534,6 +546,11 @@ def run_batched(args, rank, world):
     if dist:
         import torch.distributed as td
         td.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+
+    def barrier():
+        if dist:
+            torch.distributed.barrier()
+
     spec = wl.batched_clusters(64, 100, 5000, (0.025, 0.1, 0.5), seed=6464 + rank)
     s = 128
     wks = []
@@ -575,16 +592,19 @@ def run_batched(args, rank, world):
     for _ in range(args.warmup):
         step(devs)
     torch.cuda.synchronize()
+    barrier()
     clocks = ClockSampler(local, enabled=not args.no_clocks)
     clocks.start()
     l0 = ctx.launches
     ctx.time_kernels("step", "backward", "window")
     t0 = torch.cuda.Event(enable_timing=True); t1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
     t0.record(ctx.stream)
     for _ in range(args.steps):
         ps, obs, Fs = step(devs, record=True)
     t1.record(ctx.stream)
     torch.cuda.synchronize()
+    barrier()
     launches = ctx.launches - l0
     fam = {f: ctx.kernel_time(f) for f in ("step", "backward", "window")}
     ctx.time_kernels()
@@ -601,6 +621,7 @@ def run_batched(args, rank, world):
         e_ms.append(a.elapsed_time(b))
     clk = clocks.stop()
     units = sum(w.n_atoms * s * p for w, p in zip(wks, ps))
+    ms, e_med = replica_times(ms, statistics.median(e_ms), device=f"cuda:{local}")
     # rooflines of the two kernel families from their own launches in the timed steps: cluster c
     # takes part in K_c = p_c/2 recurrence steps and K_c adjoint steps
     _, Hs, ps_ = phase_ev[-1]
@@ -642,7 +663,7 @@ def run_batched(args, rank, world):
     dom = max(kernels, key=lambda f: kernels[f]["share_of_step"])
     h2d = sum(h.numel() * 8 for h in hosts)
     d2h = sum(w.n_atoms * 3 * 8 for w in wks)
-    line = {"metric": METRIC, "value": units * world / (ms / 1e3), "unit": UNIT, "n_gpus": world,
+    line = {"metric": METRIC, "value": job_rate(units, world, ms), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "batched64-fcc-sk9", "clusters": len(wks),
@@ -650,7 +671,7 @@ def run_batched(args, rank, world):
                        "orders_p": [int(p) for p in ps], "kT": [float(w.kT) for w in wks],
                        "l2": "merged panels (%.0f MB each) larger than L2" % (sum(w.n_atoms for w in wks) * 9 * s * 4 / 1e6),
                        "parallelism": f"replicas x{world}", "adjoint": args.adjoint},
-            "e2e": {"value": units * world / (statistics.median(e_ms) / 1e3), "unit": UNIT,
+            "e2e": {"value": job_rate(units, world, e_med), "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches,
             "roofline": dict(kernels[dom]),

@@ -518,14 +518,16 @@ def test_row_without_its_diagonal_block_is_rejected(api, ctx):
     assert torch.equal(m0, m1)
 
 
-def test_bounded_wait_reports_timeout_and_context_recovers(api, ctx):
-    """A recurrence step whose producer copies nothing: the consumers' waits give up after their
-    wall-time limit, the call returns TBK_ERR_TIMEOUT, nothing faults, and the same context then
-    computes the same moments as before."""
+@pytest.mark.parametrize("s", [128, 512])
+def test_bounded_wait_reports_timeout_and_context_recovers(api, ctx, s):
+    """A recurrence step whose producer copies nothing (the self-fed single-warp kernel at 128
+    probes, the producer-warp kernel with four consumer warps at 512): the consumers' waits give
+    up after their wall-time limit, the call returns TBK_ERR_TIMEOUT, nothing faults, and the same
+    context then computes the same moments as before."""
     from paper_1812_05264_gb300 import _lib as L
-    wk = small_fcc(40, n_probes=128)
+    wk = small_fcc(40, n_probes=s)
     sv, pos, res = _gpu_run(api, ctx, wk, 30, fp64=False)
-    args = (ctx, res.H, res.emin, res.emax, wk.probe_seed, 128, 30, False)
+    args = (ctx, res.H, res.emin, res.emax, wk.probe_seed, s, 30, False)
     m0 = api.chebyshev_moments(*args)
     L.call("tbk_test_stall_next_step", ctx.handle)
     with pytest.raises(L.TbkError) as e:

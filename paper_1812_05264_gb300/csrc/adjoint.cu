@@ -502,9 +502,8 @@ sddmm_window_g(const int n_atoms, const int32_t* __restrict__ row_ptr, const int
     if (!ok) break;
     for (int q = k0; q < k1; ++q) {
       float acc[27];
-#pragma unroll
-      for (int e = 0; e < 27; ++e) acc[e] = 0.f;
-      auto tile = [&](int t) {  // step t of the window for this block; false: a wait expired
+      // step t of the window for this block (first: the sums start here); false: a wait expired
+      auto tile = [&](int t, auto first) {
         const int st = it % D;
         ok = mbar_wait(full(st), (it / D) & 1);
         ok = __all_sync(0xffffffffu, ok);
@@ -519,8 +518,8 @@ sddmm_window_g(const int n_atoms, const int32_t* __restrict__ row_ptr, const int
           const float4 xv = *reinterpret_cast<const float4*>(X + l * P + pl);
 #pragma unroll
           for (int i = 0; i < 3; ++i) {
-            float u = acc[i * 9 + l];
-            u = fmaf(yv[i].x, xv.x, u); u = fmaf(yv[i].y, xv.y, u);
+            float u = decltype(first)::value ? yv[i].x * xv.x : fmaf(yv[i].x, xv.x, acc[i * 9 + l]);
+            u = fmaf(yv[i].y, xv.y, u);
             u = fmaf(yv[i].z, xv.z, u); u = fmaf(yv[i].w, xv.w, u);
             acc[i * 9 + l] = u;
           }
@@ -531,12 +530,16 @@ sddmm_window_g(const int n_atoms, const int32_t* __restrict__ row_ptr, const int
         return true;
       };
       if (nwa == SDW) {  // a full window: the step loop unrolled
+        if (tile(0, std::true_type())) {
 #pragma unroll
-        for (int t = 0; t < SDW; ++t)
-          if (!tile(t)) break;
+          for (int t = 1; t < SDW; ++t)
+            if (!tile(t, std::false_type())) break;
+        }
       } else {
+#pragma unroll
+        for (int e = 0; e < 27; ++e) acc[e] = 0.f;
         for (int t = 0; t < nwa; ++t)
-          if (!tile(t)) break;
+          if (!tile(t, std::false_type())) break;
       }
       if (!ok) break;
       // lanes -> lane e holds this chunk's sum of entry 27 g + e
@@ -544,6 +547,11 @@ sddmm_window_g(const int n_atoms, const int32_t* __restrict__ row_ptr, const int
 #pragma unroll
       for (int e = 0; e < 32; ++e) v[e] = e < 27 ? acc[e] : 0.f;
       butterfly32(v, lane);
+      if constexpr (NC == 1) {
+        // one chunk: this warp alone holds the totals of its 27 entries (one writer per entry)
+        if (lane < 27) atomicAdd(Gacc + (int64_t)q * 81 + 27 * g + lane, w * (double)v[0]);
+        continue;
+      }
       const int rb = r_it & 1, use = r_it >> 1;
       if (use > 0) {
         ok = mbar_wait(red_empty(rb, g), (use - 1) & 1);

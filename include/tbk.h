@@ -303,7 +303,10 @@ int tbk_batched_fermi_level(tbk_ctx* ctx, int32_t n_clusters, const double* mome
    (device pointers, n_atoms x 3 each; open clusters), emin, emax, seeds, orders, mu, kT, G and
    forces (device pointers or NULL entries; either array may be NULL).  n_probes 128, 256 or 512
    for the one-launch path; other shapes run the clusters one after another.  flags: 0 (mixed),
-   optionally TBK_WINDOWED.  Synchronises the stream. */
+   optionally TBK_WINDOWED.  max_panel_bytes as in tbk_density_and_forces: the one-launch path
+   keeps every panel y_j when they fit, each stored with only the rows of the clusters still
+   running at step j - 1, else it replays full-size panels from checkpoints.  Synchronises the
+   stream. */
 int tbk_batched_density_and_forces(tbk_ctx* ctx, int32_t n_clusters, const tbk_bsr* H,
                                    const tbk_model* model, const double* const* pos,
                                    const double* emin, const double* emax, const uint64_t* seeds,

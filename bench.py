@@ -572,8 +572,8 @@ def run_batched(args, rank, world):
     def step(pos, record=False):
         Hs, e0, e1, ps = [], [], [], []
         marks = [ev()] if record else None
-        for w, p_ in zip(wks, pos):
-            g = api.build_neighbors(ctx, p_, w.cutoff)
+        graphs = api.batched_build_neighbors(ctx, pos, wks[0].cutoff)
+        for p_, g in zip(pos, graphs):
             Hs.append(api.assemble_H(ctx, model, p_, g))
         e0, e1 = api.batched_spectral_bounds(ctx, Hs)
         ps = [order_rule(hi - lo, w.kT) for w, lo, hi in zip(wks, e0, e1)]

@@ -162,6 +162,18 @@ int tbk_build_neighbors(tbk_ctx* ctx, const double* pos, int32_t n_atoms, const 
                         double cutoff, int32_t* row_ptr, int32_t* col, int64_t col_capacity,
                         int64_t* nnzb);
 
+/* tbk_batched_build_neighbors: tbk_build_neighbors for n_clusters open clusters in one call,
+   with every pass run once over the atoms of all clusters; the same patterns, bit for bit.
+   Host arrays: pos (device pointers, n_atoms[c] x 3 FP64 each), n_atoms (each >= 1), row_ptr
+   (device pointers, n_atoms[c] + 1 int32 each, always written), col (device pointers with
+   col_capacity[c] int32 each; the array may be NULL to count only), nnzb (out, pairs per
+   cluster).  If a col entry is NULL or smaller than its cluster's pairs, the call fails with
+   TBK_ERR_ARG after writing nnzb and row_ptr, and no col is touched.  Synchronises the stream
+   twice. */
+int tbk_batched_build_neighbors(tbk_ctx* ctx, int32_t n_clusters, const double* const* pos,
+                                const int32_t* n_atoms, double cutoff, int32_t* const* row_ptr,
+                                int32_t* const* col, const int64_t* col_capacity, int64_t* nnzb);
+
 /* ---- a2: Hamiltonian assembly (Sec. II.A, Slater-Koster form of the NRL model) --------- */
 
 /* Fill H (device, nnzb * n_orb^2 FP64) for the pattern (row_ptr, col) of n_atoms atoms at pos

@@ -159,6 +159,35 @@ def build_neighbors(ctx: Context, pos: torch.Tensor, cutoff: float, box=None) ->
     return Graph(n, nnz.value, row_ptr, col[:nnz.value])
 
 
+def batched_build_neighbors(ctx: Context, positions: list, cutoff: float) -> list:
+    """a1 for many open clusters in one call: the patterns of build_neighbors, cluster by
+    cluster, with every pass run once over all the clusters' atoms."""
+    n = len(positions)
+    for p in positions:
+        assert p.is_cuda and p.dtype == torch.float64 and p.is_contiguous() and p.shape[0] >= 1
+    dev = positions[0].device
+    rps = [torch.empty(p.shape[0] + 1, dtype=torch.int32, device=dev) for p in positions]
+    pos_p = (C.c_void_p * n)(*[p.data_ptr() for p in positions])
+    n_at = (C.c_int32 * n)(*[p.shape[0] for p in positions])
+    rp_p = (C.c_void_p * n)(*[r.data_ptr() for r in rps])
+    nnz = (C.c_int64 * n)()
+    # a first capacity that holds every short-cutoff pattern in practice; the call reports the
+    # exact counts, and a cluster that does not fit is built again with them
+    cols = [torch.empty(32 * p.shape[0], dtype=torch.int32, device=dev) for p in positions]
+    for attempt in range(2):
+        col_p = (C.c_void_p * n)(*[c.data_ptr() for c in cols])
+        cap = (C.c_int64 * n)(*[c.numel() for c in cols])
+        try:
+            L.call("tbk_batched_build_neighbors", ctx.handle, n, pos_p, n_at, float(cutoff), rp_p, col_p,
+                   cap, nnz)
+            break
+        except L.TbkError as e:
+            if attempt or e.code != L.TBK_ERR_ARG or all(nnz[i] <= cols[i].numel() for i in range(n)):
+                raise
+            cols = [torch.empty(max(1, nnz[i]), dtype=torch.int32, device=dev) for i in range(n)]
+    return [Graph(positions[i].shape[0], nnz[i], rps[i], cols[i][:nnz[i]]) for i in range(n)]
+
+
 def assemble_H(ctx: Context, model: Model, pos: torch.Tensor, graph: Graph, box=None) -> BSR:
     """a2: BSR values of H on the neighbour pattern."""
     b = model.s.n_orb

@@ -214,3 +214,36 @@ def test_batched_windowed_outer_products_match_fused(api, ctx):
                                                    kTs, want_G=True, windowed=True, max_panel_bytes=30 * panel)
     for g2, g3, f2, f3 in zip(G2, G3, F2, F3):
         assert torch.equal(g2, g3) and torch.equal(f2, f3)
+
+
+def test_batched_neighbor_lists_equal_single_cluster_lists(api, ctx):
+    """One call for many open clusters of different sizes (one atom, a pair, jittered fcc
+    spheres): every cluster's pattern equals its own tbk_build_neighbors call bit for bit, and a
+    col capacity that is too small is reported and then met."""
+    import workloads as wl
+    sizes = [1, 2, 37, 500, 13, 1200]
+    pos = []
+    for i, n in enumerate(sizes):
+        p = wl.fcc_sphere(n, jitter=0.05, seed=40 + i) if n > 2 else np.array([[0.0, 0.0, 0.0], [2.0, 0.5, 0.0]])[:n]
+        pos.append(torch.as_tensor(np.ascontiguousarray(p), dtype=torch.float64, device="cuda"))
+    cutoff = wl.SK_CUTOFF
+    gs = api.batched_build_neighbors(ctx, pos, cutoff)
+    for p, g in zip(pos, gs):
+        ref = api.build_neighbors(ctx, p, cutoff)
+        assert g.n_atoms == ref.n_atoms and g.nnzb == ref.nnzb
+        assert torch.equal(g.row_ptr, ref.row_ptr) and torch.equal(g.col, ref.col)
+    # exact counts: col arrays one entry short make the call fail without touching them
+    from paper_1812_05264_gb300 import _lib as L
+    import ctypes as C
+    n = len(pos)
+    rps = [torch.empty(p.shape[0] + 1, dtype=torch.int32, device="cuda") for p in pos]
+    cols = [torch.full((max(1, g.nnzb - 1),), -7, dtype=torch.int32, device="cuda") for g in gs]
+    nnz = (C.c_int64 * n)()
+    with pytest.raises(L.TbkError) as e:
+        L.call("tbk_batched_build_neighbors", ctx.handle, n, (C.c_void_p * n)(*[p.data_ptr() for p in pos]),
+               (C.c_int32 * n)(*[p.shape[0] for p in pos]), float(cutoff),
+               (C.c_void_p * n)(*[r.data_ptr() for r in rps]), (C.c_void_p * n)(*[c.data_ptr() for c in cols]),
+               (C.c_int64 * n)(*[c.numel() for c in cols]), nnz)
+    assert e.value.code == L.TBK_ERR_ARG
+    assert [nnz[i] for i in range(n)] == [g.nnzb for g in gs]
+    assert all(bool((c == -7).all()) for c in cols)

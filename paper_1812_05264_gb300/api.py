@@ -151,11 +151,18 @@ def build_neighbors(ctx: Context, pos: torch.Tensor, cutoff: float, box=None) ->
     row_ptr = torch.empty(n + 1, dtype=torch.int32, device=pos.device)
     nnz = C.c_int64()
     _keep, bx = _box_arg(box)
-    L.call("tbk_build_neighbors", ctx.handle, _ptr(pos), n, bx, float(cutoff), _ptr(row_ptr), None,
-           0, C.byref(nnz))
-    col = torch.empty(max(1, nnz.value), dtype=torch.int32, device=pos.device)
-    L.call("tbk_build_neighbors", ctx.handle, _ptr(pos), n, bx, float(cutoff), _ptr(row_ptr),
-           _ptr(col), col.numel(), C.byref(nnz))
+    # a first capacity that holds every short-cutoff pattern in practice; the call reports the
+    # exact count, and a pattern that does not fit is built again with it
+    col = torch.empty(max(1, 32 * n), dtype=torch.int32, device=pos.device)
+    try:
+        L.call("tbk_build_neighbors", ctx.handle, _ptr(pos), n, bx, float(cutoff), _ptr(row_ptr),
+               _ptr(col), col.numel(), C.byref(nnz))
+    except L.TbkError as e:
+        if e.code != L.TBK_ERR_ARG or nnz.value <= col.numel():
+            raise
+        col = torch.empty(nnz.value, dtype=torch.int32, device=pos.device)
+        L.call("tbk_build_neighbors", ctx.handle, _ptr(pos), n, bx, float(cutoff), _ptr(row_ptr),
+               _ptr(col), col.numel(), C.byref(nnz))
     return Graph(n, nnz.value, row_ptr, col[:nnz.value])
 
 

@@ -37,11 +37,14 @@ def _dev(x):
 
 # ---- a1 neighbour list: bit-exact ---------------------------------------------------------
 
-@pytest.mark.parametrize("case", ["fcc1000", "fcc_jitter", "sc_open", "sc_periodic", "edge"])
+@pytest.mark.parametrize("case", ["fcc1000", "fcc_jitter", "sc_open", "sc_periodic", "edge", "dense"])
 def test_neighbors_bit_exact(api, ctx, case):
     box = None
     if case == "fcc1000":
         pos, rc = wl.fcc_sphere(1000), 4.0
+    elif case == "dense":
+        # more pairs per atom than the binding's first column capacity: counted, then rebuilt
+        pos, rc = wl.fcc_sphere(60, jitter=0.05, seed=9), 12.0
     elif case == "fcc_jitter":
         pos, rc = wl.fcc_sphere(700, jitter=0.05, seed=3), 4.0
     elif case == "sc_open":

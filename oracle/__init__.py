@@ -23,6 +23,9 @@ Modules (each function cites the part of arXiv 1812.05264 it follows):
 * ``coloring``   -- Welsh-Powell colouring of the atom graph (Sec. III) and the multi-colour
   probe ensemble (Sec. II.C.3): coloured probes, the estimator's exact moments and gradient,
   its sampling error.
+* ``direct``     -- direct random estimates M o P~ and M o Q~ of the density and
+  energy-density matrices (Eq. poly_PQ, Eq. random_density) and their element-wise
+  sampling error.
 
 Parity status: every public function is pinned by a ``-m "not gpu"`` test against closed
 forms, invariants or brute force (see ``tests/test_oracle_*.py``).

@@ -26,6 +26,8 @@ Modules (each function cites the part of arXiv 1812.05264 it follows):
 * ``direct``     -- direct random estimates M o P~ and M o Q~ of the density and
   energy-density matrices (Eq. poly_PQ, Eq. random_density) and their element-wise
   sampling error.
+* ``local``      -- local approximation of M o P and M o Q (Sec. II.C.1, Eq. local_density):
+  one dense local problem per atom within the localization radius.
 
 Parity status: every public function is pinned by a ``-m "not gpu"`` test against closed
 forms, invariants or brute force (see ``tests/test_oracle_*.py``).

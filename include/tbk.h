@@ -174,6 +174,21 @@ int tbk_batched_build_neighbors(tbk_ctx* ctx, int32_t n_clusters, const double* 
                                 const int32_t* n_atoms, double cutoff, int32_t* const* row_ptr,
                                 int32_t* const* col, const int64_t* col_capacity, int64_t* nnzb);
 
+/* Welsh-Powell colouring of the atoms (Sec. III), for the multi-colour probe ensemble of
+   Sec. II.C.3: the vertices are listed by non-increasing degree (equal degrees in index order),
+   and each takes the smallest colour that none of its earlier-listed neighbours has.  This is
+   the same colouring as building one colour class at a time down the list.  Two atoms of one
+   colour are never neighbours in the graph.  Pass the pattern tbk_build_neighbors returns at
+   the colouring radius (copied to the host), so that atoms of one colour are farther apart
+   than that radius.  Host only: no context, no device memory, no stream.
+   row_ptr: host, n_atoms + 1 int32, non-decreasing from 0.  col: host, row_ptr[n_atoms] int32
+   in [0, n_atoms), strictly ascending within a row; self entries are ignored, and a pair must
+   appear in both rows.  color: host, n_atoms int32, receives 0 .. *n_colors - 1.  *n_colors
+   (host) receives the number of colours.  Bad sizes or indices, unsorted rows or a pair listed
+   in one row only give TBK_ERR_ARG with color untouched.  O(n_atoms + nnz). */
+int tbk_welsh_powell(int32_t n_atoms, const int32_t* row_ptr, const int32_t* col, int32_t* color,
+                     int32_t* n_colors);
+
 /* ---- a2: Hamiltonian assembly (Sec. II.A, Slater-Koster form of the NRL model) --------- */
 
 /* Fill H (device, nnzb * n_orb^2 FP64) for the pattern (row_ptr, col) of n_atoms atoms at pos

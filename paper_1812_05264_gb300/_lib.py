@@ -78,6 +78,7 @@ SIGNATURES = {
     "tbk_build_neighbors": [_P, _P, _I, _P, _D, _P, _P, _L, C.POINTER(_L)],
     "tbk_batched_build_neighbors": [_P, _I, C.POINTER(_P), C.POINTER(_I), _D, C.POINTER(_P),
                                     C.POINTER(_P), C.POINTER(_L), C.POINTER(_L)],
+    "tbk_welsh_powell": [_I, _P, _P, _P, C.POINTER(_I)],
     "tbk_assemble_H": [_P, C.POINTER(tbk_model), _P, _I, _P, _P, _P, _L, _P],
     "tbk_spectral_bounds": [_P, C.POINTER(tbk_bsr), _I, _D, _U, C.POINTER(_D), C.POINTER(_D)],
     "tbk_batched_spectral_bounds": [_P, _I, C.POINTER(tbk_bsr), _I, _D, _U, C.POINTER(_D), C.POINTER(_D)],

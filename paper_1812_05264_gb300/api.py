@@ -166,6 +166,27 @@ def build_neighbors(ctx: Context, pos: torch.Tensor, cutoff: float, box=None) ->
     return Graph(n, nnz.value, row_ptr, col[:nnz.value])
 
 
+def welsh_powell(row_ptr: np.ndarray, col: np.ndarray) -> tuple[np.ndarray, int]:
+    """Welsh-Powell colours of a symmetric CSR graph (host int32 arrays, ascending columns, self
+    entries ignored) and their number; the library's host colouring (Sec. III)."""
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
+    cl = np.ascontiguousarray(col, dtype=np.int32)
+    n = rp.size - 1
+    color = np.empty(max(n, 1), dtype=np.int32)
+    q = C.c_int32()
+    L.call("tbk_welsh_powell", n, rp.ctypes.data, cl.ctypes.data if cl.size else None,
+           color.ctypes.data, C.byref(q))
+    return color[:n], q.value
+
+
+def atom_colors(ctx: Context, pos: torch.Tensor, r_color: float, box=None) -> tuple[np.ndarray, int]:
+    """Colours of the atoms for the multi-colour probe ensemble (Sec. II.C.3): the neighbour
+    pattern at the colouring radius built on the device, coloured by Welsh-Powell on the host,
+    so that two atoms of one colour are farther apart than r_color."""
+    g = build_neighbors(ctx, pos, r_color, box)
+    return welsh_powell(g.row_ptr.cpu().numpy(), g.col.cpu().numpy())
+
+
 def batched_build_neighbors(ctx: Context, positions: list, cutoff: float) -> list:
     """a1 for many open clusters in one call: the patterns of build_neighbors, cluster by
     cluster, with every pass run once over all the clusters' atoms."""

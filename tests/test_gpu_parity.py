@@ -71,6 +71,22 @@ def test_neighbors_single_atom_and_empty(api, ctx):
     assert g0.nnzb == 0
 
 
+@pytest.mark.parametrize("case", ["fcc500_r6", "sc_periodic_r2"])
+def test_atom_colours_equal_the_oracle(api, ctx, case):
+    """Multi-colour ensemble preprocessing (Sec. III): the device neighbour list at the colouring
+    radius, coloured by the library's Welsh-Powell pass, colour for colour the oracle's."""
+    from oracle import coloring as oco
+    box = None
+    if case == "fcc500_r6":
+        pos, r = wl.fcc_sphere(500, jitter=0.05, seed=5), 6.0
+    else:
+        pos, box = wl.sc_lattice(8)
+        r = 2.0
+    c, q = api.atom_colors(ctx, _dev(pos), r, box)
+    ref = oco.atom_colors(pos, r, box)
+    assert np.array_equal(c, ref) and q == int(ref.max()) + 1
+
+
 # ---- a2 assembly ----------------------------------------------------------------------------
 
 def test_assemble_sk_matches_oracle(api, ctx):

@@ -145,6 +145,26 @@ def exact_probe_moments(eps, V, R, emin, emax, p):
     return cheb_T(mapped(eps, emin, emax), p) @ (C * C)
 
 
+def recurrence_probe_moments(H, R, emin, emax, p):
+    """mu_k^(i) = r_i^T C_k(H^) r_i for k < p (rows) and the probes in the columns of R, by the
+    three-term recurrence of Eq. poly_PQ in FP64: y_0 = r, y_1 = H^ r, y_{k+1} = 2 H^ y_k - y_{k-1}.
+    H is anything with a matrix product (dense or SciPy sparse); for clusters too large for
+    the eigen-decomposition."""
+    R = np.asarray(R, dtype=np.float64)
+    W, c = emax - emin, emax + emin
+    hat = lambda Y: (2.0 * (H @ Y) - c * Y) / W
+    out = np.zeros((p, R.shape[1]))
+    y0 = R
+    out[0] = np.sum(R * y0, axis=0)
+    if p > 1:
+        y1 = hat(y0)
+        out[1] = np.sum(R * y1, axis=0)
+        for k in range(2, p):
+            y0, y1 = y1, 2.0 * hat(y1) - y0
+            out[k] = np.sum(R * y1, axis=0)
+    return out
+
+
 def estimator_observables(moments, emin, emax, mu, T, use_jackson=False):
     """(Omega^, E^, N^) = sum_k g_k c_k mu_k with c = beta[g], alpha[eps f], alpha[f]."""
     p = len(moments)

@@ -1,4 +1,4 @@
-"""Dense Hamiltonians for the oracle (test-only).
+"""Dense (and, for large clusters, sparse) Hamiltonians for the oracle (test-only).
 
 Two models, both orthogonal (S = I, Sec. II.A):
 
@@ -39,6 +39,20 @@ def dense_sk(pos, row_ptr, col, V, r0, decay, onsite_spd, box=None):
     for i in range(n):
         H[9 * i:9 * i + 9, 9 * i:9 * i + 9] = ons
     return H
+
+
+def sparse_sk(pos, row_ptr, col, V, r0, decay, onsite_spd, box=None):
+    """The SK Hamiltonian of ``dense_sk`` as a SciPy BSR matrix with 9 x 9 blocks, for clusters
+    whose dense matrix does not fit in memory."""
+    import scipy.sparse as sp
+    n = pos.shape[0]
+    a, b = pairs(row_ptr, col)
+    off = a != b
+    data = np.zeros((len(a), 9, 9))
+    data[off] = slater_koster.block(bond_vectors(pos, a[off], b[off], box), V, r0, decay)
+    data[~off] = slater_koster.onsite_block(*onsite_spd)
+    return sp.bsr_matrix((data, np.asarray(col, dtype=np.int64), np.asarray(row_ptr, dtype=np.int64)),
+                         shape=(9 * n, 9 * n))
 
 
 def table_lookup(d, disp, tol=1e-6):

@@ -318,3 +318,29 @@ def test_bloch_oracle_reproduces_real_space():
     wts = bloch.estimator_weights(L, R, U)
     m_bloch = ch.cheb_T(ch.mapped(wk.ravel(), emin, emax), 12) @ wts.ravel()
     assert np.allclose(m_real, m_bloch, rtol=1e-10, atol=1e-8)
+
+
+def test_sparse_hamiltonian_equals_the_dense_one():
+    pos, rp, col, V, H = _small_sk(n=30, jitter=0.08)
+    Hs = hamiltonian.sparse_sk(pos, rp, col, V, wl.SK_R0, wl.SK_DECAY, wl.SK_ONSITE)
+    assert Hs.blocksize == (9, 9) and Hs.nnz == len(col) * 81
+    assert np.array_equal(Hs.toarray(), H)
+
+
+def test_recurrence_probe_moments_equal_the_eigen_route():
+    """The FP64 three-term recurrence on the probes (the route the oracle takes for clusters too
+    large to diagonalise) against the eigen route, on sparse and dense H."""
+    pos, rp, col, V, H = _small_sk(n=19)
+    Hs = hamiltonian.sparse_sk(pos, rp, col, V, wl.SK_R0, wl.SK_DECAY, wl.SK_ONSITE)
+    w, Vv = np.linalg.eigh(H)
+    emin, emax, p = w.min() - 0.7, w.max() + 0.3, 50
+    R = ch.probes(H.shape[0], 7, 19)
+    ref = ch.exact_probe_moments(w, Vv, R, emin, emax, p)
+    for M in (Hs, H):
+        got = ch.recurrence_probe_moments(M, R, emin, emax, p)
+        assert np.abs(got - ref).max() < 1e-11 * H.shape[0]
+    assert np.array_equal(got[0], np.full(7, float(H.shape[0])))     # r^T r = n
+    # each probe runs on its own: one column alone gives its moments (to rounding order)
+    assert np.allclose(ch.recurrence_probe_moments(Hs, R[:, 2:3], emin, emax, p)[:, 0],
+                       ch.recurrence_probe_moments(Hs, R, emin, emax, p)[:, 2],
+                       rtol=0, atol=1e-12 * H.shape[0])

@@ -44,3 +44,53 @@ def test_committed_profiles_state_their_workload_and_source():
         keys = {ln.split(": ", 1)[0] for ln in lines if ": " in ln}
         assert "workload" in keys, name
         assert any(k.endswith(".cu sha256[:16]") for k in keys), name
+
+
+class _FakeProc:
+    def terminate(self):
+        pass
+
+    def wait(self, timeout=None):
+        return 0
+
+    def kill(self):
+        pass
+
+
+def _sampler(bench, lines):
+    cs = bench.ClockSampler(0)
+    cs.proc = _FakeProc()
+    cs.lines = list(lines)
+    return cs.stop()
+
+
+def test_clock_summary_reads_nvidia_smi_lines():
+    """The clocks record: median SM clock under load, the maximum, and every throttle reason seen
+    active ('Not Active' is not active); malformed lines are skipped."""
+    bench = _bench()
+    na = "Not Active"
+    lines = [f"0, {mhz}, 2070, 900.5, 0x0000000000000000, {na}, {na}, {na}, {na}" for mhz in
+             (2070, 2055, 2070, 1980, 2070)]
+    lines.append(f"0, 1965, 2070, 1398.0, 0x0000000000000004, {na}, {na}, {na}, Active")
+    lines += ["", "garbage", "0, [N/A], 2070, 1, 0x0, a, b, c, d"]
+    out = _sampler(bench, lines)
+    assert out["sm_mhz"] == 2062.5 and out["sm_max_mhz"] == 2070.0 and out["samples"] == 6
+    assert out["reasons"] == ["sw_power_cap"]
+    out = _sampler(bench, [f"0, 1500, 2070, 700, 0x68, Active, Active, {na}, {na}"])
+    assert out["reasons"] == ["hw_slowdown", "hw_thermal_slowdown"]
+    off = bench.ClockSampler(0, enabled=False)
+    off.start()
+    assert off.stop()["reasons"] == ["not sampled (--no-clocks)"]
+
+
+def test_bench_order_rule_and_default_workload():
+    """The bench takes the library's order rule and, by default, the 10,000-atom fcc workload at
+    kT = 0.025 eV with 512 probes."""
+    from paper_1812_05264_gb300 import api
+    bench = _bench()
+    for W, kT in ((120.0, 0.025), (40.0, 0.5), (10.0, 3.0)):
+        assert bench.order_rule(W, kT) == api.order_for(W, kT)
+    wk = bench.make_workload("fcc10k")
+    assert wk.n_atoms == 10000 and wk.n_probes == 512 and wk.kT == 0.025 and wk.n_orb == 9
+    assert wk.mixed and wk.name.startswith("fcc10000")
+    assert bench.make_workload("fcc10k", rank=1).probe_seed == wk.probe_seed + 1   # replicas

@@ -94,3 +94,31 @@ def test_bench_order_rule_and_default_workload():
     assert wk.n_atoms == 10000 and wk.n_probes == 512 and wk.kT == 0.025 and wk.n_orb == 9
     assert wk.mixed and wk.name.startswith("fcc10000")
     assert bench.make_workload("fcc10k", rank=1).probe_seed == wk.probe_seed + 1   # replicas
+
+
+def test_reference_arm_prints_one_contract_line(capsys):
+    """`bench.py --impl reference` times the oracle on the host: one JSON line with the contract's
+    keys, its own value as cpu_baseline and e2e, no host-device bytes; other ranks print nothing."""
+    import argparse
+    import json
+    bench = _bench()
+    bench.oracle_sample.__defaults__ = (30,)           # a 30-atom sample keeps this test short
+    args = argparse.Namespace(workload="fcc1k", atom_order="radial", probes=None, warmup=1,
+                              steps=2, gpus=1)
+    assert bench.run_reference(args, 1, 2) == 0
+    assert capsys.readouterr().out == ""
+    assert bench.run_reference(args, 0, 1) == 0
+    out = capsys.readouterr().out.strip().splitlines()
+    assert len(out) == 1
+    line = json.loads(out[0])
+    for k in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+              "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config",
+              "cpu_baseline", "e2e"):
+        assert k in line, k
+    assert line["impl"] == "reference" and line["value"] > 0 and line["steps"] == 2
+    assert line["metric"] == bench.METRIC and line["unit"] == bench.UNIT
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
+    assert line["cpu_baseline"]["cores"] >= 1 and "30 atoms" in line["cpu_baseline"]["sample"]
+    assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
+    assert line["config"]["workload"].startswith("fcc30") and line["config"]["sample_of"] == "fcc1k"

@@ -73,3 +73,18 @@ def test_missing_library_fails_loudly(tmp_path):
     r = subprocess.run(["python", "-c", code], cwd=ROOT, capture_output=True, text=True)
     assert r.returncode != 0
     assert "libtbk.so not found" in r.stderr
+
+
+def test_no_device_means_an_error_not_a_fallback(lib):
+    """On a machine without a usable GPU the context cannot be made: the ABI returns an error code
+    with a message (no handle), and the Python layer raises before any work."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_1812_05264_gb300 import _lib, api
+    h = ctypes.c_void_p()
+    rc = lib.tbk_create(ctypes.byref(h), 0, None)
+    assert rc in (_lib.TBK_ERR_CUDA, _lib.TBK_ERR_ARG) and h.value is None
+    assert lib.tbk_last_error()
+    with pytest.raises(RuntimeError, match="CUDA device"):
+        api.Context()

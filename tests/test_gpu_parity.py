@@ -28,7 +28,9 @@ def api():
 
 @pytest.fixture(scope="module")
 def ctx(api):
-    return api.Context()
+    c = api.Context()
+    yield c
+    c.close()           # give the device memory back before the next module
 
 
 def _dev(x):

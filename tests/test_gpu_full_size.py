@@ -6,7 +6,8 @@ The dense oracle does not fit at this size (90,000 rows), so the checks are:
 * the neighbour pattern, bit for bit, and every stored block of H, against the oracle's sparse
   assembly;
 * sampled outputs the oracle computes one by one: the per-probe moments r_i^T C_k(H^) r_i of
-  three probes, by the FP64 three-term recurrence on the sparse H (Eq. poly_PQ);
+  three probes, by the FP64 three-term recurrence on the sparse H (Eq. poly_PQ), against the
+  benchmarked mixed path and against the plain FP64 path;
 * properties that hold at any size: the bisection meets N^(mu^) = N_e, the forces sum to zero
   (H depends only on the bond vectors), and the one-call path's moments are those of the
   moments call.
@@ -73,18 +74,24 @@ def test_pattern_and_blocks_at_full_size(run):
     assert np.abs(val - run["Hs"].data).max() < 1e-13
 
 
-@pytest.mark.parametrize("direct", [False, True])
-def test_sampled_probe_moments_at_full_size(api, run, direct):
+@pytest.mark.parametrize("fp64,direct", [(False, False), (False, True), (True, False)])
+def test_sampled_probe_moments_at_full_size(api, run, fp64, direct):
+    """Mixed: the benchmarked precision, within 2e-6 n.  FP64: the plain FP64 path against the
+    oracle's FP64 recurrence on the same probes, within 1e-11 n (both sides round in FP64)."""
     n = run["Hs"].shape[0]
     mom, per = api.chebyshev_probe_moments(run["ctx"], run["H"], run["emin"], run["emax"], PROBE_SEED,
-                                           S, P_SAMPLED, direct=direct)
+                                           S, P_SAMPLED, fp64=fp64, direct=direct)
     R = och.probes(n, S, PROBE_SEED)[:, SAMPLED]
     ref = och.recurrence_probe_moments(run["Hs"].tocsr(), R, run["emin"], run["emax"], P_SAMPLED)
     got = per.cpu().numpy()[:, SAMPLED]
-    assert np.abs(got - ref).max() < 2e-6 * n
-    # the probe mean is the moments call, and the one-call path's sweep gives the same moments
-    assert np.allclose(per.mean(dim=1).cpu().numpy(), mom.cpu().numpy(), rtol=0, atol=1e-6 * n)
-    assert np.allclose(run["mom"][:P_SAMPLED].cpu().numpy(), mom.cpu().numpy(), rtol=0, atol=1e-6 * n)
+    assert np.abs(got - ref).max() < (1e-11 if fp64 else 2e-6) * n
+    # the probe mean is the moments call
+    assert np.allclose(per.mean(dim=1).cpu().numpy(), mom.cpu().numpy(), rtol=0,
+                       atol=(1e-12 if fp64 else 1e-6) * n)
+    if not fp64:
+        # and the one-call path's forward sweep gives the same moments
+        assert np.allclose(run["mom"][:P_SAMPLED].cpu().numpy(), mom.cpu().numpy(), rtol=0,
+                           atol=1e-6 * n)
 
 
 def test_properties_of_the_full_step(run):

@@ -55,8 +55,9 @@ def run(api):
                                              want_forces=True)
     rp, col = onb.neighbor_csr(wk.positions, wk.cutoff)
     Hs = oham.sparse_sk(wk.positions, rp, col, wk.sk_V, wl.SK_R0, wl.SK_DECAY, wl.SK_ONSITE)
+    R = och.probes(Hs.shape[0], S, PROBE_SEED)[:, SAMPLED]
     out = dict(wk=wk, ctx=ctx, g=g, H=H, emin=emin, emax=emax, p=p, mom=mom, obs=obs, F=F,
-               rp=rp, col=col, Hs=Hs)
+               rp=rp, col=col, Hs=Hs, Hcsr=Hs.tocsr(), R=R)
     yield out
     # the one-call path keeps its panels in device memory: give them back before the next module
     out.clear()
@@ -81,8 +82,7 @@ def test_sampled_probe_moments_at_full_size(api, run, fp64, direct):
     n = run["Hs"].shape[0]
     mom, per = api.chebyshev_probe_moments(run["ctx"], run["H"], run["emin"], run["emax"], PROBE_SEED,
                                            S, P_SAMPLED, fp64=fp64, direct=direct)
-    R = och.probes(n, S, PROBE_SEED)[:, SAMPLED]
-    ref = och.recurrence_probe_moments(run["Hs"].tocsr(), R, run["emin"], run["emax"], P_SAMPLED)
+    ref = och.recurrence_probe_moments(run["Hcsr"], run["R"], run["emin"], run["emax"], P_SAMPLED)
     got = per.cpu().numpy()[:, SAMPLED]
     assert np.abs(got - ref).max() < (1e-11 if fp64 else 2e-6) * n
     # the probe mean is the moments call

@@ -3,7 +3,7 @@ import numpy as np
 import pytest
 
 import workloads as wl
-from oracle import neighbors
+from oracle import hamiltonian, neighbors
 
 
 def _sc_expected(L, periodic):
@@ -83,3 +83,41 @@ def test_batched_sizes_in_range():
     assert spec.sizes.min() >= 100 and spec.sizes.max() <= 5000
     assert set(np.unique(spec.kTs)) <= {0.025, 0.1, 0.5}
     assert all(p.shape == (n, 3) for p, n in zip(spec.positions, spec.sizes))
+
+
+def test_morton_order_is_a_permutation_that_keeps_neighbours_close():
+    pos = wl.fcc_sphere(2000, seed=1)
+    perm = wl.morton_order(pos, wl.FCC_A)
+    assert np.array_equal(np.sort(perm), np.arange(2000))
+    # the same cluster: the reordered atoms are the original atoms
+    a = wl.fcc_cu(2000, kT=0.1, n_probes=8, atom_order="morton").positions
+    b = wl.fcc_cu(2000, kT=0.1, n_probes=8).positions
+    assert np.array_equal(a[np.lexsort(a.T[::-1])], b[np.lexsort(b.T[::-1])])
+    # Z-order keeps bonded atoms closer in index than the radial listing does
+    rp, col = neighbors.neighbor_csr(a, 2.6)
+    rows = np.repeat(np.arange(2000), np.diff(rp))
+    rpb, colb = neighbors.neighbor_csr(b, 2.6)
+    rowsb = np.repeat(np.arange(2000), np.diff(rpb))
+    assert np.median(np.abs(rows - col)) < np.median(np.abs(rowsb - colb))
+
+
+def test_lattice9_hermitian_table_gives_a_symmetric_h():
+    """h_{-d} = h_d^T: the periodic 9-orbital lattice built from the table is symmetric."""
+    wk = wl.sc9_periodic(L=4, n_probes=8)
+    rp, col = neighbors.neighbor_csr(wk.positions, wk.cutoff, wk.box)
+    H = hamiltonian.dense_table(wk.positions, rp, col, 9, wk.disp, wk.blocks, wk.onsite_site, wk.box)
+    assert np.array_equal(H, H.T)
+    assert len(col) == 64 * 19                              # 1 + 6 + 12 neighbours per site
+
+
+def test_batched_clusters_are_log_uniform_with_every_temperature():
+    spec = wl.batched_clusters(64, 100, 5000, (0.025, 0.1, 0.5), seed=64)
+    lg = np.log(spec.sizes)
+    # log-uniform on [log 100, log 5000]: mean 6.21, sd 1.13; 64 draws stay within 4 sigma/8
+    assert abs(lg.mean() - 0.5 * (np.log(100) + np.log(5000))) < 4 * 1.13 / 8
+    assert set(np.unique(spec.kTs)) == {0.025, 0.1, 0.5}
+    assert len(set(spec.seeds.tolist())) == 64
+    # the same seed gives the same batch
+    again = wl.batched_clusters(64, 100, 5000, (0.025, 0.1, 0.5), seed=64)
+    assert np.array_equal(spec.sizes, again.sizes) and np.array_equal(spec.kTs, again.kTs)
+    assert all(np.array_equal(p, q) for p, q in zip(spec.positions, again.positions))

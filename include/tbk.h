@@ -174,7 +174,7 @@ int tbk_batched_build_neighbors(tbk_ctx* ctx, int32_t n_clusters, const double* 
                                 const int32_t* n_atoms, double cutoff, int32_t* const* row_ptr,
                                 int32_t* const* col, const int64_t* col_capacity, int64_t* nnzb);
 
-/* Welsh-Powell colouring of the atoms (Sec. III), for the multi-colour probe ensemble of
+/* Welsh-Powell colouring of the atoms (Sec. II.E), for the multi-colour probe ensemble of
    Sec. II.C.3: the vertices are listed by non-increasing degree (equal degrees in index order),
    and each takes the smallest colour that none of its earlier-listed neighbours has.  This is
    the same colouring as building one colour class at a time down the list.  Two atoms of one
@@ -371,7 +371,14 @@ int tbk_batched_energies_and_forces(tbk_ctx* ctx, int32_t n_clusters, const tbk_
      problem whose scratch (mapped H, two panels, per-step partial sums) exceeds the static size
      fails with TBK_ERR_ARG and a message giving the bytes it would need.
    - The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
-     that device current; make that first call before any stream capture.
+     that device current; make that first call before any stream capture.  Under CUDA's lazy
+     module loading (the default) that first call is also the one that loads the library's
+     module and so commits the 64 MiB on the device: it can fail for lack of device memory, and
+     only the calls after it allocate nothing.  The address is kept per device for the life of
+     the process, so the device's primary context must stay alive between calls (no
+     cudaDeviceReset), and calls must run under that primary context.
+   - The context's kernel timer (tbk_kernel_timer) is switched off for the duration of the call:
+     timing would create CUDA events.
    - Every call on a device shares the one array and leaves its contents behind (the call clears
      what must start at zero).  Calls whose work overlaps on the GPU -- on different streams, or
      from different host threads -- race on the array and give wrong results. */

@@ -20,7 +20,7 @@ Modules (each function cites the part of arXiv 1812.05264 it follows):
   Daleckii-Krein form), estimator forces and the Hutchinson variance (Eq. sampling_error).
 * ``bloch``      -- Bloch-theorem oracle for translation-invariant periodic lattices
   (Sec. II.E, periodic reference algorithm).
-* ``coloring``   -- Welsh-Powell colouring of the atom graph (Sec. III) and the multi-colour
+* ``coloring``   -- Welsh-Powell colouring of the atom graph (Sec. II.E) and the multi-colour
   probe ensemble (Sec. II.C.3): coloured probes, the estimator's exact moments and gradient,
   its sampling error.
 * ``direct``     -- direct random estimates M o P~ and M o Q~ of the density and

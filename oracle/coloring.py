@@ -7,7 +7,7 @@ entries have unit modulus and random phase.  The mean of R_i R_i^T is I, and the
 deviation E_jk is 1 when c(j) = c(k) with j != k and 0 otherwise, so the sampling error of
 Eq. sampling_error only sees the matrix elements between distinct functions of one colour.
 
-Sec. III (implementation): atom colours come from the Welsh-Powell vertex colouring (Welsh &
+Sec. II.E (implementation details): atom colours come from the Welsh-Powell vertex colouring (Welsh &
 Powell, The Computer Journal 10, 85 (1967)) of the graph whose vertices are the atoms and whose
 edges join atoms closer than the colouring radius; each of an atom's n_orb orbitals then takes a
 colour of its own, so one atom colour stands for n_orb function colours.

@@ -168,7 +168,7 @@ def build_neighbors(ctx: Context, pos: torch.Tensor, cutoff: float, box=None) ->
 
 def welsh_powell(row_ptr: np.ndarray, col: np.ndarray) -> tuple[np.ndarray, int]:
     """Welsh-Powell colours of a symmetric CSR graph (host int32 arrays, ascending columns, self
-    entries ignored) and their number; the library's host colouring (Sec. III)."""
+    entries ignored) and their number; the library's host colouring (Sec. II.E)."""
     rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
     cl = np.ascontiguousarray(col, dtype=np.int32)
     n = rp.size - 1

@@ -1,4 +1,4 @@
-// Welsh-Powell colouring of the atoms (Sec. III) for the multi-colour probe ensemble of
+// Welsh-Powell colouring of the atoms (Sec. II.E) for the multi-colour probe ensemble of
 // Sec. II.C.3.  Host code: it runs once per geometry on the colouring graph's CSR.
 //
 // Welsh & Powell (The Computer Journal 10, 85 (1967)) list the vertices by non-increasing

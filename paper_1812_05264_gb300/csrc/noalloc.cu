@@ -19,7 +19,10 @@ constexpr size_t kStaticScratchBytes = TBK_NOALLOC_SCRATCH_BYTES;
 
 static __device__ __align__(256) unsigned char g_tbk_static_scratch[kStaticScratchBytes];
 
-// Device address of the array, looked up once per device with that device current.  In host code
+// Device address of the array, looked up once per device with that device current (under lazy
+// module loading this lookup also loads the module, which commits the array's device memory).  The
+// address belongs to the device's primary context: it stays valid while that context lives, i.e.
+// until the process exits or calls cudaDeviceReset.  In host code
 // the symbol name is only a host-side stand-in: handing it to a kernel would fault or, where the
 // GPU can reach host memory, silently use the wrong memory.  Only the address returned by
 // cudaGetSymbolAddress is passed to kernels.
@@ -41,6 +44,15 @@ static void* static_scratch_address(int device) {
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// Switches the context's kernel timer off for the scope: a timed launch records CUDA events, and
+// the first events of a context are created on demand, which this entry point must not do.
+struct TimerOff {
+  tbk_ctx* ctx;
+  int mask;
+  explicit TimerOff(tbk_ctx* c) : ctx(c), mask(c->timed_mask) { c->timed_mask = 0; }
+  ~TimerOff() { ctx->timed_mask = mask; }
+};
+
 }  // namespace tbk
 
 using namespace tbk;
@@ -57,7 +69,11 @@ extern "C" int tbk_chebyshev_moments_noalloc(tbk_ctx* ctx, const tbk_bsr* H, dou
   TBK_CHECK_ARG((flags & ~(TBK_FP64 | TBK_MOMENTS_DIRECT | TBK_PLAIN_KERNEL)) == 0, "unknown flag");
   TBK_CHECK_ARG(H->n_orb == 1 || H->n_orb == 9, "n_orb must be 1 or 9");
   TBK_CHECK_ARG(H->n_atoms >= 1 && H->nnzb >= H->n_atoms, "empty or inconsistent matrix");
+  TBK_CHECK_ARG(H->nnzb < INT32_MAX, "nnzb must be below 2^31");
+  TBK_CHECK_ARG(H->row_ptr != nullptr && H->col != nullptr && H->val != nullptr,
+                "H->row_ptr, H->col or H->val is NULL");
   DeviceGuard dg(ctx);
+  TimerOff no_events(ctx);
   unsigned char* base = (unsigned char*)static_scratch_address(ctx->device);
   const int prec = (flags & TBK_FP64) ? TBK_FP64 : TBK_MIXED;
   const int direct = (flags & TBK_MOMENTS_DIRECT) ? 1 : 0;

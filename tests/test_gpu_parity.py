@@ -75,7 +75,7 @@ def test_neighbors_single_atom_and_empty(api, ctx):
 
 @pytest.mark.parametrize("case", ["fcc500_r6", "sc_periodic_r2"])
 def test_atom_colours_equal_the_oracle(api, ctx, case):
-    """Multi-colour ensemble preprocessing (Sec. III): the device neighbour list at the colouring
+    """Multi-colour ensemble preprocessing (Sec. II.E): the device neighbour list at the colouring
     radius, coloured by the library's Welsh-Powell pass, colour for colour the oracle's."""
     from oracle import coloring as oco
     box = None

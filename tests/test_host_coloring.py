@@ -1,4 +1,4 @@
-"""The library's Welsh-Powell colouring (host code behind the C ABI; Sec. III) against the oracle,
+"""The library's Welsh-Powell colouring (host code behind the C ABI; Sec. II.E) against the oracle,
 colour for colour, and its argument checks.  CPU only: this entry point touches no device."""
 import numpy as np
 import pytest

@@ -1,4 +1,4 @@
-"""Pins for the oracle's multi-colour probe ensemble (Sec. II.C.3 and Sec. III; CPU only).
+"""Pins for the oracle's multi-colour probe ensemble (Sec. II.C.3 and Sec. II.E; CPU only).
 
 The colouring is pinned by colourings worked out by hand, by the first-fit restatement of the
 Welsh-Powell procedure, by the Welsh-Powell bound and by brute-force distances; the ensemble by

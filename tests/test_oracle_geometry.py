@@ -78,6 +78,19 @@ def test_lattice9_blocks_gershgorin_scale():
     assert abs(rows.max() - 5.0) < 1e-12
 
 
+def test_lattice9_workload_has_a_ten_ev_bloch_band():
+    """The periodic 9-orbital workload's blocks are scaled by a stored constant to a 10 eV band:
+    the Bloch eigenvalues of the scaled model on the 48^3 k-grid span exactly 10 eV, and the
+    constant is the unscaled width (the blocks are linear in it)."""
+    from oracle import bloch
+    wk = wl.sc9_periodic(L=48, n_probes=8)
+    w, _ = bloch.bands(48, wk.disp, wk.blocks)
+    assert abs((w.max() - w.min()) - 10.0) < 1e-9
+    dirs, h1 = wl.lattice9_blocks(4848, scale=1.0)
+    _, h10 = wl.lattice9_blocks(4848, band_width=10.0)
+    assert np.allclose(h10, h1 * 10.0 / wl.lattice9_width(4848), rtol=1e-15, atol=0)
+
+
 def test_batched_sizes_in_range():
     spec = wl.batched_clusters(64, 100, 5000, (0.025, 0.1, 0.5), seed=64)
     assert spec.sizes.min() >= 100 and spec.sizes.max() <= 5000

@@ -28,16 +28,26 @@ def _round(a, bits):
     return u.astype(np.uint32).view(np.float32)
 
 
+def _trunc(a, bits):
+    """float32 values with all but `bits` explicit mantissa bits cleared (rounded toward zero):
+    what a TF32 tensor-core operation reads from an FP32 register or shared-memory word."""
+    u = np.asarray(a, dtype=np.float32).view(np.uint32)
+    return (u & np.uint32((0xFFFFFFFF << (23 - bits)) & 0xFFFFFFFF)).view(np.float32)
+
+
 def _mm(A, B, fmt):
-    """A @ B with float32 operands in the emulated format; float32 result."""
+    """A @ B with float32 operands in the emulated format; float32 result.  "tf32x3t" is the
+    split as the tensor cores take it from FP32 words: head = truncation of the value, remainder
+    = value - head (exact in FP32), and each operand read truncated to TF32 again."""
     A, B = A.astype(np.float32), B.astype(np.float32)
     if fmt == "fp32":
         return A @ B
     bits = {"tf32": 10, "bf16": 7}[fmt[:4]]
-    Ah, Bh = _round(A, bits), _round(B, bits)
+    q = _trunc if fmt.endswith("t") else _round
+    Ah, Bh = q(A, bits), q(B, bits)
     out = Ah @ Bh
-    if fmt.endswith("x3"):
-        out = out + Ah @ _round(B - Bh, bits) + _round(A - Ah, bits) @ Bh
+    if "x3" in fmt:
+        out = out + Ah @ q(B - Bh, bits) + q(A - Ah, bits) @ Bh
     return out.astype(np.float32)
 
 
@@ -112,19 +122,21 @@ def test_fp32_emulation_reproduces_the_mixed_path_accuracy(case):
     assert e < 1e-5 and f < 1e-5               # the FP32 path's level (tolerances 1e-4, 1e-3)
 
 
-@pytest.mark.parametrize("fmt,ok", [("bf16x3", True), ("tf32x3", True), ("bf16", False)])
+@pytest.mark.parametrize("fmt,ok", [("bf16x3", True), ("tf32x3", True), ("tf32x3t", True),
+                                    ("bf16", False)])
 def test_outer_product_formats(case, fmt, ok):
     _, f = _errors(case, "fp32", fmt)
     assert (f < 1e-3) == ok, f
-    if fmt == "bf16x3":
+    if fmt in ("bf16x3", "tf32x3t"):
         assert f < 1e-4                          # an order of magnitude inside the tolerance
 
 
-@pytest.mark.parametrize("fmt,ok", [("tf32x3", True), ("tf32", False)])
+@pytest.mark.parametrize("fmt,ok", [("tf32x3", True), ("tf32x3t", True), ("tf32", False),
+                                    ("tf32t", False)])
 def test_recurrence_formats(case, fmt, ok):
     e, f = _errors(case, fmt, "fp32")
     assert (e < 1e-4 and f < 1e-3) == ok, (e, f)
-    if fmt == "tf32x3":
+    if fmt in ("tf32x3", "tf32x3t"):
         assert e < 1e-5 and f < 1e-5             # as accurate as FP32
 
 
@@ -138,3 +150,5 @@ def test_rounding_helper():
     assert _round(np.float32(3.0), 7) == np.float32(3.0) and _round(one, 10) == one
     b = _round(np.float32(1 + 2.0 ** -8 + 2.0 ** -12), 7)            # BF16 spacing 2^-7
     assert b == np.float32(1.0 + 2.0 ** -7)
+    t = _trunc(np.array([1 + 3 * u / 2, -(1 + 3 * u / 2), 2 - u / 4, 1 + u], dtype=np.float32), 10)
+    assert t.tolist() == [1 + u, -(1 + u), 2 - u, 1 + u]             # toward zero, exact kept

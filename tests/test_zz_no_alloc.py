@@ -43,7 +43,7 @@ def _noalloc(L, ctx, H, emin, emax, seed, s, order, flags):
     return out
 
 
-@pytest.mark.parametrize("s,fp64", [(128, False), (16, True)])
+@pytest.mark.parametrize("s,fp64", [(128, False), (512, False), (16, True)])
 def test_noalloc_matches_regular_entry_point_twice(setup, s, fp64):
     L, api, ctx = setup
     wk, H, emin, emax = _problem(api, ctx, 90, s)
@@ -67,3 +67,32 @@ def test_noalloc_rejects_problems_above_the_static_size(setup):
     # the context still works afterwards
     ok = _noalloc(L, ctx, H, emin, emax, wk.probe_seed, 128, 20, L.TBK_MIXED)
     assert torch.isfinite(ok).all()
+
+
+def test_noalloc_on_a_fresh_context_allocates_nothing(setup):
+    """On a context that no regular call has touched (so none of its scratch slots exist), after
+    one warm call the allocation-free entry point leaves the device's free memory unchanged, with
+    the kernel timer switched on (timing would create CUDA events)."""
+    L, api, ctx0 = setup
+    wk, H, emin, emax = _problem(api, ctx0, 90, 512)
+    ref = api.chebyshev_moments(ctx0, H, emin, emax, wk.probe_seed, 512, 61).cpu().numpy()
+    ctx = api.Context()
+    try:
+        ctx.time_kernels("step", "backward", "window")
+        out = torch.empty(61, dtype=torch.float64, device="cuda")
+
+        def call():
+            L.call("tbk_chebyshev_moments_noalloc", ctx.handle, C.byref(H.struct()), emin, emax,
+                   C.c_uint64(wk.probe_seed), 512, 61, L.TBK_MIXED, out.data_ptr())
+            torch.cuda.synchronize()
+
+        call()
+        free0, _ = torch.cuda.mem_get_info()
+        call()
+        free1, _ = torch.cuda.mem_get_info()
+        assert free1 == free0
+        assert ctx.kernel_time("step") == (0.0, 0)
+        n = H.graph.n_atoms * 9
+        assert np.abs(out.cpu().numpy() - ref).max() <= 1e-9 * n
+    finally:
+        ctx.close()

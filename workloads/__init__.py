@@ -13,13 +13,15 @@ simple-cubic test model, Sec. IV):
                           sites in (r^2, x, y, z) lexicographic order, optional N(0, sigma) jitter.
 * ``sk_integrals``     -- the 10 Slater-Koster bond integrals ss_sigma .. dd_delta, N(0, 1) eV.
 * ``lattice9_blocks``  -- 9x9 hopping blocks for the 3 nearest- and 6 next-nearest-neighbour
-                          directions of a 9-orbital simple-cubic lattice, scaled so that the
-                          Gershgorin half-width of the Bloch Hamiltonian is ``half_width`` eV.
+                          directions of a 9-orbital simple-cubic lattice, scaled to a given Bloch
+                          band width (a stored constant written by make_lattice9_width.py) or to
+                          a Gershgorin half-width.
 * ``batched_clusters`` -- sizes (log-uniform in [lo, hi]) and temperatures for a batch of fcc
                           clusters.
 """
 from __future__ import annotations
 
+import os
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -99,20 +101,45 @@ def sk_integrals(seed: int) -> np.ndarray:
     return rng.standard_normal(10)
 
 
-def lattice9_blocks(seed: int, half_width: float = 5.0):
-    """Hopping blocks h_d for the 9 directions ``LATTICE9_DIRS`` (h_{-d} = h_d^T).
+def lattice9_width(seed: int) -> float:
+    """The Bloch band width (eV) of the unscaled blocks of ``seed`` on the 48^3 k-grid, as stored
+    by make_lattice9_width.py (which computes it with the oracle's Bloch eigenvalues)."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "lattice9_width.txt")
+    with open(path) as f:
+        for ln in f:
+            parts = ln.split()
+            if parts and not ln.startswith("#") and int(parts[0]) == seed:
+                return float(parts[2])
+    raise KeyError(f"no stored Bloch band width for seed {seed}; run workloads/make_lattice9_width.py")
 
-    The blocks are N(0, 1) and then share one scale c chosen so that the largest Gershgorin row
-    sum over all 18 bonds, max_i sum_d sum_l |c h_d[i, l]|, equals ``half_width`` (so the Bloch
-    band is inside [-half_width, half_width]).  On-site block = 0.
+
+def lattice9_blocks(seed: int, half_width: float | None = None, band_width: float | None = None,
+                    scale: float | None = None):
+    """Hopping blocks h_d for the 9 directions ``LATTICE9_DIRS`` (h_{-d} = h_d^T), on-site block 0.
+
+    The blocks are N(0, 1) times one scale c:
+    * ``band_width``: c = band_width / (stored Bloch band width of the unscaled blocks on the 48^3
+      k-grid), so the scaled model's band is band_width wide;
+    * ``half_width``: the largest Gershgorin row sum over all 18 bonds,
+      max_i sum_d sum_l |c h_d[i, l]|, equals half_width (the band lies in [-half_width,
+      half_width]);
+    * ``scale``: c itself.
+    Exactly one may be given; none means half_width = 5.
     Returns (dirs (9, 3), blocks (9, 9, 9)).
     """
+    if sum(x is not None for x in (half_width, band_width, scale)) > 1:
+        raise ValueError("give one of half_width, band_width, scale")
     rng = np.random.default_rng(seed)
     h = rng.standard_normal((9, 9, 9))
-    rows = np.zeros(9)
-    for d in range(9):
-        rows += np.abs(h[d]).sum(axis=1) + np.abs(h[d].T).sum(axis=1)
-    h *= half_width / rows.max()
+    if band_width is not None:
+        h *= band_width / lattice9_width(seed)
+    elif scale is not None:
+        h *= scale
+    else:
+        rows = np.zeros(9)
+        for d in range(9):
+            rows += np.abs(h[d]).sum(axis=1) + np.abs(h[d].T).sum(axis=1)
+        h *= (5.0 if half_width is None else half_width) / rows.max()
     return LATTICE9_DIRS.copy(), h
 
 
@@ -205,9 +232,10 @@ def fcc_cu(n_atoms: int, kT: float, n_probes: int, seed: int = 5264, probe_seed:
 
 def sc9_periodic(L: int = 48, kT: float = 0.05, n_probes: int = 512, seed: int = 4848,
                  probe_seed: int = 48480, order: int | None = None, mixed: bool = True) -> Workload:
-    """Periodic 9-orbital simple-cubic lattice with NN and NNN 9x9 hopping blocks, half filling."""
+    """Periodic 9-orbital simple-cubic lattice with NN and NNN 9x9 hopping blocks scaled to a
+    10 eV Bloch band (on the 48^3 k-grid), half filling."""
     pos, box = sc_lattice(L)
-    dirs, h = lattice9_blocks(seed)
+    dirs, h = lattice9_blocks(seed, band_width=10.0)
     disp = np.concatenate([dirs, -dirs])
     blocks = np.concatenate([h, np.transpose(h, (0, 2, 1))])
     return Workload(name=f"sc9-{L}^3-periodic-kT{kT:g}", positions=pos, n_orb=9, kT=kT,

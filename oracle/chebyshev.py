@@ -115,6 +115,18 @@ def damping(p: int, use_jackson: bool) -> np.ndarray:
     return jackson(p) if use_jackson else np.ones(p)
 
 
+def probe_columns(n_rows: int, cols, seed: int) -> np.ndarray:
+    """Columns ``cols`` of the probe block ``probes(n_rows, s, seed)`` (any s > max(cols)),
+    generated directly from the same counter definition, for blocks too large to hold whole."""
+    with np.errstate(over="ignore"):
+        i = np.arange(n_rows, dtype=np.uint64)[:, None]
+        j = np.asarray(cols, dtype=np.uint64)[None, :]
+        x = (i << np.uint64(32)) | j
+        state = np.uint64(seed) + (x + np.uint64(1)) * _GAMMA
+        v = splitmix64(state)
+    return np.where((v >> np.uint64(63)) == 1, -1.0, 1.0)
+
+
 def cheb_T(x: np.ndarray, p: int) -> np.ndarray:
     """C_k(x) = cos(k arccos x) for k < p (rows) at points x (columns); |x| <= 1."""
     th = np.arccos(np.clip(x, -1.0, 1.0))

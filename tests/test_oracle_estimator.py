@@ -32,6 +32,8 @@ def test_probes_are_rademacher_and_balanced():
     # (1/s) R^T R ~ I
     G = R.T @ R / 4096
     assert np.abs(G - np.eye(64)).max() < 6 / np.sqrt(4096)
+    # single columns of a large block come from the same counters
+    assert np.array_equal(ch.probe_columns(4096, [0, 37, 63], 7), R[:, [0, 37, 63]])
 
 
 @pytest.mark.parametrize("m", [0, 1, 5, 17])

@@ -15,7 +15,12 @@ and forces).  Every launch of the three kernel families of the path (recurrence 
 step, windowed outer products) is bracketed by CUDA events inside the timed steps; `kernels`
 gives each family's roofline (HBM bytes or FP32 FMA flops, whichever bounds it) and `roofline`
 repeats the one with the largest share of the step.  `cpu_baseline` times the FP64 oracle on a
-bounded sub-cluster.
+bounded sub-cluster.  Two more measured configurations ride along in the same line (single GPU,
+after the main workload's memory is given back): `fp64_compare`, the 48^3 periodic 9-orbital
+lattice (1.0M orbitals, 10 eV band, kT = 0.05 eV, 512 probes) run whole by the mixed path and by
+the plain FP64 GPU path, with both times, both results and the speed-up at equal accuracy; and
+`batched64`, the 64-cluster batch (energies and forces of every cluster per step) with its own
+value, e2e and roofline.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Under torchrun (N > 1) every rank runs an independent replica (replicas only: the path has no
@@ -449,6 +454,25 @@ def run_ours(args, rank, world):
                 "sample": (f"FP64 oracle (dense eigh, exact estimator, Daleckii-Krein forces) on "
                            f"the first {swk.n_atoms} atoms of the cluster, {swk.n_probes} probes, "
                            f"p={ps}, {dt:.1f} s")}
+    if world == 1 and not args.no_extras and args.workload == "fcc10k" and not args.order:
+        # the other two measured configurations, each in a context of its own after this
+        # workload's panels (229 GB) are given back:
+        # - the 48^3 periodic lattice, mixed against the plain FP64 GPU path at equal accuracy;
+        # - the 64-cluster batch (energies and forces of every cluster per step).
+        ctx.close()
+        torch.cuda.empty_cache()
+        c5 = api.Context()
+        wk5 = make_workload("sc9-48", rank)
+        s5 = api.Solver(wk5, c5)
+        line["fp64_compare"] = fp64_compare(c5, s5, wk5, torch.as_tensor(
+            wk5.positions, dtype=torch.float64, device=f"cuda:{local}"))
+        c5.close()
+        torch.cuda.empty_cache()
+        b = batched_line(args.batch_steps, max(3, args.batch_warmup), "windowed", rank, world,
+                         not args.no_clocks)
+        line["batched64"] = {k: b[k] for k in ("value", "unit", "ms_per_step", "steps", "warmup",
+                                                 "config", "e2e", "gpu_launches", "roofline",
+                                                 "kernels", "phases_ms_per_step", "clocks")}
     if rank == 0:
         print(json.dumps(line))
     if dist:
@@ -481,13 +505,24 @@ def moments_only(args, ctx, solver, wk, pos):
 def precision_compare(args, ctx, solver, wk, pos):
     """Mixed (FP32 recurrence, FP64 moments) against the plain FP64 GPU path on the same
     workload, probes and order: time per recurrence step and the energy difference per site."""
+    print(json.dumps({"compare": "mixed_vs_fp64", **fp64_compare(ctx, solver, wk, pos)}))
+    return 0
+
+
+def fp64_compare(ctx, solver, wk, pos):
+    """One full moments run of each path (after a short warm-up of each kernel) on the same
+    operator, bounds, probes and order, then mu, Omega, E, N of each.  The FP64 path equals the
+    exact estimator to rounding (its moments agree with the Bloch oracle's to 1e-11 n in the
+    tests), so the mixed path's difference from it is the mixed path's error."""
     import torch
     from paper_1812_05264_gb300 import api
     g = api.build_neighbors(ctx, pos, wk.cutoff, solver.box)
     H = api.assemble_H(ctx, solver.model, pos, g, solver.box)
     emin, emax = api.spectral_bounds(ctx, H)
     p = wk.order or order_rule(emax - emin, wk.kT)
-    out = {}
+    out = {"workload": wk.name, "sites": wk.n_atoms, "orbitals": wk.n_atoms * wk.n_orb,
+           "probes": wk.n_probes, "order_p": p, "recurrence_steps": p // 2,
+           "bounds_eV": [emin, emax]}
     for name, fp64 in (("mixed", False), ("fp64", True)):
         api.chebyshev_moments(ctx, H, emin, emax, wk.probe_seed, wk.n_probes, 8, fp64)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -497,13 +532,14 @@ def precision_compare(args, ctx, solver, wk, pos):
         torch.cuda.synchronize()
         mu, Om, E, N = api.fermi_level(ctx, mom, emin, emax, wk.n_electrons, wk.kT, wk.jackson)
         out[name] = {"ms": e0.elapsed_time(e1), "ms_per_step": e0.elapsed_time(e1) / (p // 2),
-                     "Omega_per_site": Om / wk.n_atoms, "E_per_site": E / wk.n_atoms, "mu": mu}
+                     "mu": mu, "Omega_per_site": Om / wk.n_atoms, "E_per_site": E / wk.n_atoms,
+                     "N_per_site": N / wk.n_atoms}
     out["speedup_mixed_over_fp64"] = out["fp64"]["ms"] / out["mixed"]["ms"]
-    out["energy_diff_per_site"] = abs(out["mixed"]["E_per_site"] - out["fp64"]["E_per_site"])
-    out["omega_diff_per_site"] = abs(out["mixed"]["Omega_per_site"] - out["fp64"]["Omega_per_site"])
-    print(json.dumps({"compare": "mixed_vs_fp64", "workload": wk.name, "order": p,
-                      "probes": wk.n_probes, "sites": wk.n_atoms, **out}))
-    return 0
+    out["energy_diff_per_site_eV"] = abs(out["mixed"]["E_per_site"] - out["fp64"]["E_per_site"])
+    out["omega_diff_per_site_eV"] = abs(out["mixed"]["Omega_per_site"] - out["fp64"]["Omega_per_site"])
+    out["tolerance_per_site_eV"] = 1e-4
+    out["equal_accuracy"] = bool(max(out["energy_diff_per_site_eV"], out["omega_diff_per_site_eV"]) < 1e-4)
+    return out
 
 
 def adjoint_only(args, ctx, solver, wk, pos):
@@ -539,13 +575,26 @@ def run_batched(args, rank, world):
     import torch
     from paper_1812_05264_gb300 import build as _build
     _build.build()
-    from paper_1812_05264_gb300 import api
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     dist = world > 1
     if dist:
         import torch.distributed as td
         td.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    line = batched_line(args.steps, args.warmup, args.adjoint, rank, world, not args.no_clocks)
+    if rank == 0:
+        print(json.dumps(line))
+    if dist:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def batched_line(steps, warmup, adjoint, rank, world, clocks_on=True):
+    """The 64-cluster batch timed over `steps` steps after `warmup`; returns its JSON record."""
+    import torch
+    from paper_1812_05264_gb300 import api
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = world > 1
 
     def barrier():
         if dist:
@@ -583,24 +632,24 @@ def run_batched(args, rank, world):
         _, obs, _, Fs = api.batched_energies_and_forces(ctx, Hs, model, pos, e0, e1, seeds, s, ps,
                                                         [w.n_electrons for w in wks],
                                                         [w.kT for w in wks],
-                                                        windowed=args.adjoint == "windowed")
+                                                        windowed=adjoint == "windowed")
         if record:
             marks.append(ev())
             phase_ev.append((marks, Hs, ps))
         return ps, obs, Fs
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         step(devs)
     torch.cuda.synchronize()
     barrier()
-    clocks = ClockSampler(local, enabled=not args.no_clocks)
+    clocks = ClockSampler(local, enabled=clocks_on)
     clocks.start()
     l0 = ctx.launches
     ctx.time_kernels("step", "backward", "window")
     t0 = torch.cuda.Event(enable_timing=True); t1 = torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     t0.record(ctx.stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         ps, obs, Fs = step(devs, record=True)
     t1.record(ctx.stream)
     torch.cuda.synchronize()
@@ -608,9 +657,9 @@ def run_batched(args, rank, world):
     launches = ctx.launches - l0
     fam = {f: ctx.kernel_time(f) for f in ("step", "backward", "window")}
     ctx.time_kernels()
-    ms = t0.elapsed_time(t1) / args.steps
+    ms = t0.elapsed_time(t1) / steps
     e_ms = []
-    for _ in range(max(1, min(args.steps, 2))):
+    for _ in range(max(1, min(steps, 2))):
         a = torch.cuda.Event(enable_timing=True); b = torch.cuda.Event(enable_timing=True)
         a.record(ctx.stream)
         pe = [h.to(f"cuda:{local}", non_blocking=True) for h in hosts]
@@ -629,7 +678,7 @@ def run_batched(args, rank, world):
         if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     alu = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
-    windowed = args.adjoint == "windowed"
+    windowed = adjoint == "windowed"
     fb = ff = bb = bf = wb = wf = 0.0
     for H, p in zip(Hs, ps_):
         K = p // 2
@@ -649,7 +698,7 @@ def run_batched(args, rank, world):
         tms, nl = fam[f]
         if nl == 0:
             continue
-        sec = tms / 1e3 / args.steps
+        sec = tms / 1e3 / steps
         if fl / (alu * 1e12) >= by / (hbm * 1e9):
             r = {"bound": "alu", "achieved": fl / sec / 1e12, "peak": alu, "unit": "TFLOP/s",
                  "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz (derived, FP32 FMA)"}
@@ -658,19 +707,19 @@ def run_batched(args, rank, world):
                  "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
         r.update(frac=r["achieved"] / r["peak"], kernel=kname, traffic=None,
                  algorithmic_bytes_per_step=by, algorithmic_flops_per_step=fl,
-                 avg_launch_ms=tms / nl, launches_timed=nl, share_of_step=tms / (ms * args.steps))
+                 avg_launch_ms=tms / nl, launches_timed=nl, share_of_step=tms / (ms * steps))
         kernels[f] = r
     dom = max(kernels, key=lambda f: kernels[f]["share_of_step"])
     h2d = sum(h.numel() * 8 for h in hosts)
     d2h = sum(w.n_atoms * 3 * 8 for w in wks)
     line = {"metric": METRIC, "value": job_rate(units, world, ms), "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "steps": steps, "warmup": warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "batched64-fcc-sk9", "clusters": len(wks),
                        "atoms": int(sum(w.n_atoms for w in wks)), "probes": s,
                        "orders_p": [int(p) for p in ps], "kT": [float(w.kT) for w in wks],
                        "l2": "merged panels (%.0f MB each) larger than L2" % (sum(w.n_atoms for w in wks) * 9 * s * 4 / 1e6),
-                       "parallelism": f"replicas x{world}", "adjoint": args.adjoint},
+                       "parallelism": f"replicas x{world}", "adjoint": adjoint},
             "e2e": {"value": job_rate(units, world, e_med), "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches,
@@ -680,11 +729,8 @@ def run_batched(args, rank, world):
                 name: sum(m[i].elapsed_time(m[i + 1]) for m, _, _ in phase_ev) / len(phase_ev)
                 for i, name in enumerate(("neighbours_H_bounds", "energies_and_forces"))},
             "clocks": clk}
-    if rank == 0:
-        print(json.dumps(line))
-    if dist:
-        torch.distributed.destroy_process_group()
-    return 0
+    ctx.close()
+    return line
 
 
 def main():
@@ -708,6 +754,11 @@ def main():
                     help="probe count of the fcc10k workload (default 512; a profiling aid)")
     ap.add_argument("--atom-order", default="radial", choices=["radial", "morton"],
                     help="listing order of the fcc10k atoms (same cluster)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="fcc10k: skip the 48^3 mixed-vs-FP64 record and the 64-cluster batch record")
+    ap.add_argument("--batch-steps", type=int, default=2,
+                    help="timed steps of the 64-cluster batch record in the default line")
+    ap.add_argument("--batch-warmup", type=int, default=3)
     ap.add_argument("--adjoint", default="auto", choices=["auto", "fused", "windowed"],
                     help="outer products inside each backward step, or over windows of 4 steps "
                          "(auto: fused for 512 probes, windowed for the 128-probe batch)")

@@ -357,6 +357,41 @@ int tbk_batched_energies_and_forces(tbk_ctx* ctx, int32_t n_clusters, const tbk_
                                     int32_t flags, int64_t max_panel_bytes, double* moments,
                                     double* observables, double* const* G, double* const* forces);
 
+/* ---- f1: the multi-colour probe ensemble (Sec. II.C.3; colours from Sec. II.E) ----------
+
+   The basis functions are split into colours so that two functions of one colour sit farther
+   apart than a colouring radius: atom a has colour atom_color[a] in [0, n_colors) (e.g. from
+   tbk_welsh_powell on the pattern at that radius) and its orbital o the function colour
+   atom_color[a] * n_orb + o, q = n_colors * n_orb colours in all.  Sample i of the ensemble has q
+   columns: column i q + k is nonzero exactly on the functions of colour k, where its entry is the
+   plain probe sign of (row, i) (the Rademacher entry of tbk_chebyshev_moments for probe i).  The
+   panel has n_columns >= n_samples q columns (a multiple of 4; the ones past n_samples q are zero,
+   so a width of 128, 256 or 512 takes the TMA-fed and fused kernels), and the estimator divides by
+   the number of samples: mu_k = (1/n_samples) sum_columns r^T C_k(H^) r.  Its mean over samples is
+   the trace of C_k(H^); only matrix elements between distinct functions of one colour enter its
+   variance (Eq. sampling_error with the ensemble's deviation matrix).  The probe block is written
+   once into library scratch in the recurrence precision and read where the probe enters.
+   atom_color: device, n_atoms int32; a colour outside [0, n_colors) gives TBK_ERR_ARG. */
+
+/* tbk_colored_moments: the moments of tbk_chebyshev_moments (doubled; flags TBK_MIXED or TBK_FP64,
+   optionally | TBK_PLAIN_KERNEL) for the multi-colour ensemble.  moments: device, order FP64. */
+int tbk_colored_moments(tbk_ctx* ctx, const tbk_bsr* H, double emin, double emax, uint64_t probe_seed,
+                        const int32_t* atom_color, int32_t n_colors, int32_t n_samples, int32_t n_columns,
+                        int32_t order, int32_t flags, double* moments);
+
+/* tbk_colored_energies_and_forces: tbk_energies_and_forces (one call: moments from the adjoint's
+   forward sweep, mu, Omega, E, N, the sampled density matrix G = dOmega^/dH on the pattern and the
+   forces) for the multi-colour ensemble.  Mixed precision with 9x9 blocks and n_columns of 128, 256
+   or 512 (the doubled-moment adjoint); flags 0, TBK_WINDOWED or TBK_FUSED_ADJOINT.  Other
+   arguments and outputs as in tbk_energies_and_forces.  Synchronises the stream. */
+int tbk_colored_energies_and_forces(tbk_ctx* ctx, const tbk_bsr* H, const tbk_model* model,
+                                    const double* pos, const double* box, double emin, double emax,
+                                    uint64_t probe_seed, const int32_t* atom_color, int32_t n_colors,
+                                    int32_t n_samples, int32_t n_columns, int32_t order,
+                                    double n_electrons, double kT, int32_t damping, int32_t flags,
+                                    int64_t max_panel_bytes, double* moments, double* observables,
+                                    double* G, double* forces);
+
 /* ---- allocation-free variant of tbk_chebyshev_moments ------------------------------------
 
    No counterpart in the paper: this entry point exists for callers that cannot allocate device

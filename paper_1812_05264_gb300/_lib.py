@@ -104,6 +104,10 @@ SIGNATURES = {
     "tbk_fermi_level": [_P, _P, _I, _D, _D, _D, _D, _D, _I, C.POINTER(_D)],
     "tbk_density_and_forces": [_P, C.POINTER(tbk_bsr), C.POINTER(tbk_model), _P, _P, _D, _D, _U,
                                _I, _I, _D, _D, _I, _I, _L, _P, _P],
+    "tbk_colored_moments": [_P, C.POINTER(tbk_bsr), _D, _D, _U, _P, _I, _I, _I, _I, _I, _P],
+    "tbk_colored_energies_and_forces": [_P, C.POINTER(tbk_bsr), C.POINTER(tbk_model), _P, _P, _D, _D,
+                                        _U, _P, _I, _I, _I, _I, _D, _D, _I, _I, _L, _P,
+                                        C.POINTER(_D), _P, _P],
 }
 OTHER = {"tbk_last_error": ([], C.c_char_p), "tbk_launch_count": ([_P], C.c_int64)}
 

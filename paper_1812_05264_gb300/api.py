@@ -187,6 +187,51 @@ def atom_colors(ctx: Context, pos: torch.Tensor, r_color: float, box=None) -> tu
     return welsh_powell(g.row_ptr.cpu().numpy(), g.col.cpu().numpy())
 
 
+def colored_columns(n_colors: int, n_orb: int, n_samples: int = 1) -> int:
+    """Panel width for the multi-colour ensemble: n_samples * n_colors * n_orb columns, rounded up
+    to a multiple of 128 (the width the TMA-fed and fused kernels take) up to 512, else to 4."""
+    need = n_samples * n_colors * n_orb
+    for w in (128, 256, 512):
+        if need <= w:
+            return w
+    return (need + 3) // 4 * 4
+
+
+def colored_moments(ctx: Context, H: BSR, emin: float, emax: float, seed: int, atom_color,
+                    n_colors: int, n_samples: int, n_columns: int, order: int,
+                    fp64: bool = False, plain: bool = False) -> torch.Tensor:
+    """f1: moments of the multi-colour probe ensemble (Sec. II.C.3), divided by n_samples."""
+    col = torch.as_tensor(np.ascontiguousarray(atom_color), dtype=torch.int32, device=H.val.device)
+    out = torch.empty(order, dtype=torch.float64, device=H.val.device)
+    flags = (L.TBK_FP64 if fp64 else L.TBK_MIXED) | (L.TBK_PLAIN_KERNEL if plain else 0)
+    L.call("tbk_colored_moments", ctx.handle, C.byref(H.struct()), emin, emax, C.c_uint64(seed),
+           _ptr(col), int(n_colors), int(n_samples), int(n_columns), int(order), flags, _ptr(out))
+    return out
+
+
+def colored_energies_and_forces(ctx: Context, H: BSR, model: Model, pos: torch.Tensor, box,
+                                emin: float, emax: float, seed: int, atom_color, n_colors: int,
+                                n_samples: int, n_columns: int, order: int, n_electrons: float,
+                                kT: float, jackson: bool = False, want_G: bool = False,
+                                want_forces: bool = True, max_panel_bytes: int = 0,
+                                windowed: bool | None = None):
+    """f1, a5-a10 in one call for the multi-colour ensemble: (moments, (mu, Omega, E, N), G or
+    None, forces or None)."""
+    dev = H.val.device
+    col = torch.as_tensor(np.ascontiguousarray(atom_color), dtype=torch.int32, device=dev)
+    mom = torch.empty(order, dtype=torch.float64, device=dev)
+    G = torch.empty_like(H.val) if want_G else None
+    F = torch.empty((H.graph.n_atoms, 3), dtype=torch.float64, device=dev) if want_forces else None
+    obs = (C.c_double * 4)()
+    _keep, bx = _box_arg(box)
+    L.call("tbk_colored_energies_and_forces", ctx.handle, C.byref(H.struct()),
+           C.byref(model.s) if model is not None else None, _ptr(pos), bx, emin, emax,
+           C.c_uint64(seed), _ptr(col), int(n_colors), int(n_samples), int(n_columns), int(order),
+           float(n_electrons), float(kT), L.TBK_DAMP_JACKSON if jackson else L.TBK_DAMP_NONE,
+           _schedule_flag(windowed), int(max_panel_bytes), _ptr(mom), obs, _ptr(G), _ptr(F))
+    return mom, tuple(obs[:]), G, F
+
+
 def batched_build_neighbors(ctx: Context, positions: list, cutoff: float) -> list:
     """a1 for many open clusters in one call: the patterns of build_neighbors, cluster by
     cluster, with every pass run once over all the clusters' atoms."""

@@ -991,7 +991,12 @@ __global__ void ybar_init(int64_t n, int s, float ca, const float* __restrict__ 
 // so the caller can finish the moments, solve for mu and return the coefficients c_0 .. c_{p-1}).
 void adjoint_doubling(tbk_ctx* ctx, const HOp& op, uint64_t probe_seed, int s, int p,
                       const std::function<std::vector<double>()>& get_coefs, double* partials, int nctas,
-                      int64_t max_panel_bytes, double* Gacc, int* err, bool windowed, const AdjBatch* bt) {
+                      int64_t max_panel_bytes, double* Gacc, int* err, bool windowed, const AdjBatch* bt,
+                      const void* probe_panel, int s_norm) {
+  TBK_CHECK_ARG(!(bt && probe_panel), "a batch regenerates its probes");
+  // a stored probe block y_0 (single system): read wherever the probe enters
+  const bool r_panel = probe_panel != nullptr;
+  const double nrm = r_panel && s_norm > 0 ? s_norm : s;
   const int K = bt ? (bt->K.empty() ? 0 : bt->K[0]) : p / 2;
   if (K < 1) {
     if (get_coefs) get_coefs();
@@ -1018,9 +1023,9 @@ void adjoint_doubling(tbk_ctx* ctx, const HOp& op, uint64_t probe_seed, int s, i
     v[1] = p > 1 ? c[1] : 0.0;
     for (int k = 2; 2 * k - 1 < p; ++k) v[1] -= c[2 * k - 1];
   };
-  auto ca = [&](int k) { return (float)(2.0 * w[k] / s); };
-  auto cb = [&](int k) { return (float)(v[k] / s); };
-  auto cc = [&](int k) { return (float)(v[k + 1] / s); };
+  auto ca = [&](int k) { return (float)(2.0 * w[k] / nrm); };
+  auto cb = [&](int k) { return (float)(v[k] / nrm); };
+  auto cc = [&](int k) { return (float)(v[k + 1] / nrm); };
 
   const size_t panel = (size_t)op.n_rows * s * 4;
   size_t budget = max_panel_bytes > 0 ? (size_t)max_panel_bytes : panel_budget(ctx, WS_CHECKPOINTS);
@@ -1090,7 +1095,7 @@ void adjoint_doubling(tbk_ctx* ctx, const HOp& op, uint64_t probe_seed, int s, i
   auto CK = [&](int sg, int which) { return P(n_seg_pan + 2 * (size_t)sg + which); };
   void* E = P(n_seg_pan + n_ckpt);
   auto YB = [&](int j) { return P(n_seg_pan + n_ckpt + 1 + (size_t)(j % NB)); };
-  void* R0 = bt ? P(n_seg_pan + n_ckpt + 1 + NB) : nullptr;
+  void* R0 = bt ? P(n_seg_pan + n_ckpt + 1 + NB) : const_cast<void*>(probe_panel);
   const BatchRows br = bt ? bt->br : BatchRows();
   if (bt) {
     // the probe block of every cluster, and ybar = 0 on the rows of clusters not yet started
@@ -1106,10 +1111,10 @@ void adjoint_doubling(tbk_ctx* ctx, const HOp& op, uint64_t probe_seed, int s, i
     a.seed = probe_seed;
     a.s = s;
     a.yin = t == 1 ? R0 : yin;
-    a.cur_is_probe = t == 1 && !bt;
+    a.cur_is_probe = t == 1 && !bt && !r_panel;
     a.alpha = t == 1 ? 1.0 : 2.0;
     if (t == 2) {
-      if (bt) a.yprev = R0; else a.c_r = -1.0;
+      if (bt || r_panel) a.yprev = R0; else a.c_r = -1.0;
     } else if (t >= 3) {
       a.yprev = const_cast<void*>(yprev);
     }
@@ -1164,9 +1169,9 @@ void adjoint_doubling(tbk_ctx* ctx, const HOp& op, uint64_t probe_seed, int s, i
       }
     }
     if (!have_coefs) load_coefs();
-    // y_j for j in [t0 - 1, t1 + 1] (nullptr = the probe block r = y_0)
+    // y_j for j in [t0 - 1, t1 + 1] (nullptr = the probe block r = y_0, regenerated in the kernels)
     auto Y = [&](int j) -> const void* {
-      if (j == 0) return nullptr;
+      if (j == 0) return r_panel ? R0 : nullptr;
       if (j == t1 + 1) return E;
       return P(j - t0 + 1);
     };
@@ -1183,11 +1188,14 @@ void adjoint_doubling(tbk_ctx* ctx, const HOp& op, uint64_t probe_seed, int s, i
       }
       if (k >= 1) {
         // ybar_k = g_k + 2 H^ ybar_{k+1} - ybar_{k+2}; fused: and G += 2 y_k ybar_{k+1}^T on the pattern
+        // (the probe coefficient .x scales the regenerated y_0; a stored y_0 streams as y_{k-1})
+        const bool r_gen = k == 1 && !r_panel;
         const float4 cf = bt ? make_float4(0.f, 0.f, 0.f, 0.f)
-                             : make_float4(k == 1 ? cb(1) : 0.f, ca(k), k == 1 ? 0.f : cb(k), cc(k));
+                             : make_float4(r_gen ? cb(1) : 0.f, ca(k), r_gen ? 0.f : cb(k), cc(k));
         const float4* cfk = bt ? bt->cft + (size_t)k * bt->K.size() : nullptr;
         launch_fused(ctx, o, YB(k + 1), (k + 2 <= K || bt) ? YB(k + 2) : nullptr, YB(k), Y(k), cf, probe_seed, s,
-                     2.0, windowed ? nullptr : Gacc, err, br, cfk, k >= 2 ? Y(k - 1) : nullptr, Y(k + 1));
+                     2.0, windowed ? nullptr : Gacc, err, br, cfk, (k >= 2 || r_panel) ? Y(k - 1) : nullptr,
+                     Y(k + 1));
         if (windowed && (k - 1) % SDW == 0) {
           // G += 2 y_j ybar_{j+1}^T on the pattern for the window j = k .. min(k + SDW, K) - 1
           WindowPanels wp{};
@@ -1201,11 +1209,11 @@ void adjoint_doubling(tbk_ctx* ctx, const HOp& op, uint64_t probe_seed, int s, i
       } else if (windowed) {
         // G += y_0 ybar_1^T
         WindowPanels wp{};
-        wp.y[0] = nullptr;
+        wp.y[0] = (const float*)Y(0);
         wp.x[0] = (const float*)YB(1);
         launch_window(ctx, o, wp, 1, probe_seed, s, 1.0, Gacc, err, br, bt ? bt->d_K : nullptr, 0);
       } else {
-        launch_fused(ctx, o, YB(1), nullptr, nullptr, nullptr, make_float4(0.f, 0.f, 0.f, 0.f), probe_seed, s,
+        launch_fused(ctx, o, YB(1), nullptr, nullptr, Y(0), make_float4(0.f, 0.f, 0.f, 0.f), probe_seed, s,
                      1.0, Gacc, err, br, nullptr, nullptr, nullptr);
       }
     }
@@ -1411,6 +1419,90 @@ void fermi_enqueue(tbk_ctx* ctx, const double* moments, int order, double emin, 
 int quad_nodes(int p);
 }  // namespace tbk
 
+namespace tbk {
+// The one-call energies and forces on the doubled-moment adjoint (fused-eligible shapes): the
+// adjoint's forward sweep over y_1 .. y_{p/2} also yields the moments, so no separate moment pass
+// runs.  probe_panel / s_norm: a stored probe block and its sample count (NULL / 0: the
+// Rademacher probes regenerated from probe_seed, s of them).
+void energies_and_forces_doubled(tbk_ctx* ctx, const tbk_bsr* H, const tbk_model* model, const double* pos,
+                                 const double* box, double emin, double emax, uint64_t probe_seed, int s,
+                                 int order, double n_electrons, double kT, int damping, int flags,
+                                 int64_t max_panel_bytes, double* moments, double* observables, double* G,
+                                 double* forces, const void* probe_panel, int s_norm) {
+  const int prec = (flags & TBK_FP64) ? TBK_FP64 : TBK_MIXED;
+  DevModel M{};
+  if (forces) {
+    M = upload_model(ctx, model, box, WS_TABLE);
+    TBK_CHECK_ARG(M.kind == TBK_MODEL_SK, "forces need the Slater-Koster model");
+    TBK_CHECK_ARG(pos != nullptr, "pos is NULL");
+  }
+  // err: bit 4 = a row has no diagonal block, bit 2 = a bounded wait expired, bit 1 = the pattern
+  // is not symmetric; err[1] bit 1 = a panel outgrew ||r|| (the spectrum is not inside [emin, emax])
+  int* err = (int*)scratch(ctx, WS_FLAGS, 64);
+  TBK_CUDA(cudaMemsetAsync(err, 0, 2 * sizeof(int), ctx->stream));
+  HOp op = prepare_hop(ctx, H, emin, emax, prec, WS_HHAT, err);
+  const int p = order, BB = op.B * op.B;
+  const int nrm = probe_panel && s_norm > 0 ? s_norm : s;
+  const double W = emax - emin;
+  int32_t* tr = (int32_t*)scratch(ctx, WS_TRANSPOSE, sizeof(int32_t) * (size_t)op.nnzb);
+  launch_transpose_map(ctx, op.n_atoms, op.row_ptr, op.col, tr, err);
+  double* Gacc = (double*)scratch(ctx, WS_GACC, sizeof(double) * (size_t)op.nnzb * BB * 2);
+  double* Gsym = Gacc + (size_t)op.nnzb * BB;
+  TBK_CUDA(cudaMemsetAsync(Gacc, 0, sizeof(double) * (size_t)op.nnzb * BB, ctx->stream));
+  const int K = p / 2;
+  const int nctas = step_grid_ctas(ctx, op, s);
+  double* partials = (double*)scratch(ctx, WS_PARTIALS, sizeof(double) * 2 * (size_t)std::max(1, K) * nctas);
+  const int M_nodes = quad_nodes(p);
+  double* fbuf = (double*)scratch(ctx, WS_SEGMENT, sizeof(double) * ((size_t)2 * K + 64 + 5 * (size_t)M_nodes + 16 +
+                                                                     (size_t)p + 8));
+  double* sums = fbuf;
+  double* tab = sums + 2 * (size_t)K + 64;
+  double* rho = tab + 4 * (size_t)M_nodes;
+  double* res = rho + M_nodes;
+  double* mom = moments ? moments : res + 16;
+  double* dcoef = (double*)scratch(ctx, WS_COEF, sizeof(double) * (size_t)p);
+  auto after_forward = [&]() {
+    // moments from the doubling identities, then mu, Omega, E, N, then c_k = d_k beta_k[g](mu)
+    launch_moment_reduction(ctx, partials, nctas, K, p, nrm, op.n_rows, 0, sums, mom, err + 1);
+    fermi_enqueue(ctx, mom, p, emin, emax, n_electrons, 0.0, kT, damping, tab, rho, res);
+    double h[5];
+    int herr[2] = {0, 0};
+    TBK_CUDA(cudaMemcpyAsync(h, res, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
+    TBK_CUDA(cudaMemcpyAsync(herr, err, sizeof(herr), cudaMemcpyDeviceToHost, ctx->stream));
+    sync(ctx);
+    check_diagonal_flag(herr[0]);
+    if ((herr[0] | herr[1]) & 2) throw Error(TBK_ERR_TIMEOUT, "a bounded wait in the recurrence kernel expired");
+    TBK_CHECK_ARG(herr[0] == 0, "the block pattern is not symmetric");
+    if (herr[1])
+      throw Error(TBK_ERR_SPECTRUM, "a Chebyshev panel grew beyond ||r||: the spectrum of H is not "
+                                    "inside [emin, emax]");
+    if (h[4] != 0.0) throw Error(TBK_ERR_NOCONV, "n_electrons is outside the range of the estimated N(mu)");
+    for (int i = 0; i < 4; ++i) observables[i] = h[i];
+    coefficients(ctx, TBK_FN_FREE, p, emin, emax, h[0], kT, damping, dcoef);
+    std::vector<double> c(p);
+    TBK_CUDA(cudaMemcpyAsync(c.data(), dcoef, sizeof(double) * p, cudaMemcpyDeviceToHost, ctx->stream));
+    sync(ctx);
+    return c;
+  };
+  adjoint_doubling(ctx, op, probe_seed, s, p, after_forward, partials, nctas, max_panel_bytes, Gacc, err,
+                   windowed_schedule(ctx, op, s, flags), nullptr, probe_panel, s_norm);
+  double* Gout = G ? G : Gsym;
+  const int64_t tot = op.nnzb * BB;
+  symmetrize<9><<<(unsigned)((tot + 255) / 256), 256, 0, ctx->stream>>>(op.nnzb, tr, Gacc, 2.0 / W, Gout);
+  post_launch(ctx, "symmetrize");
+  if (forces) {
+    double* tq = (double*)scratch(ctx, WS_MISC, sizeof(double) * 3 * (size_t)op.nnzb);
+    launch_forces(ctx, M, pos, op.n_atoms, op.row_ptr, op.col, tr, Gout, tq, forces);
+  }
+  int herr = 0;
+  TBK_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  sync(ctx);
+  check_diagonal_flag(herr);
+  if (herr & 2) throw Error(TBK_ERR_TIMEOUT, "a bounded wait in the recurrence kernel expired");
+  TBK_CHECK_ARG(herr == 0, "the block pattern is not symmetric");
+}
+}  // namespace tbk
+
 // Energies and forces in one call: the adjoint's forward sweep over y_1 .. y_{p/2} also yields
 // the (doubled) moments, so no separate moment pass is run.
 extern "C" int tbk_energies_and_forces(tbk_ctx* ctx, const tbk_bsr* H, const tbk_model* model,
@@ -1447,74 +1539,7 @@ extern "C" int tbk_energies_and_forces(tbk_ctx* ctx, const tbk_bsr* H, const tbk
     }
     return TBK_OK;
   }
-  DevModel M{};
-  if (forces) {
-    M = upload_model(ctx, model, box, WS_TABLE);
-    TBK_CHECK_ARG(M.kind == TBK_MODEL_SK, "forces need the Slater-Koster model");
-    TBK_CHECK_ARG(pos != nullptr, "pos is NULL");
-  }
-  // err: bit 4 = a row has no diagonal block, bit 2 = a bounded wait expired, bit 1 = the pattern
-  // is not symmetric; err[1] bit 1 = a panel outgrew ||r|| (the spectrum is not inside [emin, emax])
-  int* err = (int*)scratch(ctx, WS_FLAGS, 64);
-  TBK_CUDA(cudaMemsetAsync(err, 0, 2 * sizeof(int), ctx->stream));
-  HOp op = prepare_hop(ctx, H, emin, emax, prec, WS_HHAT, err);
-  const int p = order, s = n_probes, BB = op.B * op.B;
-  const double W = emax - emin;
-  int32_t* tr = (int32_t*)scratch(ctx, WS_TRANSPOSE, sizeof(int32_t) * (size_t)op.nnzb);
-  launch_transpose_map(ctx, op.n_atoms, op.row_ptr, op.col, tr, err);
-  double* Gacc = (double*)scratch(ctx, WS_GACC, sizeof(double) * (size_t)op.nnzb * BB * 2);
-  double* Gsym = Gacc + (size_t)op.nnzb * BB;
-  TBK_CUDA(cudaMemsetAsync(Gacc, 0, sizeof(double) * (size_t)op.nnzb * BB, ctx->stream));
-  const int K = p / 2;
-  const int nctas = step_grid_ctas(ctx, op, s);
-  double* partials = (double*)scratch(ctx, WS_PARTIALS, sizeof(double) * 2 * (size_t)std::max(1, K) * nctas);
-  const int M_nodes = quad_nodes(p);
-  double* fbuf = (double*)scratch(ctx, WS_SEGMENT, sizeof(double) * ((size_t)2 * K + 64 + 5 * (size_t)M_nodes + 16 +
-                                                                     (size_t)p + 8));
-  double* sums = fbuf;
-  double* tab = sums + 2 * (size_t)K + 64;
-  double* rho = tab + 4 * (size_t)M_nodes;
-  double* res = rho + M_nodes;
-  double* mom = moments ? moments : res + 16;
-  double* dcoef = (double*)scratch(ctx, WS_COEF, sizeof(double) * (size_t)p);
-  auto after_forward = [&]() {
-    // moments from the doubling identities, then mu, Omega, E, N, then c_k = d_k beta_k[g](mu)
-    launch_moment_reduction(ctx, partials, nctas, K, p, s, op.n_rows, 0, sums, mom, err + 1);
-    fermi_enqueue(ctx, mom, p, emin, emax, n_electrons, 0.0, kT, damping, tab, rho, res);
-    double h[5];
-    int herr[2] = {0, 0};
-    TBK_CUDA(cudaMemcpyAsync(h, res, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
-    TBK_CUDA(cudaMemcpyAsync(herr, err, sizeof(herr), cudaMemcpyDeviceToHost, ctx->stream));
-    sync(ctx);
-    check_diagonal_flag(herr[0]);
-    if ((herr[0] | herr[1]) & 2) throw Error(TBK_ERR_TIMEOUT, "a bounded wait in the recurrence kernel expired");
-    TBK_CHECK_ARG(herr[0] == 0, "the block pattern is not symmetric");
-    if (herr[1])
-      throw Error(TBK_ERR_SPECTRUM, "a Chebyshev panel grew beyond ||r||: the spectrum of H is not "
-                                    "inside [emin, emax]");
-    if (h[4] != 0.0) throw Error(TBK_ERR_NOCONV, "n_electrons is outside the range of the estimated N(mu)");
-    for (int i = 0; i < 4; ++i) observables[i] = h[i];
-    coefficients(ctx, TBK_FN_FREE, p, emin, emax, h[0], kT, damping, dcoef);
-    std::vector<double> c(p);
-    TBK_CUDA(cudaMemcpyAsync(c.data(), dcoef, sizeof(double) * p, cudaMemcpyDeviceToHost, ctx->stream));
-    sync(ctx);
-    return c;
-  };
-  adjoint_doubling(ctx, op, probe_seed, s, p, after_forward, partials, nctas, max_panel_bytes, Gacc, err,
-                   windowed_schedule(ctx, op, s, flags), nullptr);
-  double* Gout = G ? G : Gsym;
-  const int64_t tot = op.nnzb * BB;
-  symmetrize<9><<<(unsigned)((tot + 255) / 256), 256, 0, ctx->stream>>>(op.nnzb, tr, Gacc, 2.0 / W, Gout);
-  post_launch(ctx, "symmetrize");
-  if (forces) {
-    double* tq = (double*)scratch(ctx, WS_MISC, sizeof(double) * 3 * (size_t)op.nnzb);
-    launch_forces(ctx, M, pos, op.n_atoms, op.row_ptr, op.col, tr, Gout, tq, forces);
-  }
-  int herr = 0;
-  TBK_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
-  sync(ctx);
-  check_diagonal_flag(herr);
-  if (herr & 2) throw Error(TBK_ERR_TIMEOUT, "a bounded wait in the recurrence kernel expired");
-  TBK_CHECK_ARG(herr == 0, "the block pattern is not symmetric");
+  energies_and_forces_doubled(ctx, H, model, pos, box, emin, emax, probe_seed, n_probes, order, n_electrons,
+                              kT, damping, flags, max_panel_bytes, moments, observables, G, forces, nullptr, 0);
   TBK_API_END
 }

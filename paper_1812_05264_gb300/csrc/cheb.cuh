@@ -108,9 +108,27 @@ struct AdjBatch {
 // gives the per-cluster tables; p is unused; get_coefs, when given, is called once the forward
 // sweep is done and fills bt->cft (its return value is ignored); partials, when given, receive
 // per (atom, warp) sums of every forward step at partials + (t - 1) bt->pstride.
+// probe_panel (single system only): the probe block y_0 stored as a panel (s columns) instead of
+// regenerated from the seed, for probe ensembles other than plain Rademacher signs; s_norm: the
+// number of samples the estimator divides by (0 = s).
 void adjoint_doubling(tbk_ctx* ctx, const HOp& op, uint64_t probe_seed, int s, int p,
                       const std::function<std::vector<double>()>& get_coefs, double* partials, int nctas,
-                      int64_t max_panel_bytes, double* Gacc, int* err, bool windowed, const AdjBatch* bt);
+                      int64_t max_panel_bytes, double* Gacc, int* err, bool windowed, const AdjBatch* bt,
+                      const void* probe_panel = nullptr, int s_norm = 0);
+// The moments sweep of tbk_chebyshev_moments (per_probe: also each probe's moments).  With
+// probe_panel the probe block y_0 is read from that panel (s columns, the precision of the
+// recurrence) and the moments divide by s_norm samples; flags may not ask for direct moments then.
+void moments_sweep(tbk_ctx* ctx, const tbk_bsr* H, double emin, double emax, uint64_t probe_seed,
+                   int32_t n_probes, int32_t order, int32_t flags, double* moments, double* per_probe,
+                   const void* probe_panel = nullptr, int s_norm = 0);
+// The one-call energies and forces of the doubled-moment adjoint (mixed, 9x9, s = 128/256/512),
+// with the probe block regenerated from probe_seed or read from probe_panel (s_norm samples).
+void energies_and_forces_doubled(tbk_ctx* ctx, const tbk_bsr* H, const tbk_model* model, const double* pos,
+                                 const double* box, double emin, double emax, uint64_t probe_seed, int s,
+                                 int order, double n_electrons, double kT, int damping, int flags,
+                                 int64_t max_panel_bytes, double* moments, double* observables, double* G,
+                                 double* forces, const void* probe_panel, int s_norm);
+bool fused_eligible(const HOp& op, int s, int plain);
 void launch_batch_probe_panel(tbk_ctx* ctx, const HOp& op, const BatchRows& br, int s, void* out);
 
 }  // namespace tbk

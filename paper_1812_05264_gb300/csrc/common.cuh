@@ -38,7 +38,7 @@ void set_error(const char* msg);
 enum Slot {
   WS_PANEL0 = 0, WS_PANEL1, WS_PANEL2, WS_PANEL3, WS_HHAT, WS_PARTIALS, WS_FLAGS, WS_COEF,
   WS_TABLE, WS_NODES, WS_CELLS, WS_CELLS2, WS_CELLS3, WS_LANCZOS, WS_GACC, WS_TRANSPOSE,
-  WS_CHECKPOINTS, WS_SEGMENT, WS_MISC, WS_NSLOTS
+  WS_CHECKPOINTS, WS_SEGMENT, WS_MISC, WS_PROBES, WS_NSLOTS
 };
 
 }  // namespace tbk

@@ -1027,15 +1027,19 @@ using namespace tbk;
 
 namespace tbk {
 // The moments sweep of tbk_chebyshev_moments; with per_probe, every step is followed by the
-// per-probe dot products of its panels.
-static void moments_sweep(tbk_ctx* ctx, const tbk_bsr* H, double emin, double emax, uint64_t probe_seed,
-                          int32_t n_probes, int32_t order, int32_t flags, double* moments, double* per_probe) {
+// per-probe dot products of its panels.  With probe_panel the probe block y_0 is that panel (the
+// first step reads it as its source, the second as its y_{j-1}) and the moments divide by s_norm.
+void moments_sweep(tbk_ctx* ctx, const tbk_bsr* H, double emin, double emax, uint64_t probe_seed,
+                   int32_t n_probes, int32_t order, int32_t flags, double* moments, double* per_probe,
+                   const void* probe_panel, int s_norm) {
   TBK_CHECK_ARG(order >= 1, "order must be >= 1");
   TBK_CHECK_ARG(n_probes >= 4 && n_probes % 4 == 0, "n_probes must be a positive multiple of 4");
   TBK_CHECK_ARG((flags & ~(TBK_FP64 | TBK_MOMENTS_DIRECT | TBK_PLAIN_KERNEL | TBK_TENSOR_CORES)) == 0,
                 "unknown flag");
   const int prec = (flags & TBK_FP64) ? TBK_FP64 : TBK_MIXED;
   const int direct = (flags & TBK_MOMENTS_DIRECT) ? 1 : 0;
+  TBK_CHECK_ARG(!probe_panel || (!direct && !per_probe), "a stored probe block takes doubled moments only");
+  const int nrm = probe_panel && s_norm > 0 ? s_norm : n_probes;
   int* flag = (int*)scratch(ctx, WS_FLAGS, 64);
   TBK_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), ctx->stream));
   HOp op = prepare_hop(ctx, H, emin, emax, prec, WS_HHAT, flag);
@@ -1065,14 +1069,15 @@ static void moments_sweep(tbk_ctx* ctx, const tbk_bsr* H, double emin, double em
     a.force_simple = (flags & TBK_PLAIN_KERNEL) ? 1 : 0;
     a.use_tc = (flags & TBK_TENSOR_CORES) ? 1 : 0;
     if (j == 1) {
-      a.cur_is_probe = 1;
+      a.cur_is_probe = probe_panel ? 0 : 1;
+      a.yin = probe_panel;
       a.alpha = 1.0;
       a.yout = A;
       cur = A;
     } else if (j == 2) {
       a.yin = A;
       a.alpha = 2.0;
-      a.c_r = -1.0;
+      if (probe_panel) a.yprev = const_cast<void*>(probe_panel); else a.c_r = -1.0;
       a.yout = Bp;
       prev = A;
       cur = Bp;
@@ -1102,7 +1107,7 @@ static void moments_sweep(tbk_ctx* ctx, const tbk_bsr* H, double emin, double em
     reduce_partials<<<K, 256, 0, ctx->stream>>>(partials, nctas, sums);
     post_launch(ctx, "reduce_partials");
   }
-  finish_moments<<<1, 256, 0, ctx->stream>>>(sums, K, order, s, op.n_rows, direct, moments, flag);
+  finish_moments<<<1, 256, 0, ctx->stream>>>(sums, K, order, nrm, op.n_rows, direct, moments, flag);
   post_launch(ctx, "finish_moments");
   if (per_probe) {
     const int64_t n = (int64_t)order * s;

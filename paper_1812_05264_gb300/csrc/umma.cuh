@@ -1,0 +1,99 @@
+// Tensor-core building blocks for sm_100-family GPUs (tcgen05 + TMA), written from the PTX ISA's
+// descriptions of the instructions and of their operand formats:
+//  - 2-D tiled TMA loads (cp.async.bulk.tensor) from a CUtensorMap passed as a __grid_constant__
+//    kernel parameter, completing on an mbarrier;
+//  - shared-memory matrix descriptors of K-major operands in the 128-byte-swizzle layout (8-row
+//    groups of 128-byte rows, 1024 bytes apart; the XOR swizzle of 16-byte chunks by row follows
+//    the shared-memory address, so each group must start 1024-byte aligned);
+//  - the kind::tf32 instruction descriptor (FP32 accumulator, K-major A and B);
+//  - TMEM allocation, MMA issue and commit, and 32-lane TMEM loads.
+#pragma once
+#include <cuda.h>
+#include <stdint.h>
+
+#include "bulk.cuh"
+
+namespace tbk {
+
+// ---- host: tensor maps ----------------------------------------------------------------------
+
+// A 2-D FP32 tensor map over a row-major matrix (rows x cols, row stride ld floats) with boxes of
+// box_rows x box_cols, in the 128-byte swizzle (box_cols = 32) or without swizzle; out-of-range
+// elements of a box read as zero.  Throws on failure.
+void make_tmap_2d(CUtensorMap* map, const float* base, int64_t rows, int64_t cols, int64_t ld,
+                  int box_rows, int box_cols, bool swizzle128);
+
+// ---- device ------------------------------------------------------------------------------
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+      ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+// K-major operand in the 128-byte swizzle: start address (1024-byte aligned group base plus the
+// K offset inside the 128-byte row), stride between 8-row groups sbo (bytes), descriptor version 1,
+// layout type 2 (128-byte swizzle).  The leading-dimension offset is unused for this layout (1).
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t addr, uint32_t sbo) {
+  return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)1 << 16) | ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+// Instruction descriptor of kind::tf32: D FP32 (bits 4-5 = 1), A and B TF32 (bits 7-9, 10-12 = 2),
+// both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t tf32_idesc(int M, int N) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// D[tmem] (+)= A[smem desc] x B[smem desc]^T, one thread issues.
+__device__ __forceinline__ void umma_tf32(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                          uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate));
+}
+
+// Arrive on an mbarrier once every MMA this thread issued before has completed.
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t slot_smem, uint32_t cols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot_smem), "r"(cols));
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t tm, uint32_t cols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tm), "r"(cols));
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// 16 consecutive 32-bit TMEM columns of this warp's 32 lanes (lane = thread), then wait.
+__device__ __forceinline__ void tmem_ld16(uint32_t addr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(addr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// The TF32 head of an FP32 word as the tensor core reads it (the 13 low mantissa bits cleared) and
+// the remainder x - head, exact in FP32.
+__device__ __forceinline__ float tf32_rest(float x) {
+  return x - __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
+}
+
+// Byte offset of element (row r, column k) of a 128-byte-swizzle tile of 32 FP32 columns whose
+// 8-row groups are 1024 bytes apart: the 16-byte chunk index is XORed with r mod 8.
+__device__ __forceinline__ uint32_t sw128_offset(int r, int k) {
+  return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((((k >> 2) ^ (r & 7)) & 7) << 4) + (k & 3) * 4);
+}
+
+}  // namespace tbk

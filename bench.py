@@ -15,8 +15,9 @@ and forces).  Every launch of the three kernel families of the path (recurrence 
 step, windowed outer products) is bracketed by CUDA events inside the timed steps; `kernels`
 gives each family's roofline (HBM bytes or FP32 FMA flops, whichever bounds it) and `roofline`
 repeats the one with the largest share of the step.  `cpu_baseline` times the FP64 oracle on a
-bounded sub-cluster.  Two more measured configurations ride along in the same line (single GPU,
-after the main workload's memory is given back): `fp64_compare`, the 48^3 periodic 9-orbital
+bounded sub-cluster.  More measured records ride along in the same line (single GPU, after the
+main workload's memory is given back): `colored_sigma`, the sampling error of Omega^ for plain
+probes and for the multi-colour ensemble at a 6 A colouring radius at equal columns; `fp64_compare`, the 48^3 periodic 9-orbital
 lattice (1.0M orbitals, 10 eV band, kT = 0.05 eV, 512 probes) run whole by the mixed path and by
 the plain FP64 GPU path, with both times, both results and the speed-up at equal accuracy; and
 `batched64`, the 64-cluster batch (energies and forces of every cluster per step) with its own
@@ -286,7 +287,7 @@ def run_ours(args, rank, world):
             ctx, H, solver.model if solver.model.is_sk else None, p_dev, box, emin, emax,
             wk.probe_seed, wk.n_probes, p, wk.n_electrons, wk.kT, wk.jackson, fp64,
             want_G=not solver.model.is_sk, want_forces=solver.model.is_sk,
-            windowed={"auto": None, "fused": False, "windowed": True}[args.adjoint])
+            windowed=None if args.adjoint == "auto" else args.adjoint)
         return p, obs, F, H.graph.nnzb
 
     if args.only_moments:
@@ -358,12 +359,15 @@ def run_ours(args, rank, world):
     nwin = (K - 1 + 3) // 4 + 1 if K >= 1 else 0
     # algorithmic bytes and flops (2 per FMA) of each family over the timed steps
     hb, blk = nnzb * B2 * esz, 2 * nnzb * B2 * wk.n_probes
-    windowed = args.adjoint == "windowed" or (args.adjoint == "auto" and bool(tuned and tuned[1]))
+    sched = args.adjoint if args.adjoint != "auto" else (tuned[1] if tuned else "fused")
+    windowed = sched == "windowed"
+    tensor = sched == "tensor"
     # the kernels that ran: 128-probe tasks take the self-fed kernels; the profiles under
     # profiles/ are of the TMA-fed step and the fused adjoint step
     chunk = tuned[0] if tuned else wk.n_probes
     step_k = "cheb_step_self" if chunk == 128 or wk.n_probes == 128 else "cheb_step_bulk"
-    bwd_k = "clenshaw_self" if windowed and wk.n_probes == 128 else "clenshaw_sddmm_bulk"
+    bwd_k = "clenshaw_self" if sched != "fused" and wk.n_probes == 128 else "clenshaw_sddmm_bulk"
+    alone = sched != "fused"     # the backward step without its outer products
     alg = {
         # y_{k+1} = 2 H^ y_k - y_{k-1}: reads y_k, y_{k-1}, the H^ blocks, writes y_{k+1}
         "step": (lambda n: n * (3 * panel + hb), lambda n: n * blk, step_k,
@@ -371,14 +375,17 @@ def run_ours(args, rank, world):
         # ybar_k = g_k + 2 H^ ybar_{k+1} - ybar_{k+2}: reads ybar_{k+1}, ybar_{k+2}, y_k, y_{k-1},
         # y_{k+1}, the H^ blocks, writes ybar_k; fused: and G += 2 y_k ybar_{k+1}^T (the same
         # tiles, as many FMAs again, the FP64 accumulator read and written once)
-        "backward": (lambda n: n * (6 * panel + hb + (0 if windowed else nnzb * B2 * 16)),
-                     lambda n: n * blk * (1 if windowed else 2), bwd_k,
-                     None if windowed else "clenshaw_sddmm_bulk_fcc10000.md", "adjoint.cu"),
-        # G += sum_j y_j ybar_{j+1}^T (j = 0 .. K-1, K pairs a step): reads both panels of every
-        # pair, reads and writes the FP64 accumulator once per window
-        "window": (lambda n: args.steps * (K * 2 * panel + nwin * nnzb * B2 * 16),
-                   lambda n: args.steps * K * blk,
-                   "sddmm_window_g", None, "adjoint.cu"),
+        "backward": (lambda n: n * (6 * panel + hb + (0 if alone else nnzb * B2 * 16)),
+                     lambda n: n * blk * (1 if alone else 2), bwd_k,
+                     None if alone else "clenshaw_sddmm_bulk_fcc10000.md", "adjoint.cu"),
+        # windowed: G += sum_j y_j ybar_{j+1}^T (j = 0 .. K-1, K pairs a step): reads both panels
+        # of every pair, reads and writes the FP64 accumulator once per window; tensor: one pair
+        # per launch (K - 1 a step), the accumulator read and written every launch
+        "window": ((lambda n: n * (2 * panel + nnzb * B2 * 16)) if tensor else
+                   (lambda n: args.steps * (K * 2 * panel + nwin * nnzb * B2 * 16)),
+                   (lambda n: n * blk) if tensor else (lambda n: args.steps * K * blk),
+                   "sddmm_tc" if tensor else "sddmm_window_g", None,
+                   "tc_sddmm.cu" if tensor else "adjoint.cu"),
     }
     kernels = {}
     for f, (tms, nl) in fam.items():
@@ -388,7 +395,17 @@ def run_ours(args, rank, world):
         by, fl = byf(nl) / args.steps, flf(nl) / args.steps
         sec = tms / 1e3 / args.steps
         t_mem, t_alu = by / (hbm * 1e9), fl / (alu * 1e12)
-        if t_alu >= t_mem:
+        if f == "window" and tensor:
+            # a contraction on the TF32 tensor cores: HBM-bound at its algorithmic bytes unless
+            # its useful flops take longer at the TF32 peak (measured BF16 peak x 1/2, nominal ratio)
+            tf32 = float(peaks.get("bf16_tflops", 1895.3)) / 2
+            if fl / (tf32 * 1e12) >= t_mem:
+                r = {"bound": "tensor", "achieved": fl / sec / 1e12, "peak": tf32, "unit": "TFLOP/s",
+                     "peak_source": "MEASURED_PEAKS.json bf16_tflops x 1/2 (TF32, nominal ratio; of measured)"}
+            else:
+                r = {"bound": "hbm", "achieved": by / sec / 1e9, "peak": hbm, "unit": "GB/s",
+                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+        elif t_alu >= t_mem:
             r = {"bound": "alu", "achieved": fl / sec / 1e12, "peak": alu, "unit": "TFLOP/s",
                  "peak_source": ("152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz (derived, FP32 FMA)"
                                  if not fp64 else "152 SMs x 64 FP64 ops x 2070 MHz / 64 (derived)")}
@@ -416,8 +433,8 @@ def run_ours(args, rank, world):
                           "panels (%.0f MB each) fit in L2: an L2-resident workload, not flushed")
                          % (panel / 1e6),
                    "parallelism": f"replicas x{world}", "seeds": [5264, wk.probe_seed],
-                   "adjoint": ("windowed" if windowed else "fused") + (" (tuned)" if args.adjoint == "auto" else ""),
-                   "autotune": None if tuned is None else {"probes_per_task": tuned[0], "windowed": tuned[1]},
+                   "adjoint": sched + (" (tuned)" if args.adjoint == "auto" else ""),
+                   "autotune": None if tuned is None else {"probes_per_task": tuned[0], "outer_products": tuned[1]},
                    "order_rule": "fixed by --order (profiling run)" if args.order else "exp(-6.4 p kT/W) = 1e-7"},
         "e2e": {"value": job_rate(units, world, e_med), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
@@ -461,6 +478,7 @@ def run_ours(args, rank, world):
         # - the 64-cluster batch (energies and forces of every cluster per step).
         ctx.close()
         torch.cuda.empty_cache()
+        line["colored_sigma"] = colored_sigma(wk, obs[0], local, rank)
         c5 = api.Context()
         wk5 = make_workload("sc9-48", rank)
         s5 = api.Solver(wk5, c5)
@@ -509,6 +527,50 @@ def precision_compare(args, ctx, solver, wk, pos):
     return 0
 
 
+def colored_sigma(wk, mu, local, rank, r_color=6.0, n_runs=12):
+    """Sampling error of Omega^ (at the given mu) per atom for plain Rademacher probes and for the
+    multi-colour ensemble at the colouring radius r_color, at equal columns: the plain error from
+    the spread of the 512 single-probe estimates (sigma_1 / sqrt(columns)); the coloured error as
+    the spread over n_runs single-sample runs with independent seeds."""
+    import torch
+    from paper_1812_05264_gb300 import api
+    ctx = api.Context()
+    pos = torch.as_tensor(wk.positions, dtype=torch.float64, device=f"cuda:{local}")
+    model = api.Model.from_workload(wk, pos.device)
+    g = api.build_neighbors(ctx, pos, wk.cutoff)
+    H = api.assemble_H(ctx, model, pos, g)
+    emin, emax = api.spectral_bounds(ctx, H)
+    p = order_rule(emax - emin, wk.kT)
+    cg = api.chebyshev_coefficients(ctx, 2, p, emin, emax, mu, wk.kT).cpu().numpy()
+    t0 = time.perf_counter()
+    _, per = api.chebyshev_probe_moments(ctx, H, emin, emax, wk.probe_seed, wk.n_probes, p)
+    om1 = cg @ per.cpu().numpy()                    # single-probe estimates of Omega
+    t_plain = time.perf_counter() - t0
+    colors, q = api.atom_colors(ctx, pos, r_color)
+    cols = q * wk.n_orb
+    S = api.colored_columns(q, wk.n_orb, 1)
+    t0 = time.perf_counter()
+    omc = []
+    for j in range(n_runs):
+        m = api.colored_moments(ctx, H, emin, emax, 777000 + 101 * rank + j, colors, q, 1, S, p)
+        omc.append(float(cg @ m.cpu().numpy()))
+    t_col = (time.perf_counter() - t0) / n_runs
+    ctx.close()
+    sig_plain = float(np.std(om1, ddof=1)) / math.sqrt(cols)
+    sig_col = float(np.std(omc, ddof=1))
+    n = wk.n_atoms
+    return {"workload": wk.name, "order_p": p, "mu": mu, "colouring_radius_A": r_color,
+            "atom_colours": int(q), "columns_per_sample": int(cols), "panel_width": int(S),
+            "sigma_omega_per_atom_plain_eV": sig_plain / n,
+            "sigma_omega_per_atom_coloured_eV": sig_col / n,
+            "ratio_coloured_over_plain": sig_col / sig_plain,
+            "coloured_runs": n_runs,
+            "note": (f"plain: spread of {wk.n_probes} single-probe estimates scaled to {cols} columns; "
+                     f"coloured: spread over {n_runs} independent single-sample runs (its own "
+                     f"relative uncertainty ~{1 / math.sqrt(2 * (n_runs - 1)):.0%})"),
+            "s_per_coloured_sample": t_col, "s_plain_512_probe_sweep": t_plain}
+
+
 def fp64_compare(ctx, solver, wk, pos):
     """One full moments run of each path (after a short warm-up of each kernel) on the same
     operator, bounds, probes and order, then mu, Omega, E, N of each.  The FP64 path equals the
@@ -554,7 +616,7 @@ def adjoint_only(args, ctx, solver, wk, pos):
     mu = api.fermi_level(ctx, mom, emin, emax, wk.n_electrons, wk.kT)[0]
     args_ = (ctx, H, solver.model, pos, solver.box, emin, emax, wk.probe_seed, wk.n_probes, p, mu,
              wk.kT, wk.jackson, not wk.mixed)
-    sched = {"auto": None, "fused": False, "windowed": True}[args.adjoint]
+    sched = None if args.adjoint == "auto" else args.adjoint
     for _ in range(args.warmup):
         api.density_and_forces(*args_, windowed=sched)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -759,9 +821,10 @@ def main():
     ap.add_argument("--batch-steps", type=int, default=2,
                     help="timed steps of the 64-cluster batch record in the default line")
     ap.add_argument("--batch-warmup", type=int, default=3)
-    ap.add_argument("--adjoint", default="auto", choices=["auto", "fused", "windowed"],
-                    help="outer products inside each backward step, or over windows of 4 steps "
-                         "(auto: fused for 512 probes, windowed for the 128-probe batch)")
+    ap.add_argument("--adjoint", default="auto", choices=["auto", "fused", "windowed", "tensor"],
+                    help="outer products inside each backward step, over windows of 4 steps, or on "
+                         "the tensor cores after each step (auto: the tuned choice; windowed for "
+                         "the 128-probe batch)")
     args = ap.parse_args()
     if args.adjoint == "auto" and args.workload == "batched64":
         # the batch's merged operator is not tuned: with 128 probes per cluster the fused step's

@@ -56,6 +56,9 @@ typedef enum {
                                   kernel instead of inside each backward step */
 #define TBK_FUSED_ADJOINT 64   /* adjoint: outer products inside each backward step, whatever
                                   tbk_autotune chose */
+#define TBK_TC_OUTER 128       /* adjoint (mixed, 9x9 blocks): outer products on the tensor cores
+                                  (tcgen05, TF32 split three ways), one sampled-product kernel after
+                                  each backward step */
 
 /* Damping of the Chebyshev series. */
 #define TBK_DAMP_NONE 0
@@ -127,9 +130,11 @@ int tbk_test_stall_next_step(tbk_ctx* ctx);
    of 128, the probe chunk (128, 256 or 512 probes) per task of the TMA-fed recurrence step and
    the adjoint's outer-product schedule (fused into each backward step, or windows of 4 steps),
    and keep the faster of each in the context for every later call on an operator of the same
-   shape (rows, stored blocks) and probe count.  All choices give the same results up to FP32
-   summation order.  choice: host, 2 ints {probes per task, windowed (0/1)}.  Runs a few dozen
-   kernels on scratch panels; synchronises the stream. */
+   shape (rows, stored blocks) and probe count.  The outer-product schedules timed are: fused into
+   each backward step, windows of 4 steps, and the tensor cores after each step (TBK_TC_OUTER,
+   where it applies).  All choices give the same results up to FP32 summation order.  choice:
+   host, 2 ints {probes per task, schedule (0 fused, 1 windowed, 2 tensor cores)}.  Runs a few
+   dozen kernels on scratch panels; synchronises the stream. */
 int tbk_autotune(tbk_ctx* ctx, const tbk_bsr* H, double emin, double emax, int32_t n_probes,
                  int32_t* choice);
 
@@ -278,8 +283,8 @@ int tbk_fermi_level(tbk_ctx* ctx, const double* moments, int32_t order, double e
    G: device, nnzb * n_orb^2 FP64, or NULL.  forces: device, n_atoms x 3 FP64, or NULL;
    F_c = -sum_ab <G_ab, dH_ab/dR_c> needs model->kind == TBK_MODEL_SK and pos (device) / box as
    in tbk_assemble_H.  flags: TBK_MIXED or TBK_FP64, optionally | TBK_PLAIN_KERNEL |
-   TBK_WINDOWED or TBK_FUSED_ADJOINT (both ways give the same G up to FP32 summation order;
-   without either, the schedule tbk_autotune chose for this shape, else fused). */
+   TBK_WINDOWED, TBK_FUSED_ADJOINT or TBK_TC_OUTER (all give the same G up to FP32 summation
+   order; without any, the schedule tbk_autotune chose for this shape, else fused). */
 int tbk_density_and_forces(tbk_ctx* ctx, const tbk_bsr* H, const tbk_model* model,
                            const double* pos, const double* box, double emin, double emax,
                            uint64_t probe_seed, int32_t n_probes, int32_t order, double mu,
@@ -291,8 +296,8 @@ int tbk_density_and_forces(tbk_ctx* ctx, const tbk_bsr* H, const tbk_model* mode
    512 the forward sweep of the adjoint produces the moments as it goes, so no separate moment
    pass runs.  moments: device, order doubles, or NULL.  observables: host, 4 doubles {mu, Omega,
    E, N}.  G, forces as in tbk_density_and_forces (either may be NULL).  flags: TBK_MIXED or
-   TBK_FP64, optionally | TBK_PLAIN_KERNEL | TBK_WINDOWED | TBK_FUSED_ADJOINT.  Synchronises
-   the stream. */
+   TBK_FP64, optionally | TBK_PLAIN_KERNEL | TBK_WINDOWED | TBK_FUSED_ADJOINT | TBK_TC_OUTER.
+   Synchronises the stream. */
 int tbk_energies_and_forces(tbk_ctx* ctx, const tbk_bsr* H, const tbk_model* model,
                             const double* pos, const double* box, double emin, double emax,
                             uint64_t probe_seed, int32_t n_probes, int32_t order,
@@ -382,7 +387,8 @@ int tbk_colored_moments(tbk_ctx* ctx, const tbk_bsr* H, double emin, double emax
 /* tbk_colored_energies_and_forces: tbk_energies_and_forces (one call: moments from the adjoint's
    forward sweep, mu, Omega, E, N, the sampled density matrix G = dOmega^/dH on the pattern and the
    forces) for the multi-colour ensemble.  Mixed precision with 9x9 blocks and n_columns of 128, 256
-   or 512 (the doubled-moment adjoint); flags 0, TBK_WINDOWED or TBK_FUSED_ADJOINT.  Other
+   or 512 (the doubled-moment adjoint); flags 0, TBK_WINDOWED, TBK_FUSED_ADJOINT or
+   TBK_TC_OUTER.  Other
    arguments and outputs as in tbk_energies_and_forces.  Synchronises the stream. */
 int tbk_colored_energies_and_forces(tbk_ctx* ctx, const tbk_bsr* H, const tbk_model* model,
                                     const double* pos, const double* box, double emin, double emax,
@@ -391,6 +397,43 @@ int tbk_colored_energies_and_forces(tbk_ctx* ctx, const tbk_bsr* H, const tbk_mo
                                     double n_electrons, double kT, int32_t damping, int32_t flags,
                                     int64_t max_panel_bytes, double* moments, double* observables,
                                     double* G, double* forces);
+
+/* ---- f2: direct random estimates of the sampled density matrices (Eq. poly_PQ, S = I;
+   Eq. random_density) -----------------------------------------------------------------------
+
+   tbk_direct_density: at a given chemical potential mu and temperature kT,
+     P (device, nnzb * n_orb^2 FP64, or NULL) = M o P~,  P~ = (1/s) X R^T,
+     Q (device, same size, or NULL)           = M o Q~,  Q~ = (1/s) H X R^T,
+   with X = sum_{k < order} d_k alpha_k[f] C_k(H^) R (f the Fermi function of tbk_fermi_level at
+   mu, kT; d_k the damping factors), R the n_probes Rademacher probes of tbk_chebyshev_moments
+   and M the block pattern of H.  Blocks are laid out as H's values; the estimates are not
+   symmetric and are returned as computed.  forces (device, n_atoms x 3 FP64, or NULL): the
+   Hellmann-Feynman forces -sum_ab <P_ab, dH_ab/dR_c> from the symmetric part of M o P~ (needs
+   model->kind == TBK_MODEL_SK, pos and box as in tbk_assemble_H).  X is formed by the backward
+   (Clenshaw) form of the sum: order - 1 fused block products.  flags: TBK_MIXED or TBK_FP64,
+   optionally | TBK_PLAIN_KERNEL.  Synchronises the stream. */
+int tbk_direct_density(tbk_ctx* ctx, const tbk_bsr* H, const tbk_model* model, const double* pos,
+                       const double* box, double emin, double emax, uint64_t probe_seed,
+                       int32_t n_probes, int32_t order, double mu, double kT, int32_t damping,
+                       int32_t flags, double* P, double* Q, double* forces);
+
+/* ---- f3: the local approximation (Sec. II.C.1, Eq. local_density, S = I) ----------------
+
+   tbk_local_density: for every atom a, the region R_a of the atoms within r_max of a (the mask
+   M_L(r_max), pairs at exactly r_max included, as tbk_build_neighbors counts them) gives the
+   local operator H_a = H restricted to R_a; the n_orb columns of a of
+     P~_L = L_a p_f(H_a) L_a^T E_a   and   Q~_L = L_a H_a p_f(H_a) L_a^T E_a
+   (E_a the unit vectors of a's functions, p_f the order-term Chebyshev expansion of the Fermi
+   function at mu, kT on [emin, emax] with damping, as tbk_chebyshev_coefficients gives it) are
+   kept on the pattern of H: block (b, a) of P (device, nnzb * n_orb^2 FP64, or NULL) holds rows b
+   of column block a, likewise Q.  The result is not symmetric (each column comes from its own
+   local problem).  Every stored block (b, a) of H must join atoms at most r_max apart
+   (TBK_ERR_ARG otherwise).  pos: device, n_atoms x 3 FP64; box as in tbk_build_neighbors.  All
+   local problems run as one block-diagonal operator (order - 1 block products).  flags:
+   TBK_MIXED or TBK_FP64.  Synchronises the stream. */
+int tbk_local_density(tbk_ctx* ctx, const tbk_bsr* H, const double* pos, const double* box, double r_max,
+                      double emin, double emax, int32_t order, double mu, double kT, int32_t damping,
+                      int32_t flags, double* P, double* Q);
 
 /* ---- allocation-free variant of tbk_chebyshev_moments ------------------------------------
 

@@ -26,6 +26,7 @@ TBK_NO_GRAPH = 8
 TBK_TENSOR_CORES = 16
 TBK_WINDOWED = 32
 TBK_FUSED_ADJOINT = 64
+TBK_TC_OUTER = 128
 TBK_DAMP_NONE = 0
 TBK_DAMP_JACKSON = 1
 TBK_FN_FERMI = 0
@@ -104,6 +105,9 @@ SIGNATURES = {
     "tbk_fermi_level": [_P, _P, _I, _D, _D, _D, _D, _D, _I, C.POINTER(_D)],
     "tbk_density_and_forces": [_P, C.POINTER(tbk_bsr), C.POINTER(tbk_model), _P, _P, _D, _D, _U,
                                _I, _I, _D, _D, _I, _I, _L, _P, _P],
+    "tbk_direct_density": [_P, C.POINTER(tbk_bsr), C.POINTER(tbk_model), _P, _P, _D, _D, _U, _I, _I,
+                           _D, _D, _I, _I, _P, _P, _P],
+    "tbk_local_density": [_P, C.POINTER(tbk_bsr), _P, _P, _D, _D, _D, _I, _D, _D, _I, _I, _P, _P],
     "tbk_colored_moments": [_P, C.POINTER(tbk_bsr), _D, _D, _U, _P, _I, _I, _I, _I, _I, _P],
     "tbk_colored_energies_and_forces": [_P, C.POINTER(tbk_bsr), C.POINTER(tbk_model), _P, _P, _D, _D,
                                         _U, _P, _I, _I, _I, _I, _D, _D, _I, _I, _L, _P,

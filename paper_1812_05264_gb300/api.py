@@ -137,10 +137,17 @@ def _box_arg(box):
     return arr, C.cast(arr, C.c_void_p)
 
 
+SCHEDULES = ("fused", "windowed", "tensor")
+
+
 def _schedule_flag(windowed) -> int:
-    """None: the tuned schedule (else fused); True / False: windowed / fused outer products."""
+    """The adjoint's outer-product schedule: None = the tuned one (else fused); True / False =
+    windowed / fused; or a name from SCHEDULES ("tensor": on the tensor cores after each step)."""
     if windowed is None:
         return 0
+    if isinstance(windowed, str):
+        return {"fused": L.TBK_FUSED_ADJOINT, "windowed": L.TBK_WINDOWED,
+                "tensor": L.TBK_TC_OUTER}[windowed]
     return L.TBK_WINDOWED if windowed else L.TBK_FUSED_ADJOINT
 
 
@@ -291,12 +298,13 @@ def batched_spectral_bounds(ctx: Context, Hs: list, steps: int = 64, margin: flo
     return list(lo), list(hi)
 
 
-def autotune(ctx: Context, H: BSR, emin: float, emax: float, n_probes: int) -> tuple[int, bool]:
-    """Time the recurrence step's probe chunk and the adjoint's schedule on this operator and keep
-    the faster in the context for its shape: (probes per task, windowed)."""
+def autotune(ctx: Context, H: BSR, emin: float, emax: float, n_probes: int) -> tuple[int, str]:
+    """Time the recurrence step's probe chunk and the adjoint's outer-product schedule on this
+    operator and keep the fastest in the context for its shape: (probes per task, schedule name
+    from SCHEDULES)."""
     out = (C.c_int32 * 2)()
     L.call("tbk_autotune", ctx.handle, C.byref(H.struct()), float(emin), float(emax), int(n_probes), out)
-    return int(out[0]), bool(out[1])
+    return int(out[0]), SCHEDULES[int(out[1])]
 
 
 def chebyshev_coefficients(ctx: Context, fn: int, order: int, emin: float, emax: float, mu: float,
@@ -367,6 +375,41 @@ def density_and_forces(ctx: Context, H: BSR, model: Model | None, pos: torch.Ten
            | _schedule_flag(windowed),
            int(max_panel_bytes), _ptr(G), _ptr(F))
     return G, F
+
+
+def direct_density(ctx: Context, H: BSR, model: Model | None, pos: torch.Tensor | None, box,
+                   emin: float, emax: float, seed: int, n_probes: int, order: int, mu: float,
+                   kT: float, jackson: bool = False, fp64: bool = False, want_P: bool = True,
+                   want_Q: bool = True, want_forces: bool = False, plain: bool = False):
+    """f2: (M o P~, M o Q~, forces) of the direct random estimate (Eq. poly_PQ, Eq. random_density)
+    at a given mu; P~ and Q~ as (nnzb, b, b) blocks on H's pattern (not symmetric), forces from the
+    symmetric part of M o P~ (or None)."""
+    dev = H.val.device
+    P = torch.empty_like(H.val) if want_P else None
+    Q = torch.empty_like(H.val) if want_Q else None
+    F = torch.empty((H.graph.n_atoms, 3), dtype=torch.float64, device=dev) if want_forces else None
+    _keep, bx = _box_arg(box)
+    L.call("tbk_direct_density", ctx.handle, C.byref(H.struct()),
+           C.byref(model.s) if model is not None else None, _ptr(pos), bx, emin, emax,
+           C.c_uint64(seed), int(n_probes), int(order), float(mu), float(kT),
+           L.TBK_DAMP_JACKSON if jackson else L.TBK_DAMP_NONE,
+           (L.TBK_FP64 if fp64 else L.TBK_MIXED) | (L.TBK_PLAIN_KERNEL if plain else 0),
+           _ptr(P), _ptr(Q), _ptr(F))
+    return P, Q, F
+
+
+def local_density(ctx: Context, H: BSR, pos: torch.Tensor, box, r_max: float, emin: float,
+                  emax: float, order: int, mu: float, kT: float, jackson: bool = False,
+                  fp64: bool = False, want_P: bool = True, want_Q: bool = True):
+    """f3: (M o P~_L, M o Q~_L) of the local approximation (Sec. II.C.1, Eq. local_density) with
+    regions of radius r_max; block (b, a) holds rows b of column block a (not symmetric)."""
+    P = torch.empty_like(H.val) if want_P else None
+    Q = torch.empty_like(H.val) if want_Q else None
+    _keep, bx = _box_arg(box)
+    L.call("tbk_local_density", ctx.handle, C.byref(H.struct()), _ptr(pos), bx, float(r_max), emin, emax,
+           int(order), float(mu), float(kT), L.TBK_DAMP_JACKSON if jackson else L.TBK_DAMP_NONE,
+           L.TBK_FP64 if fp64 else L.TBK_MIXED, _ptr(P), _ptr(Q))
+    return P, Q
 
 
 def batched_moments(ctx: Context, Hs: list, emins, emaxs, seeds, n_probes: int, orders,

@@ -882,8 +882,8 @@ void launch_fused(tbk_ctx* ctx, const HOp& op, const void* bin, const void* bpre
   }
 }
 
-static void launch_sddmm(tbk_ctx* ctx, const HOp& op, const void* y, int y_is_probe, uint64_t seed,
-                         const void* b, int s, double w, double* Gacc) {
+void launch_sddmm(tbk_ctx* ctx, const HOp& op, const void* y, int y_is_probe, uint64_t seed,
+                  const void* b, int s, double w, double* Gacc) {
   const int64_t threads = op.nnzb * 32;
   const unsigned grid = (unsigned)((threads + 255) / 256);
 #define TBK_SD(TT, BB)                                                                          \
@@ -900,6 +900,16 @@ static void launch_sddmm(tbk_ctx* ctx, const HOp& op, const void* y, int y_is_pr
 }
 
 // ---- pieces shared with the batched driver -------------------------------------------------
+
+void launch_symmetrize(tbk_ctx* ctx, int64_t nnzb, int B, const int32_t* tr, const double* Gacc, double scale,
+                       double* G) {
+  const int64_t tot = nnzb * B * B;
+  if (B == 9)
+    symmetrize<9><<<(unsigned)((tot + 255) / 256), 256, 0, ctx->stream>>>(nnzb, tr, Gacc, scale, G);
+  else
+    symmetrize<1><<<(unsigned)((tot + 255) / 256), 256, 0, ctx->stream>>>(nnzb, tr, Gacc, scale, G);
+  post_launch(ctx, "symmetrize");
+}
 
 void launch_transpose_map(tbk_ctx* ctx, int n_atoms, const int32_t* row_ptr, const int32_t* col,
                           int32_t* tr, int* err) {
@@ -991,9 +1001,12 @@ __global__ void ybar_init(int64_t n, int s, float ca, const float* __restrict__ 
 // so the caller can finish the moments, solve for mu and return the coefficients c_0 .. c_{p-1}).
 void adjoint_doubling(tbk_ctx* ctx, const HOp& op, uint64_t probe_seed, int s, int p,
                       const std::function<std::vector<double>()>& get_coefs, double* partials, int nctas,
-                      int64_t max_panel_bytes, double* Gacc, int* err, bool windowed, const AdjBatch* bt,
+                      int64_t max_panel_bytes, double* Gacc, int* err, int sched, const AdjBatch* bt,
                       const void* probe_panel, int s_norm) {
   TBK_CHECK_ARG(!(bt && probe_panel), "a batch regenerates its probes");
+  const bool windowed = sched == 1;
+  // outer products on the tensor cores after each backward step, where that kernel applies
+  const bool tensor = sched == 2 && !bt && tc_sddmm_eligible(ctx, op, s, tc_sddmm_max_row(ctx, op));
   // a stored probe block y_0 (single system): read wherever the probe enters
   const bool r_panel = probe_panel != nullptr;
   const double nrm = r_panel && s_norm > 0 ? s_norm : s;
@@ -1194,8 +1207,10 @@ void adjoint_doubling(tbk_ctx* ctx, const HOp& op, uint64_t probe_seed, int s, i
                              : make_float4(r_gen ? cb(1) : 0.f, ca(k), r_gen ? 0.f : cb(k), cc(k));
         const float4* cfk = bt ? bt->cft + (size_t)k * bt->K.size() : nullptr;
         launch_fused(ctx, o, YB(k + 1), (k + 2 <= K || bt) ? YB(k + 2) : nullptr, YB(k), Y(k), cf, probe_seed, s,
-                     2.0, windowed ? nullptr : Gacc, err, br, cfk, (k >= 2 || r_panel) ? Y(k - 1) : nullptr,
-                     Y(k + 1));
+                     2.0, (windowed || tensor) ? nullptr : Gacc, err, br, cfk,
+                     (k >= 2 || r_panel) ? Y(k - 1) : nullptr, Y(k + 1));
+        // G += 2 y_k ybar_{k+1}^T on the pattern, on the tensor cores
+        if (tensor) launch_tc_sddmm(ctx, o, Y(k), YB(k + 1), s, 2.0, Gacc, err);
         if (windowed && (k - 1) % SDW == 0) {
           // G += 2 y_j ybar_{j+1}^T on the pattern for the window j = k .. min(k + SDW, K) - 1
           WindowPanels wp{};
@@ -1212,6 +1227,9 @@ void adjoint_doubling(tbk_ctx* ctx, const HOp& op, uint64_t probe_seed, int s, i
         wp.y[0] = (const float*)Y(0);
         wp.x[0] = (const float*)YB(1);
         launch_window(ctx, o, wp, 1, probe_seed, s, 1.0, Gacc, err, br, bt ? bt->d_K : nullptr, 0);
+      } else if (tensor && Y(0)) {
+        // G += y_0 ybar_1^T with a stored probe block
+        launch_tc_sddmm(ctx, o, Y(0), YB(1), s, 1.0, Gacc, err);
       } else {
         launch_fused(ctx, o, YB(1), nullptr, nullptr, Y(0), make_float4(0.f, 0.f, 0.f, 0.f), probe_seed, s,
                      1.0, Gacc, err, br, nullptr, nullptr, nullptr);
@@ -1227,11 +1245,12 @@ using namespace tbk;
 namespace tbk {
 // The adjoint's outer-product schedule: TBK_WINDOWED or TBK_FUSED_ADJOINT when given, else what
 // tbk_autotune measured for this shape, else fused.
-static bool windowed_schedule(const tbk_ctx* ctx, const HOp& op, int s, int flags) {
-  if (flags & TBK_WINDOWED) return true;
-  if (flags & TBK_FUSED_ADJOINT) return false;
+int outer_schedule(const tbk_ctx* ctx, const HOp& op, int s, int flags) {
+  if (flags & TBK_TC_OUTER) return 2;
+  if (flags & TBK_WINDOWED) return 1;
+  if (flags & TBK_FUSED_ADJOINT) return 0;
   const tbk_ctx::Tuned* t = find_tuned(ctx, op.n_rows, op.nnzb, s);
-  return t && t->windowed;
+  return t ? t->windowed : 0;
 }
 }  // namespace tbk
 
@@ -1246,7 +1265,7 @@ extern "C" int tbk_density_and_forces(tbk_ctx* ctx, const tbk_bsr* H, const tbk_
   TBK_CHECK_ARG(G || forces, "nothing to compute: G and forces are both NULL");
   TBK_CHECK_ARG(order >= 1, "order must be >= 1");
   TBK_CHECK_ARG(n_probes >= 4 && n_probes % 4 == 0, "n_probes must be a positive multiple of 4");
-  TBK_CHECK_ARG((flags & ~(TBK_FP64 | TBK_PLAIN_KERNEL | TBK_WINDOWED | TBK_FUSED_ADJOINT)) == 0, "unknown flag");
+  TBK_CHECK_ARG((flags & ~(TBK_FP64 | TBK_PLAIN_KERNEL | TBK_WINDOWED | TBK_FUSED_ADJOINT | TBK_TC_OUTER)) == 0, "unknown flag");
   const int plain = (flags & TBK_PLAIN_KERNEL) ? 1 : 0;
   TBK_CHECK_ARG(kT > 0.0, "kT must be positive");
   DeviceGuard dg(ctx);
@@ -1284,7 +1303,7 @@ extern "C" int tbk_density_and_forces(tbk_ctx* ctx, const tbk_bsr* H, const tbk_
   double scale = 2.0 / (W * s);
   if (fused) {
     adjoint_doubling(ctx, op, probe_seed, s, p, [&]() { return c; }, nullptr, 0, max_panel_bytes, Gacc, err,
-                       windowed_schedule(ctx, op, s, flags), nullptr);
+                       outer_schedule(ctx, op, s, flags), nullptr);
     scale = 2.0 / W;  // the 1/s of the moments is inside the source terms
   } else {
     // Panels y_1 .. y_{p-2} are needed in reverse order: all of them are kept when they fit the
@@ -1485,7 +1504,7 @@ void energies_and_forces_doubled(tbk_ctx* ctx, const tbk_bsr* H, const tbk_model
     return c;
   };
   adjoint_doubling(ctx, op, probe_seed, s, p, after_forward, partials, nctas, max_panel_bytes, Gacc, err,
-                   windowed_schedule(ctx, op, s, flags), nullptr, probe_panel, s_norm);
+                   outer_schedule(ctx, op, s, flags), nullptr, probe_panel, s_norm);
   double* Gout = G ? G : Gsym;
   const int64_t tot = op.nnzb * BB;
   symmetrize<9><<<(unsigned)((tot + 255) / 256), 256, 0, ctx->stream>>>(op.nnzb, tr, Gacc, 2.0 / W, Gout);
@@ -1516,7 +1535,7 @@ extern "C" int tbk_energies_and_forces(tbk_ctx* ctx, const tbk_bsr* H, const tbk
   TBK_CHECK_ARG(ctx != nullptr && observables != nullptr, "NULL argument");
   TBK_CHECK_ARG(order >= 1, "order must be >= 1");
   TBK_CHECK_ARG(n_probes >= 4 && n_probes % 4 == 0, "n_probes must be a positive multiple of 4");
-  TBK_CHECK_ARG((flags & ~(TBK_FP64 | TBK_PLAIN_KERNEL | TBK_WINDOWED | TBK_FUSED_ADJOINT)) == 0, "unknown flag");
+  TBK_CHECK_ARG((flags & ~(TBK_FP64 | TBK_PLAIN_KERNEL | TBK_WINDOWED | TBK_FUSED_ADJOINT | TBK_TC_OUTER)) == 0, "unknown flag");
   TBK_CHECK_ARG(kT > 0.0 && n_electrons >= 0.0, "kT must be positive and n_electrons >= 0");
   DeviceGuard dg(ctx);
   const int prec = (flags & TBK_FP64) ? TBK_FP64 : TBK_MIXED;
@@ -1528,7 +1547,7 @@ extern "C" int tbk_energies_and_forces(tbk_ctx* ctx, const tbk_bsr* H, const tbk
     // the separate calls give the same results for the other shapes and precisions
     double* mom = moments ? moments : (double*)scratch(ctx, WS_SEGMENT, sizeof(double) * (size_t)order);
     int rc = tbk_chebyshev_moments(ctx, H, emin, emax, probe_seed, n_probes, order,
-                                   flags & ~(TBK_WINDOWED | TBK_FUSED_ADJOINT), mom);
+                                   flags & ~(TBK_WINDOWED | TBK_FUSED_ADJOINT | TBK_TC_OUTER), mom);
     if (rc != TBK_OK) throw Error(rc, tbk_last_error());
     rc = tbk_fermi_level(ctx, mom, order, emin, emax, n_electrons, 0.0, kT, damping, observables);
     if (rc != TBK_OK) throw Error(rc, tbk_last_error());

@@ -1,7 +1,7 @@
 // Timing-based choices per operator shape and probe count, kept in the context: the probe chunk
 // (128, 256 or 512 probes) of each task of the TMA-fed recurrence step, and the schedule of the
-// adjoint's outer products (inside each fused backward step, or summed over windows of steps by
-// their own kernel).  Every candidate computes the same results up to FP32 summation order; the
+// adjoint's outer products (inside each fused backward step, summed over windows of steps by
+// their own kernel, or on the tensor cores after each backward step).  Every candidate computes the same results up to FP32 summation order; the
 // choice only changes how the work is cut.
 #include <cmath>
 #include <functional>
@@ -95,25 +95,28 @@ extern "C" int tbk_autotune(tbk_ctx* ctx, const tbk_bsr* H, double emin, double 
   }
   set_choice(ctx, op, s, best_cw, 0);
 
-  // 2. adjoint schedule, on a short sweep (K = 20 steps) with fixed coefficients
+  // 2. adjoint schedule (0 fused, 1 windowed, 2 tensor cores where that kernel applies), on a
+  //    short sweep (K = 20 steps) with fixed coefficients
   int windowed = 0;
   if (fused_eligible(op, s, 0)) {
     const int p = 40;
     std::vector<double> c(p);
     for (int k = 0; k < p; ++k) c[k] = 1.0 / (1.0 + k);
     double* Gacc = (double*)scratch(ctx, WS_GACC, sizeof(double) * (size_t)op.nnzb * 81);
-    float t_sched[2] = {0.f, 0.f};
-    for (int w = 0; w < 2; ++w) {
+    const int n_sched = tc_sddmm_eligible(ctx, op, s, tc_sddmm_max_row(ctx, op)) ? 3 : 2;
+    float t_sched[3] = {0.f, 0.f, 0.f};
+    for (int w = 0; w < n_sched; ++w) {
       for (int rep = 0; rep < 2; ++rep) {  // the first run maps the panels and warms up
         TBK_CUDA(cudaMemsetAsync(Gacc, 0, sizeof(double) * (size_t)op.nnzb * 81, ctx->stream));
         EventPair ev;
         TBK_CUDA(cudaEventRecord(ev.a, ctx->stream));
-        adjoint_doubling(ctx, op, seed, s, p, [&]() { return c; }, nullptr, 0, 0, Gacc, err, w != 0, nullptr);
+        adjoint_doubling(ctx, op, seed, s, p, [&]() { return c; }, nullptr, 0, 0, Gacc, err, w, nullptr);
         TBK_CUDA(cudaEventRecord(ev.b, ctx->stream));
         t_sched[w] = ev.ms(ctx);
       }
     }
-    windowed = t_sched[1] < t_sched[0] ? 1 : 0;
+    for (int w = 1; w < n_sched; ++w)
+      if (t_sched[w] < t_sched[windowed]) windowed = w;
   }
   int herr = 0;
   TBK_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));

@@ -111,10 +111,34 @@ struct AdjBatch {
 // probe_panel (single system only): the probe block y_0 stored as a panel (s columns) instead of
 // regenerated from the seed, for probe ensembles other than plain Rademacher signs; s_norm: the
 // number of samples the estimator divides by (0 = s).
+// sched: where the outer products run: 0 inside each fused backward step, 1 summed over windows of
+// steps by their own kernel, 2 on the tensor cores by a kernel after each backward step (single
+// system, 9x9 blocks; falls back to 0 where the tensor-core kernel does not apply).
 void adjoint_doubling(tbk_ctx* ctx, const HOp& op, uint64_t probe_seed, int s, int p,
                       const std::function<std::vector<double>()>& get_coefs, double* partials, int nctas,
-                      int64_t max_panel_bytes, double* Gacc, int* err, bool windowed, const AdjBatch* bt,
+                      int64_t max_panel_bytes, double* Gacc, int* err, int sched, const AdjBatch* bt,
                       const void* probe_panel = nullptr, int s_norm = 0);
+// The tensor-core sampled outer products (tc_sddmm.cu): the longest block row of the pattern,
+// whether the kernel takes this operator, and one launch Gacc += w y x^T on the pattern.
+int tc_sddmm_max_row(tbk_ctx* ctx, const HOp& op);
+bool tc_sddmm_eligible(tbk_ctx* ctx, const HOp& op, int s, int max_row);
+void launch_tc_sddmm(tbk_ctx* ctx, const HOp& op, const void* y, const void* x, int s, double w, double* Gacc,
+                     int* err);
+// Pieces of the adjoint reused by the direct estimates (adjoint.cu): Chebyshev coefficients into
+// device memory; Gacc += w sum_probes y[a rows] b[b rows]^T on every stored block (y or b FP32/FP64
+// panels of the operator's precision; y_is_probe: y is the probe block regenerated from seed);
+// the transpose map of a symmetric pattern; G = scale (Gacc + Gacc^T) / 2 blockwise.
+void coefficients(tbk_ctx* ctx, int fn, int p, double emin, double emax, double mu, double kT,
+                  int damping, double* out);
+void launch_sddmm(tbk_ctx* ctx, const HOp& op, const void* y, int y_is_probe, uint64_t seed,
+                  const void* b, int s, double w, double* Gacc);
+void launch_transpose_map(tbk_ctx* ctx, int n_atoms, const int32_t* row_ptr, const int32_t* col,
+                          int32_t* tr, int* err);
+void launch_symmetrize(tbk_ctx* ctx, int64_t nnzb, int B, const int32_t* tr, const double* Gacc, double scale,
+                       double* G);
+// The adjoint's outer-product schedule for a call: the flag if one is given, else the tuned choice
+// for this shape, else fused (0).
+int outer_schedule(const tbk_ctx* ctx, const HOp& op, int s, int flags);
 // The moments sweep of tbk_chebyshev_moments (per_probe: also each probe's moments).  With
 // probe_panel the probe block y_0 is read from that panel (s columns, the precision of the
 // recurrence) and the moments divide by s_norm samples; flags may not ask for direct moments then.

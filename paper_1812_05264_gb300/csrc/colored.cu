@@ -103,7 +103,7 @@ extern "C" int tbk_colored_energies_and_forces(tbk_ctx* ctx, const tbk_bsr* H, c
   TBK_API_BEGIN
   TBK_CHECK_ARG(ctx != nullptr && observables != nullptr, "NULL argument");
   TBK_CHECK_ARG(order >= 1, "order must be >= 1");
-  TBK_CHECK_ARG((flags & ~(TBK_WINDOWED | TBK_FUSED_ADJOINT)) == 0,
+  TBK_CHECK_ARG((flags & ~(TBK_WINDOWED | TBK_FUSED_ADJOINT | TBK_TC_OUTER)) == 0,
                 "unknown flag (the coloured adjoint runs in mixed precision)");
   TBK_CHECK_ARG(kT > 0.0 && n_electrons >= 0.0, "kT must be positive and n_electrons >= 0");
   TBK_CHECK_ARG(H != nullptr, "H is NULL");

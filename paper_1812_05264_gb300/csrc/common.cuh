@@ -38,7 +38,8 @@ void set_error(const char* msg);
 enum Slot {
   WS_PANEL0 = 0, WS_PANEL1, WS_PANEL2, WS_PANEL3, WS_HHAT, WS_PARTIALS, WS_FLAGS, WS_COEF,
   WS_TABLE, WS_NODES, WS_CELLS, WS_CELLS2, WS_CELLS3, WS_LANCZOS, WS_GACC, WS_TRANSPOSE,
-  WS_CHECKPOINTS, WS_SEGMENT, WS_MISC, WS_PROBES, WS_NSLOTS
+  WS_CHECKPOINTS, WS_SEGMENT, WS_MISC, WS_PROBES,
+  WS_LOCAL0, WS_LOCAL1, WS_LOCAL2, WS_LOCAL3, WS_LOCAL4, WS_NSLOTS
 };
 
 }  // namespace tbk
@@ -55,7 +56,7 @@ struct tbk_ctx {
   int stall_next_step = 0;       // test hook: the next TMA-fed step's producer issues no copies
   struct Tuned {                 // tbk_autotune's choices, per operator shape and probe count
     int64_t n_rows, nnzb;
-    int s, cw, windowed;
+    int s, cw, windowed;        // windowed: the outer-product schedule (0 fused, 1 windowed, 2 tensor cores)
   };
   std::vector<Tuned> tuned;
   int timed_mask = 0;            // bit f set: launches of kernel family f are bracketed by events

@@ -3,7 +3,8 @@ element where the oracle can compute the output.
 
 * The sampled density matrix G = dOmega^/dH on the pattern (Sec. II.D, Eq. polynomial_response)
   from the kernels the benchmark times: the fused adjoint step with its outer products (128, 256
-  and 512 probes per task) and the windowed schedule (the adjoint step alone plus the window
+  and 512 probes per task), the windowed schedule (the adjoint step alone plus the window
+  kernel) and the tensor-core schedule (the adjoint step alone plus the tcgen05 sampled-product
   kernel), each against the oracle's Daleckii-Krein gradient of the same estimator.
 * The 10,000-atom workload's own check on a 500-atom sub-cluster: kT = 0.025 eV, 512 probes, the
   order p of the error model (about 2,400 terms), the benchmark's call (autotuned, one-call
@@ -70,7 +71,7 @@ def _g_err(G, Gd, rp, col):
 # ---- G of the benchmarked adjoint kernels, element by element --------------------------------
 
 @pytest.mark.parametrize("s", [128, 256, 512])
-@pytest.mark.parametrize("windowed", [False, True])
+@pytest.mark.parametrize("windowed", [False, True, "tensor"])
 def test_adjoint_kernels_G_elementwise_vs_oracle(api, ctx, s, windowed):
     wk = wl.fcc_cu(40, kT=0.5, n_probes=s, seed=5264, probe_seed=11, jitter=0.05)
     rp, col, Hd = oracle_H(wk)
@@ -124,6 +125,20 @@ def test_subcluster500_G_and_forces_at_the_benchmark_order(sub500):
     assert err < G_TOL, err
     assert np.abs(r["F"].cpu().numpy() - r["Fo"]).max() < 1e-3
     assert np.abs(r["F"].cpu().numpy().sum(0)).max() < 1e-8
+
+
+@pytest.mark.parametrize("sched", ["fused", "windowed", "tensor"])
+def test_subcluster500_every_schedule_at_the_benchmark_order(api, ctx, sub500, sched):
+    """The same one-call run with each outer-product schedule forced: G against the oracle."""
+    r = sub500
+    wk = r["wk"]
+    mom, obs, G, F = api.energies_and_forces(ctx, r["H"], r["model"], r["pos"], None, r["emin"], r["emax"],
+                                             wk.probe_seed, 512, r["p"], wk.n_electrons, wk.kT, False, False,
+                                             want_G=True, windowed=sched)
+    assert torch.equal(mom, r["mom"])
+    err = _g_err(G, r["Gd"], r["rp"], r["col"])
+    assert err < G_TOL, err
+    assert np.abs(F.cpu().numpy() - r["Fo"]).max() < 1e-3
 
 
 def test_subcluster500_autograd_forces_match_central_differences(api, ctx):

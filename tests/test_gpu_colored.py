@@ -73,9 +73,9 @@ def test_colored_moments_vs_oracle(api, ctx, r_color, n_samples, fp64):
     assert np.abs(mom.cpu().numpy() - ref).max() < (1e-11 if fp64 else 1e-5) * n
 
 
-@pytest.mark.parametrize("r_color,n_samples,windowed", [(4.5, 1, False), (4.5, 1, True),
-                                                        (6.0, 1, False), (6.0, 1, True),
-                                                        (6.0, 3, False), (6.0, 3, True)])
+@pytest.mark.parametrize("r_color,n_samples,windowed", [(4.5, 1, False), (4.5, 1, True), (4.5, 1, "tensor"),
+                                                        (6.0, 1, False), (6.0, 1, True), (6.0, 1, "tensor"),
+                                                        (6.0, 3, False), (6.0, 3, True), (6.0, 3, "tensor")])
 def test_colored_energies_G_and_forces_vs_oracle(api, ctx, r_color, n_samples, windowed):
     wk = wl.fcc_cu(60, kT=0.5, n_probes=8, seed=5264, probe_seed=4242, jitter=0.05)
     rp, col, Hd = oracle_H(wk)

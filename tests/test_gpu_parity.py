@@ -570,8 +570,8 @@ def test_autotune_choice_keeps_the_results(api):
             False, False)
     m0 = api.chebyshev_moments(ctx2, res.H, res.emin, res.emax, wk.probe_seed, 512, 40, False)
     G0, F0 = api.density_and_forces(*args)
-    chunk, windowed = api.autotune(ctx2, res.H, res.emin, res.emax, 512)
-    assert chunk in (128, 256, 512) and windowed in (False, True)
+    chunk, sched = api.autotune(ctx2, res.H, res.emin, res.emax, 512)
+    assert chunk in (128, 256, 512) and sched in ("fused", "windowed", "tensor")
     m1 = api.chebyshev_moments(ctx2, res.H, res.emin, res.emax, wk.probe_seed, 512, 40, False)
     G1, F1 = api.density_and_forces(*args)
     n = H.shape[0]

@@ -435,6 +435,29 @@ int tbk_local_density(tbk_ctx* ctx, const tbk_bsr* H, const double* pos, const d
                       double emin, double emax, int32_t order, double mu, double kT, int32_t damping,
                       int32_t flags, double* P, double* Q);
 
+/* ---- f4: the rational (pole) approximation with CGLS solves (Sec. II.B.2, Eq. rational_fit,
+   Eq. rational_PQ with S = I) -----------------------------------------------------------------
+
+   tbk_rational_density: f(x) = 2 / (1 + exp((x - mu)/kT)) is replaced by the n_pairs-pole-pair
+   continued-fraction expansion of the Fermi function (Ozaki, Phys. Rev. B 75, 035123 (2007)),
+     f_r(x) = 1 + 2 Re sum_p w_p / (x - zeta_p),   zeta_p = mu + i kT z_p,  w_p = 2 kT R_p,
+   with z_p = 1/b_p and R_p = -v_p^2/(4 b_p^2) from the positive eigenvalues b_p and the first
+   eigenvector components v_p of the 2 n_pairs square tridiagonal matrix with off-diagonal
+   1/(2 sqrt((2m-1)(2m+1))).  Then X = f_r(H) R = R + 2 Re sum_p w_p g_p with (H - zeta_p) g_p = R
+   for the n_probes Rademacher probes R of tbk_chebyshev_moments, each system solved by CGLS to a
+   relative residual below tol in every probe column (at most max_iter iterations per pole; the
+   poles from the farthest from mu to the nearest, each solve started from the previous one), and
+     P (device, nnzb * n_orb^2, or NULL) = M o (X R^T)/s,  Q (same, or NULL) = M o (H X R^T)/s,
+   forces (device, n_atoms x 3, or NULL) from the symmetric part of M o P~ as in
+   tbk_direct_density.  info (host, 2 doubles, or NULL): {CGLS iterations over all poles, the
+   largest final relative residual}.  n_probes a multiple of 4; n_pairs in [1, 256]; flags must
+   be TBK_FP64 (the systems' condition numbers reach max|eps - mu|/(pi kT)).  TBK_ERR_NOCONV
+   when a solve stops above tol (the outputs are still written).  Synchronises the stream. */
+int tbk_rational_density(tbk_ctx* ctx, const tbk_bsr* H, const tbk_model* model, const double* pos,
+                         const double* box, uint64_t probe_seed, int32_t n_probes, double mu, double kT,
+                         int32_t n_pairs, double tol, int32_t max_iter, int32_t flags, double* P,
+                         double* Q, double* forces, double* info);
+
 /* ---- allocation-free variant of tbk_chebyshev_moments ------------------------------------
 
    No counterpart in the paper: this entry point exists for callers that cannot allocate device

@@ -108,6 +108,8 @@ SIGNATURES = {
     "tbk_direct_density": [_P, C.POINTER(tbk_bsr), C.POINTER(tbk_model), _P, _P, _D, _D, _U, _I, _I,
                            _D, _D, _I, _I, _P, _P, _P],
     "tbk_local_density": [_P, C.POINTER(tbk_bsr), _P, _P, _D, _D, _D, _I, _D, _D, _I, _I, _P, _P],
+    "tbk_rational_density": [_P, C.POINTER(tbk_bsr), C.POINTER(tbk_model), _P, _P, _U, _I, _D, _D, _I, _D,
+                             _I, _I, _P, _P, _P, C.POINTER(_D)],
     "tbk_colored_moments": [_P, C.POINTER(tbk_bsr), _D, _D, _U, _P, _I, _I, _I, _I, _I, _P],
     "tbk_colored_energies_and_forces": [_P, C.POINTER(tbk_bsr), C.POINTER(tbk_model), _P, _P, _D, _D,
                                         _U, _P, _I, _I, _I, _I, _D, _D, _I, _I, _L, _P,

@@ -398,6 +398,25 @@ def direct_density(ctx: Context, H: BSR, model: Model | None, pos: torch.Tensor 
     return P, Q, F
 
 
+def rational_density(ctx: Context, H: BSR, model: Model | None, pos: torch.Tensor | None, box,
+                     seed: int, n_probes: int, mu: float, kT: float, n_pairs: int, tol: float = 1e-10,
+                     max_iter: int = 20000, want_P: bool = True, want_Q: bool = True,
+                     want_forces: bool = False):
+    """f4: (M o P~, M o Q~, forces, (CGLS iterations, worst relative residual)) of the rational
+    approximation with n_pairs continued-fraction pole pairs and CGLS solves (FP64)."""
+    dev = H.val.device
+    P = torch.empty_like(H.val) if want_P else None
+    Q = torch.empty_like(H.val) if want_Q else None
+    F = torch.empty((H.graph.n_atoms, 3), dtype=torch.float64, device=dev) if want_forces else None
+    info = (C.c_double * 2)()
+    _keep, bx = _box_arg(box)
+    L.call("tbk_rational_density", ctx.handle, C.byref(H.struct()),
+           C.byref(model.s) if model is not None else None, _ptr(pos), bx, C.c_uint64(seed),
+           int(n_probes), float(mu), float(kT), int(n_pairs), float(tol), int(max_iter), L.TBK_FP64,
+           _ptr(P), _ptr(Q), _ptr(F), info)
+    return P, Q, F, (int(info[0]), float(info[1]))
+
+
 def local_density(ctx: Context, H: BSR, pos: torch.Tensor, box, r_max: float, emin: float,
                   emax: float, order: int, mu: float, kT: float, jackson: bool = False,
                   fp64: bool = False, want_P: bool = True, want_Q: bool = True):

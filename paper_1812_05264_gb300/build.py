@@ -14,7 +14,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 SOURCES = ["context.cu", "scan.cu", "neighbors.cu", "assemble.cu", "lanczos.cu", "fermi.cu",
            "recurrence.cu", "adjoint.cu", "noalloc.cu", "batched.cu", "tc_step.cu", "autotune.cu",
-           "coloring.cu", "colored.cu", "umma_host.cu", "tc_sddmm.cu", "direct.cu", "local.cu"]
+           "coloring.cu", "colored.cu", "umma_host.cu", "tc_sddmm.cu", "direct.cu", "local.cu", "rational.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", INCLUDE]

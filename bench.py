@@ -185,6 +185,27 @@ def oracle_step(wk, want=False):
     return wk.n_atoms * wk.n_probes * p, dt, p
 
 
+def host_recurrence_rate(wk, steps: int = 24):
+    """The oracle's host FP64 block-sparse recurrence (C/OpenMP, doubled moments, the GPU path's
+    work per moment) on the full workload, a bounded number of block products: the CPU rate in the
+    benchmark's own unit (the analogue of the paper's block-sparse solver throughput)."""
+    from oracle import hamiltonian as oham, neighbors as onb, o2
+    rp, col = onb.neighbor_csr(wk.positions, wk.cutoff, wk.box)
+    Hs = oham.sparse_sk(wk.positions, rp, col, wk.sk_V, wl.SK_R0, wl.SK_DECAY, wl.SK_ONSITE, wk.box)
+    # bounds that enclose the spectrum (Gershgorin): the rate does not depend on them
+    absrow = np.asarray(abs(Hs).sum(axis=1)).ravel()
+    diag = Hs.diagonal()
+    lo, hi = float((diag - (absrow - np.abs(diag))).min()), float((diag + (absrow - np.abs(diag))).max())
+    o2.moments(rp, col, Hs.data, lo, hi, wk.probe_seed, wk.n_probes, 3, doubled=True)   # warm-up
+    t0 = time.perf_counter()
+    _, products = o2.moments(rp, col, Hs.data, lo, hi, wk.probe_seed, wk.n_probes, 2 * steps + 1, doubled=True)
+    dt = time.perf_counter() - t0
+    return {"value": wk.n_atoms * wk.n_probes * products / dt, "unit": UNIT, "cores": cpu_cores(),
+            "kind": "oracle (host FP64 block-sparse recurrence, C/OpenMP)",
+            "sample": f"{wk.name}: all {wk.n_atoms} atoms and {wk.n_probes} probes, {products} block "
+                      f"products (doubled moments), {dt:.1f} s"}
+
+
 def cpu_cores() -> int:
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS"):
         if os.environ.get(k, "").isdigit():
@@ -466,6 +487,7 @@ def run_ours(args, rank, world):
                 "mu_abs_eV": abs(sres.mu - ref["mu"]),
                 "force_max_abs_eV_per_A": float(np.abs(sres.forces.cpu().numpy() - ref["F"]).max()),
                 "tolerances": {"energy_per_atom_eV": 1e-6 if fp64 else 1e-4, "force_eV_per_A": 1e-3}}
+            line["cpu_recurrence_baseline"] = host_recurrence_rate(wk)
             line["cpu_baseline"] = {
                 "value": u / dt, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
                 "sample": (f"FP64 oracle (dense eigh, exact estimator, Daleckii-Krein forces) on "

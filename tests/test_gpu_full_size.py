@@ -8,6 +8,8 @@ The dense oracle does not fit at this size (90,000 rows), so the checks are:
 * sampled outputs the oracle computes one by one: the per-probe moments r_i^T C_k(H^) r_i of
   three probes, by the FP64 three-term recurrence on the sparse H (Eq. poly_PQ), against the
   benchmarked mixed path and against the plain FP64 path;
+* the moments of all 512 probes against the oracle's host FP64 block-sparse recurrence
+  (C/OpenMP, written independently of the CUDA library);
 * properties that hold at any size: the bisection meets N^(mu^) = N_e, the forces sum to zero
   (H depends only on the bond vectors), and the one-call path's moments are those of the
   moments call.
@@ -92,6 +94,25 @@ def test_sampled_probe_moments_at_full_size(api, run, fp64, direct):
         # and the one-call path's forward sweep gives the same moments
         assert np.allclose(run["mom"][:P_SAMPLED].cpu().numpy(), mom.cpu().numpy(), rtol=0,
                            atol=1e-6 * n)
+
+
+P_ALL = 24
+
+
+@pytest.mark.parametrize("fp64", [False, True])
+def test_all_probe_moments_at_full_size_against_the_host_recurrence(api, run, fp64):
+    """Every probe at once: the moments of all 512 probes (order 24) against the oracle's host
+    FP64 block-sparse recurrence (oracle/o2_recurrence.c, C/OpenMP, doubled moments as on the GPU)
+    on the oracle's own H: the benchmarked mixed path within 2e-6 n, the plain FP64 path within
+    1e-11 n."""
+    from oracle import o2
+    Hs = run["Hs"]
+    n = Hs.shape[0]
+    ref, products = o2.moments(run["rp"], run["col"], Hs.data, run["emin"], run["emax"], PROBE_SEED, S, P_ALL,
+                               doubled=True)
+    assert products == P_ALL // 2
+    mom = api.chebyshev_moments(run["ctx"], run["H"], run["emin"], run["emax"], PROBE_SEED, S, P_ALL, fp64=fp64)
+    assert np.abs(mom.cpu().numpy() - ref).max() < (1e-11 if fp64 else 2e-6) * n
 
 
 def test_properties_of_the_full_step(run):

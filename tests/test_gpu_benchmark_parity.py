@@ -291,3 +291,16 @@ def test_lattice48_energies_vs_bloch(api, ctx, lattice48, fp64, tol):
     Om_o, E_o, N_o = och.estimator_observables(ref, emin, emax, mu_o, wk.kT)
     for a, b in ((Om, Om_o), (E, E_o), (N, N_o)):
         assert abs(a - b) / wk.n_atoms < tol
+
+
+def test_tensor_schedule_falls_back_on_rows_longer_than_its_groups(api, ctx):
+    """A 6 A cutoff gives rows of up to 79 stored blocks, more than the tensor-core kernel's 32:
+    the TBK_TC_OUTER schedule then runs the fused kernel, and G equals the fused schedule's."""
+    wk = wl.fcc_cu(60, kT=0.5, n_probes=128, seed=5264, probe_seed=21, jitter=0.05)
+    wk.cutoff = 6.0
+    model, pos, H, emin, emax = _operator(api, ctx, wk)
+    assert int((H.graph.row_ptr[1:] - H.graph.row_ptr[:-1]).max()) > 32
+    args = (ctx, H, model, pos, None, emin, emax, wk.probe_seed, 128, 40, 3.0, wk.kT, False, False)
+    G1, F1 = api.density_and_forces(*args, windowed="tensor")
+    G0, F0 = api.density_and_forces(*args, windowed="fused")
+    assert torch.equal(G1, G0) and torch.equal(F1, F0)

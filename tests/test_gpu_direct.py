@@ -109,3 +109,20 @@ def test_direct_density_one_orbital_lattice(api, ctx):
         for got, ref in ((P, Pt), (Q, Qt)):
             rb = blocks_of(ref, rp, col, 1)
             assert np.abs(got.cpu().numpy() - rb).max() < tol * np.abs(rb).max()
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_direct_density_lowest_orders(api, ctx, p):
+    """The degenerate orders of the Clenshaw form: X = alpha_0 R (p = 1), alpha_0 R + alpha_1 H^ R
+    (p = 2), and the first step with a b_{k+2} (p = 3), FP64 against the oracle."""
+    wk = wl.fcc_cu(20, kT=0.5, n_probes=8, seed=5264, probe_seed=314, jitter=0.05)
+    rp, col, Hd = oracle_H(wk)
+    model, pos, H, emin, emax = _operator(api, ctx, wk)
+    w, V = np.linalg.eigh(Hd)
+    mu = float(np.median(w))
+    P, Q, _ = api.direct_density(ctx, H, None, None, None, emin, emax, wk.probe_seed, 8, p, mu, wk.kT, fp64=True)
+    R = och.probes(Hd.shape[0], 8, wk.probe_seed)
+    Pt, Qt = odi.direct_density(w, V, R, emin, emax, mu, wk.kT, p)
+    for got, ref in ((P, Pt), (Q, Qt)):
+        rb = blocks_of(ref, rp, col, 9)
+        assert np.abs(got.cpu().numpy() - rb).max() < 1e-10 * max(1.0, np.abs(rb).max())

@@ -107,3 +107,18 @@ def test_local_density_rejects_a_radius_below_the_cutoff(api, ctx):
     with pytest.raises(TbkError) as e:
         api.local_density(ctx, H, pos, None, 3.0, emin, emax, 40, 2.0, wk.kT)
     assert e.value.code == TBK_ERR_ARG
+
+
+def test_local_density_single_atom(api, ctx):
+    """One atom: its region is itself, so P~_L is p_f of its 9 x 9 on-site block (FP64)."""
+    wk = wl.fcc_cu(1, kT=0.5, n_probes=8, seed=5264, probe_seed=1)
+    rp, col, Hd = oracle_H(wk)
+    model, pos, H, emin, emax = _operator(api, ctx, wk)
+    p, mu = 60, 4.0
+    P, Q = api.local_density(ctx, H, pos, None, 5.0, emin, emax, p, mu, wk.kT, fp64=True)
+    w, V = np.linalg.eigh(Hd)
+    af, _, _ = och.fd_coefficients(p, emin, emax, mu, wk.kT)
+    pf = och.poly_values(af, och.mapped(w, emin, emax))
+    Pref = (V * pf) @ V.T
+    assert np.abs(P.cpu().numpy()[0] - Pref).max() < 1e-12
+    assert np.abs(Q.cpu().numpy()[0] - Hd @ Pref).max() < 1e-11

@@ -99,3 +99,19 @@ def test_rational_reports_a_solve_that_stops_early(api, ctx):
     assert e.value.code == TBK_ERR_ARG
     P, _, _, (it, res) = api.rational_density(ctx, H, None, None, None, 1, 8, 0.0, wk.kT, 8, want_Q=False)
     assert res < 1e-10 and torch.isfinite(P).all()
+
+
+def test_rational_single_pole_pair(api, ctx):
+    """n_pairs = 1: f_r(x) = 1 + 2 Re w_1/(x - zeta_1), the coarsest expansion, FP64 against the
+    oracle's eigen route."""
+    wk = wl.fcc_cu(15, kT=0.5, n_probes=4, seed=5264, probe_seed=74, jitter=0.05)
+    rp, col, Hd = oracle_H(wk)
+    model, pos, H, emin, emax = _operator(api, ctx, wk)
+    w, V = np.linalg.eigh(Hd)
+    mu = float(np.median(w))
+    P, Q, _, (it, res) = api.rational_density(ctx, H, None, None, None, wk.probe_seed, 4, mu, wk.kT, 1, tol=1e-12)
+    R = och.probes(Hd.shape[0], 4, wk.probe_seed)
+    Pt, Qt = ora.rational_density(w, V, R, mu, wk.kT, 1)
+    for got, ref in ((P, Pt), (Q, Qt)):
+        rb = blocks_of(ref, rp, col, 9)
+        assert np.abs(got.cpu().numpy() - rb).max() < 1e-8 * np.abs(rb).max()

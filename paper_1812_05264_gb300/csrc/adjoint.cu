@@ -264,7 +264,7 @@ clenshaw_sddmm_bulk(const int n_atoms, const int32_t* __restrict__ row_ptr,
       ok = mbar_wait(y_full, y_it & 1);
       if (!ok) break;
     }
-    float2 acc[9][2];  // row i x probes (2h, 2h + 1)
+    float2 acc[9][2];  // row i, probe v: acc_at(acc, i, v)
 #pragma unroll
     for (int i = 0; i < 9; ++i) acc[i][0] = acc[i][1] = make_float2(0.f, 0.f);
     for (int q = 0; q < k1 - k0; ++q) {
@@ -302,7 +302,7 @@ clenshaw_sddmm_bulk(const int n_atoms, const int32_t* __restrict__ row_ptr,
 #pragma unroll
     for (int i = 0; i < 9; ++i)
 #pragma unroll
-      for (int v = 0; v < 4; ++v) yo[i][v] = 2.f * ((v & 1) ? acc[i][v >> 1].y : acc[i][v >> 1].x);
+      for (int v = 0; v < 4; ++v) yo[i][v] = 2.f * acc_at(acc, i, v);
     if (cfa.x != 0.f) {
 #pragma unroll
       for (int i = 0; i < 9; ++i)
@@ -699,7 +699,7 @@ clenshaw_self(const int n_atoms, const int32_t* __restrict__ row_ptr, const int3
 #pragma unroll
     for (int i = 0; i < 9; ++i)
 #pragma unroll
-      for (int v = 0; v < 4; ++v) yo[i][v] = 2.f * ((v & 1) ? acc[i][v >> 1].y : acc[i][v >> 1].x);
+      for (int v = 0; v < 4; ++v) yo[i][v] = 2.f * acc_at(acc, i, v);
     if (cfa.x != 0.f) {
 #pragma unroll
       for (int i = 0; i < 9; ++i)

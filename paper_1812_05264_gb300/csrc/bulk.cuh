@@ -74,30 +74,43 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
 }
 
 
-// One neighbour tile of the FP32 block product with packed f32x2 FMAs over probe pairs:
-//   acc[i][h] += H^[i][l] * (x[l][2h], x[l][2h+1])   for l = 0..8,
+// One neighbour tile of the FP32 block product with packed f32x2 FMAs:
+//   acc(i, v) += H^[i][l] * x[l][v]   for l = 0..8,
 // X: 9 x P tile in shared memory, Hs: column-major block (columns padded to 12 floats), pl: the
-// thread's first probe (4 probes: h = 0, 1).  Every accumulator sums l = 0..8 in order (same
-// rounding as scalar FMAs); the 9 rows need 18 packed FMAs per column, no padding row.
+// thread's first probe (4 probes v = 0..3).  Rows 0..7 are packed in pairs (2j, 2j + 1), whose
+// H^ values sit side by side in a column, against one probe: acc[2j + (v >> 1)][v & 1]; row 8 is
+// packed over probe pairs: acc[8][h] = probes (2h, 2h + 1).  Per column this takes 18 packed
+// FMAs with 4 probe values and one H^ value duplicated into pairs (9 duplications when every row
+// is packed over probes).  Every accumulator sums l = 0..8 in order (same rounding as scalar
+// FMAs); acc_at() reads the accumulator of (i, v).
 __device__ __forceinline__ void spmm_tile_f2(const float* X, const float* Hs, int P, int pl,
                                              float2 (&acc)[9][2]) {
 #pragma unroll
   for (int l = 0; l < 9; ++l) {
     const float4 t = *reinterpret_cast<const float4*>(X + l * P + pl);
-    const float2 x01 = make_float2(t.x, t.y), x23 = make_float2(t.z, t.w);
-    float hc[12];
+    const float xv[4] = {t.x, t.y, t.z, t.w};
+    const float4 u0 = *reinterpret_cast<const float4*>(Hs + l * 12);
+    const float4 u1 = *reinterpret_cast<const float4*>(Hs + l * 12 + 4);
+    const float h8 = Hs[l * 12 + 8];
+    const float2 hp[4] = {make_float2(u0.x, u0.y), make_float2(u0.z, u0.w), make_float2(u1.x, u1.y),
+                          make_float2(u1.z, u1.w)};
 #pragma unroll
-    for (int j = 0; j < 12; j += 4) {
-      const float4 u = *reinterpret_cast<const float4*>(Hs + l * 12 + j);
-      hc[j] = u.x; hc[j + 1] = u.y; hc[j + 2] = u.z; hc[j + 3] = u.w;
-    }
+    for (int v = 0; v < 4; ++v) {
+      const float2 x2 = make_float2(xv[v], xv[v]);
 #pragma unroll
-    for (int i = 0; i < 9; ++i) {
-      const float2 h2 = make_float2(hc[i], hc[i]);
-      acc[i][0] = __ffma2_rn(h2, x01, acc[i][0]);
-      acc[i][1] = __ffma2_rn(h2, x23, acc[i][1]);
+      for (int j = 0; j < 4; ++j) acc[2 * j + (v >> 1)][v & 1] = __ffma2_rn(hp[j], x2, acc[2 * j + (v >> 1)][v & 1]);
     }
+    const float2 h2 = make_float2(h8, h8);
+    acc[8][0] = __ffma2_rn(h2, make_float2(t.x, t.y), acc[8][0]);
+    acc[8][1] = __ffma2_rn(h2, make_float2(t.z, t.w), acc[8][1]);
   }
+}
+
+// The accumulator of row i, probe v (0..3) in the layout spmm_tile_f2 fills.
+__device__ __forceinline__ float acc_at(const float2 (&acc)[9][2], int i, int v) {
+  if (i == 8) return (v & 1) ? acc[8][v >> 1].y : acc[8][v >> 1].x;
+  const float2 p = acc[2 * (i >> 1) + (v >> 1)][v & 1];
+  return (i & 1) ? p.y : p.x;
 }
 
 }  // namespace tbk

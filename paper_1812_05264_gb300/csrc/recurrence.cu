@@ -12,6 +12,32 @@ template <typename T> struct Vec16;
 template <> struct Vec16<float> { using type = float4; static constexpr int N = 4; };
 template <> struct Vec16<double> { using type = double2; static constexpr int N = 2; };
 
+// The order in which the stored blocks of row a enter its block product: the off-diagonal blocks
+// in stored order, then the diagonal block (a, a).  Every step kernel sums in this order, so that
+// they agree to the bit on y_{k+1}; the TMA-fed kernel receives the tile of the row's own y_k last
+// and keeps it in shared memory for the moment partials.  next() returns the stored index of the
+// next block and sets b to its column.  Each call reads col at most twice, within k0 .. k1 - 1,
+// and the diagonal is moved at most once (a pattern without one keeps its stored order).
+struct DiagLast {
+  int kn, kd, left;  // next stored index; the diagonal's index once passed (-1 before); blocks left
+  __device__ __forceinline__ DiagLast(int k0, int k1) : kn(k0), kd(-1), left(k1 - k0) {}
+  __device__ __forceinline__ int next(const int32_t* __restrict__ col, int a, int& b) {
+    if (--left == 0) {
+      const int k = kd >= 0 ? kd : kn;
+      b = __ldg(col + k);
+      return k;
+    }
+    int k = kn++;
+    b = __ldg(col + k);
+    if (kd < 0 && b == a) {
+      kd = k;
+      k = kn++;
+      b = __ldg(col + k);
+    }
+    return k;
+  }
+};
+
 template <typename T>
 __device__ __forceinline__ void ld16(const T* p, T* x) {
   if constexpr (sizeof(T) == 4) {
@@ -135,9 +161,11 @@ cheb_step_kernel(const int n_atoms, const int32_t* __restrict__ row_ptr,
       for (int i = 0; i < B; ++i)
 #pragma unroll
         for (int v = 0; v < VEC; ++v) acc[i][v] = T(0);
-      const int k1 = __ldg(row_ptr + a + 1);
-      for (int k = __ldg(row_ptr + a); k < k1; ++k) {
-        const int b = __ldg(col + k);
+      const int k0 = __ldg(row_ptr + a), k1 = __ldg(row_ptr + a + 1);
+      DiagLast order(k0, k1);
+      for (int q = 0; q < k1 - k0; ++q) {
+        int b;
+        const int k = order.next(col, a, b);
         T x[B][VEC];
 #pragma unroll
         for (int l = 0; l < B; ++l) {
@@ -252,10 +280,11 @@ cheb_step_kernel(const int n_atoms, const int32_t* __restrict__ row_ptr,
 // P = 128 CW probes (each consumer thread owns 4 consecutive probes).  The producer streams, for
 // every neighbour block k = (a, b) of the task, the 9 x P tile of y_in rows 9b..9b+8 and the
 // block H^_ab through a (D + 1)-stage shared-memory ring with cp.async.bulk copies completing on
-// mbarriers, and the y_prev tile of the row last.  The row's own y_in values, needed for the
-// moment sum, are read back from global memory in the epilogue (the tile was just copied, so
-// they are normally in L2).  Every wait is bounded: on expiry the CTA raises *err = 2 and leaves
-// the loop, and the producer waits (bounded) for the copies it issued before returning.
+// mbarriers, in DiagLast order (the diagonal block last), then the y_prev tile of the row.  The
+// consumers keep the last two stages (the row's own y_in tile, needed for the moment sums, and
+// y_prev) until the epilogue has read them, so the epilogue reads nothing from global memory but
+// the probe signs it regenerates.  Every wait is bounded: on expiry the CTA raises *err = 2 and
+// leaves the loop, and the producer waits (bounded) for the copies it issued before returning.
 
 template <int CW, int D>
 struct BulkCfg {
@@ -275,9 +304,10 @@ cheb_step_bulk(const int n_atoms, const int32_t* __restrict__ row_ptr, const int
                const int direct, double* __restrict__ partials, int* __restrict__ err,
                const BatchRows batch, const int per_task, const int stall) {
   using C = BulkCfg<CW, D>;
-  // every tile, the diagonal one included, streams through a ring of R = D + 1 stages; the
-  // epilogue reads the row's own y_in values (for the moment partials) from global memory
+  // every tile, the diagonal one included, streams through a ring of R = D + 1 stages (R >= 2:
+  // the epilogue holds two)
   constexpr int R = D + 1;
+  static_assert(R >= 2, "the epilogue holds two stages");
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + R * C::SB);
   // bars: full[0..R), empty[R..2R)
@@ -307,9 +337,11 @@ cheb_step_bulk(const int n_atoms, const int32_t* __restrict__ row_ptr, const int
         const int a = task / n_chunks, ch = task - a * n_chunks;
         const int k0 = __ldg(row_ptr + a), k1 = __ldg(row_ptr + a + 1);
         const int nt = k1 - k0 + (has_prev ? 1 : 0);
+        DiagLast order(k0, k1);
         for (int q = 0; q < nt && ok; ++q) {
           const bool is_prev = q == k1 - k0;
-          const int b = is_prev ? a : __ldg(col + k0 + q);
+          int b = a, k = 0;
+          if (!is_prev) k = order.next(col, a, b);
           const int st = it % R;
           ok = mbar_wait(empty(st), ((it / R) & 1) ^ 1);
           if (!ok) break;
@@ -322,7 +354,7 @@ cheb_step_bulk(const int n_atoms, const int32_t* __restrict__ row_ptr, const int
           } else {
             for (int l = 0; l < 9; ++l) bulk_g2s(dst + l * C::P * 4, src + (int64_t)l * s, C::P * 4, bar);
           }
-          if (!is_prev) bulk_g2s(dst + C::XB, hv + (int64_t)(k0 + q) * Layout<float, 9>::BS, C::HB, bar);
+          if (!is_prev) bulk_g2s(dst + C::XB, hv + (int64_t)k * Layout<float, 9>::BS, C::HB, bar);
         }
       }
       if (!ok) {
@@ -335,6 +367,9 @@ cheb_step_bulk(const int n_atoms, const int32_t* __restrict__ row_ptr, const int
   }
 
   // ---------------- consumers ----------------
+  // The last neighbour tile of a task is the diagonal block's, i.e. the row's own y_k, and the
+  // y_prev tile follows it: both stay in the ring (their stages are released after the epilogue,
+  // in order) and the epilogue reads them from shared memory.
   double sum0 = 0.0, sum1 = 0.0;
   int it = 0;
   bool ok = true;
@@ -342,11 +377,13 @@ cheb_step_bulk(const int n_atoms, const int32_t* __restrict__ row_ptr, const int
   for (int task = blockIdx.x; task < n_tasks && ok; task += gridDim.x) {
     const int a = task / n_chunks, ch = task - a * n_chunks;
     const int k0 = __ldg(row_ptr + a), k1 = __ldg(row_ptr + a + 1);
+    const int nb = k1 - k0;
     const int pl = 4 * threadIdx.x;  // probe offset inside the chunk
-    float2 acc[9][2];  // acc[i][h] = row i for probes (2h, 2h + 1)
+    float2 acc[9][2];  // row i, probe v: acc_at(acc, i, v)
 #pragma unroll
     for (int i = 0; i < 9; ++i) acc[i][0] = acc[i][1] = make_float2(0.f, 0.f);
-    for (int q = 0; q < k1 - k0; ++q) {
+    int held = 0;  // stages held for the epilogue, starting at it - held
+    for (int q = 0; q < nb; ++q) {
       const int st = it % R;
       if (!rdy) ok = mbar_wait(full(st), (it / R) & 1);
       ok = __all_sync(0xffffffffu, ok);  // one decision per warp: the warps meet at a barrier below
@@ -356,27 +393,25 @@ cheb_step_bulk(const int n_atoms, const int32_t* __restrict__ row_ptr, const int
       const float* X = reinterpret_cast<const float*>(base);
       const float* Hs = reinterpret_cast<const float*>(base + C::XB);
       spmm_tile_f2(X, Hs, C::P, pl, acc);
-      __syncwarp();
-      if (lane == 0) mbar_arrive(empty(st));
+      if (q == nb - 1) {
+        held = 1;  // the diagonal block's tile: the row's own y_k
+      } else {
+        __syncwarp();
+        if (lane == 0) mbar_arrive(empty(st));
+      }
       ++it;
     }
     if (!ok) break;
-    // previous panel tile of this row (streamed last)
-    float yp[9][4];
+    const float* Xown = held ? reinterpret_cast<const float*>(smem + ((it - 1) % R) * C::SB) : nullptr;
+    const float* Xprev = nullptr;
     if (has_prev) {
       const int st = it % R;
       if (!rdy) ok = mbar_wait(full(st), (it / R) & 1);
       ok = __all_sync(0xffffffffu, ok);  // one decision per warp: the warps meet at a barrier below
       if (!ok) break;
       rdy = mbar_test(full((it + 1) % R), ((it + 1) / R) & 1);
-      const float* X = reinterpret_cast<const float*>(smem + st * C::SB);
-#pragma unroll
-      for (int l = 0; l < 9; ++l) {
-        const float4 t = *reinterpret_cast<const float4*>(X + l * C::P + pl);
-        yp[l][0] = t.x; yp[l][1] = t.y; yp[l][2] = t.z; yp[l][3] = t.w;
-      }
-      __syncwarp();
-      if (lane == 0) mbar_arrive(empty(st));
+      Xprev = reinterpret_cast<const float*>(smem + st * C::SB);
+      ++held;
       ++it;
     }
     // epilogue: y_out = alpha acc + c_r r - y_prev, moment partial sums
@@ -393,7 +428,7 @@ cheb_step_bulk(const int n_atoms, const int32_t* __restrict__ row_ptr, const int
       const int64_t row = (int64_t)9 * a + i;
       float yo[4], r[4];
 #pragma unroll
-      for (int v = 0; v < 4; ++v) yo[v] = alpha * ((v & 1) ? acc[i][v >> 1].y : acc[i][v >> 1].x);
+      for (int v = 0; v < 4; ++v) yo[v] = alpha * acc_at(acc, i, v);
       if (c_r != 0.f || direct) {
 #pragma unroll
         for (int v = 0; v < 4; ++v) r[v] = tbk_probe_sign(sd, rloc + i, p0 + v);
@@ -402,9 +437,9 @@ cheb_step_bulk(const int n_atoms, const int32_t* __restrict__ row_ptr, const int
 #pragma unroll
         for (int v = 0; v < 4; ++v) yo[v] = fmaf(c_r, r[v], yo[v]);
       }
-      if (has_prev) {
-#pragma unroll
-        for (int v = 0; v < 4; ++v) yo[v] -= yp[i][v];
+      if (Xprev) {
+        const float4 t = *reinterpret_cast<const float4*>(Xprev + i * C::P + pl);
+        yo[0] -= t.x; yo[1] -= t.y; yo[2] -= t.z; yo[3] -= t.w;
       }
       *reinterpret_cast<float4*>(yout + row * s + p0) = make_float4(yo[0], yo[1], yo[2], yo[3]);
       if (partials) {
@@ -413,7 +448,10 @@ cheb_step_bulk(const int n_atoms, const int32_t* __restrict__ row_ptr, const int
 #pragma unroll
           for (int v = 0; v < 4; ++v) xin[v] = r[v];
         } else {
-          const float4 t = __ldg(reinterpret_cast<const float4*>(yin + row * s + p0));
+          // the row's own y_k: from the held diagonal tile (every valid row stores its diagonal
+          // block, and it is the last one streamed)
+          const float4 t = Xown ? *reinterpret_cast<const float4*>(Xown + i * C::P + pl)
+                                : __ldg(reinterpret_cast<const float4*>(yin + row * s + p0));
           xin[0] = t.x; xin[1] = t.y; xin[2] = t.z; xin[3] = t.w;
         }
         float q0 = 0.f, q1 = 0.f;
@@ -426,6 +464,10 @@ cheb_step_bulk(const int n_atoms, const int32_t* __restrict__ row_ptr, const int
         sum1 += (double)q1;
       }
     }
+    // release the held stages in ring order
+    __syncwarp();
+    if (lane == 0)
+      for (int h = held; h > 0; --h) mbar_arrive(empty((it - h) % R));
     if (per_task && partials) {
       // per (atom, warp) partial sums: no barrier between warps is needed
       for (int o = 16; o > 0; o >>= 1) {
@@ -501,12 +543,15 @@ cheb_step_self(const int n_atoms, const int32_t* __restrict__ row_ptr, const int
   }
   __syncwarp();
   // producer cursor (lane 0): the next tile to issue, as (task, tile index within the task)
-  int p_task = blockIdx.x, p_q = 0, p_nt = 0, p_k0 = 0, issued = 0;
+  // (the neighbour tiles of a task in DiagLast order, the same sums as every other step kernel)
+  int p_task = blockIdx.x, p_q = 0, p_nt = 0, issued = 0;
+  DiagLast p_order(0, 0);
   auto load_task = [&]() {  // tasks with no tile (an empty row, no y_{k-1}) are skipped
     for (; p_task < n_tasks; p_task += gridDim.x) {
       const int a = p_task / n_chunks;
-      p_k0 = __ldg(row_ptr + a);
-      p_nt = __ldg(row_ptr + a + 1) - p_k0 + (has_prev ? 1 : 0);
+      const int k0 = __ldg(row_ptr + a), k1 = __ldg(row_ptr + a + 1);
+      p_order = DiagLast(k0, k1);
+      p_nt = k1 - k0 + (has_prev ? 1 : 0);
       if (p_nt > 0) break;
     }
   };
@@ -514,7 +559,8 @@ cheb_step_self(const int n_atoms, const int32_t* __restrict__ row_ptr, const int
     if (stall || p_task >= n_tasks) return;
     const int a = p_task / n_chunks, ch = p_task - a * n_chunks;
     const bool is_prev = p_q == p_nt - (has_prev ? 1 : 0) && has_prev;
-    const int b = is_prev ? a : __ldg(col + p_k0 + p_q);
+    int b = a, k = 0;
+    if (!is_prev) k = p_order.next(col, a, b);
     const int st = issued % R;
     const uint32_t dst = smem_u32(smem + st * C::SB), bar = full(st);
     const float* src = (is_prev ? yprev : yin) + (int64_t)9 * b * s + (int64_t)ch * C::P;
@@ -525,7 +571,7 @@ cheb_step_self(const int n_atoms, const int32_t* __restrict__ row_ptr, const int
     } else {
       for (int l = 0; l < 9; ++l) bulk_g2s(dst + l * C::P * 4, src + (int64_t)l * s, C::P * 4, bar);
     }
-    if (!is_prev) bulk_g2s(dst + C::XB, hv + (int64_t)(p_k0 + p_q) * Layout<float, 9>::BS, C::HB, bar);
+    if (!is_prev) bulk_g2s(dst + C::XB, hv + (int64_t)k * Layout<float, 9>::BS, C::HB, bar);
     ++issued;
     if (++p_q == p_nt) {
       p_task += gridDim.x;
@@ -598,7 +644,7 @@ cheb_step_self(const int n_atoms, const int32_t* __restrict__ row_ptr, const int
       const int64_t row = (int64_t)9 * a + i;
       float yo[4], r[4];
 #pragma unroll
-      for (int v = 0; v < 4; ++v) yo[v] = alpha * ((v & 1) ? acc[i][v >> 1].y : acc[i][v >> 1].x);
+      for (int v = 0; v < 4; ++v) yo[v] = alpha * acc_at(acc, i, v);
       if (c_r != 0.f || direct) {
 #pragma unroll
         for (int v = 0; v < 4; ++v) r[v] = tbk_probe_sign(sd, rloc + i, p0 + v);

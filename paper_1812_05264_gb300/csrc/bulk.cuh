@@ -106,6 +106,18 @@ __device__ __forceinline__ void spmm_tile_f2(const float* X, const float* Hs, in
   }
 }
 
+// Compensated FP32 accumulation (Knuth's TwoSum): s + c carries the running sum of the q's with
+// each addition's rounding error kept in c, so that (double)s + (double)c matches an FP64 sum of
+// the q's to ~n 2^-48 relative.  Used for a task's moment partials, which then take one FP64
+// conversion and add per task instead of one per row (FP64 is a 1/64-rate pipe on this part).
+__device__ __forceinline__ void two_sum_acc(float& s, float& c, float q) {
+  const float t = __fadd_rn(s, q);
+  const float bb = __fsub_rn(t, s);
+  const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bb)), __fsub_rn(q, bb));
+  s = t;
+  c = __fadd_rn(c, err);
+}
+
 // The accumulator of row i, probe v (0..3) in the layout spmm_tile_f2 fills.
 __device__ __forceinline__ float acc_at(const float2 (&acc)[9][2], int i, int v) {
   if (i == 8) return (v & 1) ? acc[8][v >> 1].y : acc[8][v >> 1].x;

@@ -12,32 +12,6 @@ template <typename T> struct Vec16;
 template <> struct Vec16<float> { using type = float4; static constexpr int N = 4; };
 template <> struct Vec16<double> { using type = double2; static constexpr int N = 2; };
 
-// The order in which the stored blocks of row a enter its block product: the off-diagonal blocks
-// in stored order, then the diagonal block (a, a).  Every step kernel sums in this order, so that
-// they agree to the bit on y_{k+1}; the TMA-fed kernel receives the tile of the row's own y_k last
-// and keeps it in shared memory for the moment partials.  next() returns the stored index of the
-// next block and sets b to its column.  Each call reads col at most twice, within k0 .. k1 - 1,
-// and the diagonal is moved at most once (a pattern without one keeps its stored order).
-struct DiagLast {
-  int kn, kd, left;  // next stored index; the diagonal's index once passed (-1 before); blocks left
-  __device__ __forceinline__ DiagLast(int k0, int k1) : kn(k0), kd(-1), left(k1 - k0) {}
-  __device__ __forceinline__ int next(const int32_t* __restrict__ col, int a, int& b) {
-    if (--left == 0) {
-      const int k = kd >= 0 ? kd : kn;
-      b = __ldg(col + k);
-      return k;
-    }
-    int k = kn++;
-    b = __ldg(col + k);
-    if (kd < 0 && b == a) {
-      kd = k;
-      k = kn++;
-      b = __ldg(col + k);
-    }
-    return k;
-  }
-};
-
 template <typename T>
 __device__ __forceinline__ void ld16(const T* p, T* x) {
   if constexpr (sizeof(T) == 4) {
@@ -161,11 +135,9 @@ cheb_step_kernel(const int n_atoms, const int32_t* __restrict__ row_ptr,
       for (int i = 0; i < B; ++i)
 #pragma unroll
         for (int v = 0; v < VEC; ++v) acc[i][v] = T(0);
-      const int k0 = __ldg(row_ptr + a), k1 = __ldg(row_ptr + a + 1);
-      DiagLast order(k0, k1);
-      for (int q = 0; q < k1 - k0; ++q) {
-        int b;
-        const int k = order.next(col, a, b);
+      const int k1 = __ldg(row_ptr + a + 1);
+      for (int k = __ldg(row_ptr + a); k < k1; ++k) {
+        const int b = __ldg(col + k);
         T x[B][VEC];
 #pragma unroll
         for (int l = 0; l < B; ++l) {
@@ -280,11 +252,13 @@ cheb_step_kernel(const int n_atoms, const int32_t* __restrict__ row_ptr,
 // P = 128 CW probes (each consumer thread owns 4 consecutive probes).  The producer streams, for
 // every neighbour block k = (a, b) of the task, the 9 x P tile of y_in rows 9b..9b+8 and the
 // block H^_ab through a (D + 1)-stage shared-memory ring with cp.async.bulk copies completing on
-// mbarriers, in DiagLast order (the diagonal block last), then the y_prev tile of the row.  The
-// consumers keep the last two stages (the row's own y_in tile, needed for the moment sums, and
-// y_prev) until the epilogue has read them, so the epilogue reads nothing from global memory but
-// the probe signs it regenerates.  Every wait is bounded: on expiry the CTA raises *err = 2 and
-// leaves the loop, and the producer waits (bounded) for the copies it issued before returning.
+// mbarriers, in stored order, then the row's own y_in tile a second time (when the moment sums
+// need it) and the y_prev tile.  The consumers keep those last two stages until the epilogue
+// has read them, so the epilogue reads nothing from global memory but the probe signs it
+// regenerates (the second copy of the own tile is normally an L2 hit; holding the first one
+// instead would stall the ring in the middle of the row).  Every wait is bounded: on expiry the
+// CTA raises *err = 2 and leaves the loop, and the producer waits (bounded) for the copies it
+// issued before returning.
 
 template <int CW, int D>
 struct BulkCfg {
@@ -318,6 +292,7 @@ cheb_step_bulk(const int n_atoms, const int32_t* __restrict__ row_ptr, const int
   const int n_chunks = s / C::P;
   const int n_tasks = n_atoms * n_chunks;
   const bool has_prev = yprev != nullptr;
+  const bool own = partials != nullptr && !direct;  // the moment sums read the row's own y_in
   if (threadIdx.x == 0) {
     for (int i = 0; i < R; ++i) {
       mbar_init(full(i), 1);
@@ -336,25 +311,27 @@ cheb_step_bulk(const int n_atoms, const int32_t* __restrict__ row_ptr, const int
       for (int task = blockIdx.x; task < n_tasks && ok; task += gridDim.x) {
         const int a = task / n_chunks, ch = task - a * n_chunks;
         const int k0 = __ldg(row_ptr + a), k1 = __ldg(row_ptr + a + 1);
-        const int nt = k1 - k0 + (has_prev ? 1 : 0);
-        DiagLast order(k0, k1);
+        const int nb = k1 - k0;
+        const int nt = nb + (own ? 1 : 0) + (has_prev ? 1 : 0);
         for (int q = 0; q < nt && ok; ++q) {
-          const bool is_prev = q == k1 - k0;
-          int b = a, k = 0;
-          if (!is_prev) k = order.next(col, a, b);
+          // tiles: the nb neighbour tiles with their blocks, then the row's own y_in tile again
+          // (own: for the moment sums), then y_prev
+          const bool is_nb = q < nb, is_prev = q == nt - 1 && has_prev;
+          const int k = k0 + q;
+          const int b = is_nb ? __ldg(col + k) : a;
           const int st = it % R;
           ok = mbar_wait(empty(st), ((it / R) & 1) ^ 1);
           if (!ok) break;
           const uint32_t dst = smem_u32(smem + st * C::SB), bar = full(st);
           ++it;
           const float* src = (is_prev ? yprev : yin) + (int64_t)9 * b * s + (int64_t)ch * C::P;
-          mbar_expect_tx(bar, C::XB + (is_prev ? 0 : C::HB));
+          mbar_expect_tx(bar, C::XB + (is_nb ? C::HB : 0));
           if (C::P == s) {
             bulk_g2s(dst, src, C::XB, bar);
           } else {
             for (int l = 0; l < 9; ++l) bulk_g2s(dst + l * C::P * 4, src + (int64_t)l * s, C::P * 4, bar);
           }
-          if (!is_prev) bulk_g2s(dst + C::XB, hv + (int64_t)k * Layout<float, 9>::BS, C::HB, bar);
+          if (is_nb) bulk_g2s(dst + C::XB, hv + (int64_t)k * Layout<float, 9>::BS, C::HB, bar);
         }
       }
       if (!ok) {
@@ -367,9 +344,9 @@ cheb_step_bulk(const int n_atoms, const int32_t* __restrict__ row_ptr, const int
   }
 
   // ---------------- consumers ----------------
-  // The last neighbour tile of a task is the diagonal block's, i.e. the row's own y_k, and the
-  // y_prev tile follows it: both stay in the ring (their stages are released after the epilogue,
-  // in order) and the epilogue reads them from shared memory.
+  // After the neighbour tiles come the row's own y_k tile (own) and the y_prev tile: both stay in
+  // the ring (their stages are released after the epilogue, in order) and the epilogue reads them
+  // from shared memory.
   double sum0 = 0.0, sum1 = 0.0;
   int it = 0;
   bool ok = true;
@@ -393,17 +370,23 @@ cheb_step_bulk(const int n_atoms, const int32_t* __restrict__ row_ptr, const int
       const float* X = reinterpret_cast<const float*>(base);
       const float* Hs = reinterpret_cast<const float*>(base + C::XB);
       spmm_tile_f2(X, Hs, C::P, pl, acc);
-      if (q == nb - 1) {
-        held = 1;  // the diagonal block's tile: the row's own y_k
-      } else {
-        __syncwarp();
-        if (lane == 0) mbar_arrive(empty(st));
-      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(empty(st));
       ++it;
     }
     if (!ok) break;
-    const float* Xown = held ? reinterpret_cast<const float*>(smem + ((it - 1) % R) * C::SB) : nullptr;
+    const float* Xown = nullptr;
     const float* Xprev = nullptr;
+    if (own) {
+      const int st = it % R;
+      if (!rdy) ok = mbar_wait(full(st), (it / R) & 1);
+      ok = __all_sync(0xffffffffu, ok);  // one decision per warp: the warps meet at a barrier below
+      if (!ok) break;
+      rdy = mbar_test(full((it + 1) % R), ((it + 1) / R) & 1);
+      Xown = reinterpret_cast<const float*>(smem + st * C::SB);
+      ++held;
+      ++it;
+    }
     if (has_prev) {
       const int st = it % R;
       if (!rdy) ok = mbar_wait(full(st), (it / R) & 1);
@@ -449,8 +432,8 @@ cheb_step_bulk(const int n_atoms, const int32_t* __restrict__ row_ptr, const int
 #pragma unroll
           for (int v = 0; v < 4; ++v) xin[v] = r[v];
         } else {
-          // the row's own y_k: from the held diagonal tile (every valid row stores its diagonal
-          // block, and it is the last one streamed)
+          // the row's own y_k from its held tile (Xown is set whenever these sums run: the global
+          // read is never taken, but with it the kernel compiles to 96 registers without spills)
           const float4 t = Xown ? *reinterpret_cast<const float4*>(Xown + i * C::P + pl)
                                 : __ldg(reinterpret_cast<const float4*>(yin + row * s + p0));
           xin[0] = t.x; xin[1] = t.y; xin[2] = t.z; xin[3] = t.w;
@@ -548,15 +531,12 @@ cheb_step_self(const int n_atoms, const int32_t* __restrict__ row_ptr, const int
   }
   __syncwarp();
   // producer cursor (lane 0): the next tile to issue, as (task, tile index within the task)
-  // (the neighbour tiles of a task in DiagLast order, the same sums as every other step kernel)
-  int p_task = blockIdx.x, p_q = 0, p_nt = 0, issued = 0;
-  DiagLast p_order(0, 0);
+  int p_task = blockIdx.x, p_q = 0, p_nt = 0, p_k0 = 0, issued = 0;
   auto load_task = [&]() {  // tasks with no tile (an empty row, no y_{k-1}) are skipped
     for (; p_task < n_tasks; p_task += gridDim.x) {
       const int a = p_task / n_chunks;
-      const int k0 = __ldg(row_ptr + a), k1 = __ldg(row_ptr + a + 1);
-      p_order = DiagLast(k0, k1);
-      p_nt = k1 - k0 + (has_prev ? 1 : 0);
+      p_k0 = __ldg(row_ptr + a);
+      p_nt = __ldg(row_ptr + a + 1) - p_k0 + (has_prev ? 1 : 0);
       if (p_nt > 0) break;
     }
   };
@@ -564,8 +544,7 @@ cheb_step_self(const int n_atoms, const int32_t* __restrict__ row_ptr, const int
     if (stall || p_task >= n_tasks) return;
     const int a = p_task / n_chunks, ch = p_task - a * n_chunks;
     const bool is_prev = p_q == p_nt - (has_prev ? 1 : 0) && has_prev;
-    int b = a, k = 0;
-    if (!is_prev) k = p_order.next(col, a, b);
+    const int b = is_prev ? a : __ldg(col + p_k0 + p_q);
     const int st = issued % R;
     const uint32_t dst = smem_u32(smem + st * C::SB), bar = full(st);
     const float* src = (is_prev ? yprev : yin) + (int64_t)9 * b * s + (int64_t)ch * C::P;
@@ -576,7 +555,7 @@ cheb_step_self(const int n_atoms, const int32_t* __restrict__ row_ptr, const int
     } else {
       for (int l = 0; l < 9; ++l) bulk_g2s(dst + l * C::P * 4, src + (int64_t)l * s, C::P * 4, bar);
     }
-    if (!is_prev) bulk_g2s(dst + C::XB, hv + (int64_t)k * Layout<float, 9>::BS, C::HB, bar);
+    if (!is_prev) bulk_g2s(dst + C::XB, hv + (int64_t)(p_k0 + p_q) * Layout<float, 9>::BS, C::HB, bar);
     ++issued;
     if (++p_q == p_nt) {
       p_task += gridDim.x;
@@ -604,7 +583,7 @@ cheb_step_self(const int n_atoms, const int32_t* __restrict__ row_ptr, const int
   for (int task = blockIdx.x; task < n_tasks && ok; task += gridDim.x) {
     const int a = task / n_chunks, ch = task - a * n_chunks;
     const int k0 = __ldg(row_ptr + a), k1 = __ldg(row_ptr + a + 1);
-    float2 acc[9][2];
+    float2 acc[9][2];  // row i, probe v: acc_at_pp(acc, i, v)
 #pragma unroll
     for (int i = 0; i < 9; ++i) acc[i][0] = acc[i][1] = make_float2(0.f, 0.f);
     for (int q = 0; q < k1 - k0; ++q) {
@@ -615,8 +594,8 @@ cheb_step_self(const int n_atoms, const int32_t* __restrict__ row_ptr, const int
       }
       rdy = mbar_test(full((it + 1) % R), ((it + 1) / R) & 1);
       const unsigned char* base = smem + st * C::SB;
-      spmm_tile_f2(reinterpret_cast<const float*>(base), reinterpret_cast<const float*>(base + C::XB), C::P,
-                   pl, acc);
+      spmm_tile_f2_pp(reinterpret_cast<const float*>(base), reinterpret_cast<const float*>(base + C::XB), C::P,
+                      pl, acc);
       consumed();
     }
     if (!ok) break;
@@ -644,13 +623,12 @@ cheb_step_self(const int n_atoms, const int32_t* __restrict__ row_ptr, const int
       sd = __ldg(batch.seed + cl);
       rloc = (int64_t)9 * (a - __ldg(batch.atom0 + cl));
     }
-    float cs0 = 0.f, cc0 = 0.f, cs1 = 0.f, cc1 = 0.f;  // the task's compensated partial sums
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
       const int64_t row = (int64_t)9 * a + i;
       float yo[4], r[4];
 #pragma unroll
-      for (int v = 0; v < 4; ++v) yo[v] = alpha * acc_at(acc, i, v);
+      for (int v = 0; v < 4; ++v) yo[v] = alpha * acc_at_pp(acc, i, v);
       if (c_r != 0.f || direct) {
 #pragma unroll
         for (int v = 0; v < 4; ++v) r[v] = tbk_probe_sign(sd, rloc + i, p0 + v);
@@ -679,13 +657,9 @@ cheb_step_self(const int n_atoms, const int32_t* __restrict__ row_ptr, const int
           q0 = fmaf(yo[v], xin[v], q0);
           q1 = fmaf(yo[v], yo[v], q1);
         }
-        two_sum_acc(cs0, cc0, q0);
-        two_sum_acc(cs1, cc1, q1);
+        sum0 += (double)q0;
+        sum1 += (double)q1;
       }
-    }
-    if (partials) {
-      sum0 += (double)cs0 + (double)cc0;
-      sum1 += (double)cs1 + (double)cc1;
     }
     if (per_task && partials) {
       for (int o = 16; o > 0; o >>= 1) {

@@ -582,3 +582,18 @@ def test_autotune_choice_keeps_the_results(api):
     _, F = oracle_estimator_forces(wk, rp, col, est, res.emin, res.emax, 40)
     assert np.abs(F1.cpu().numpy() - F).max() < 1e-3
     ctx2.close()
+
+
+@pytest.mark.parametrize("s", [128, 256, 512])
+def test_every_step_kernel_forms_the_same_panels(api, ctx, s):
+    """The plain, self-fed (128-probe tasks) and TMA-fed (256/512) FP32 step kernels sum each
+    row's blocks in stored order and each block's columns l = 0..8 in order, so they form the
+    same y_k to the bit: the per-probe moments, computed from the panels by the same reduction,
+    are equal bit for bit (doubled and direct)."""
+    wk = small_fcc(60, n_probes=s, jitter=0.05)
+    sv, pos, res = _gpu_run(api, ctx, wk, 20, fp64=False)
+    args = (ctx, res.H, res.emin, res.emax, wk.probe_seed, s, 57)
+    for direct in (False, True):
+        _, per = api.chebyshev_probe_moments(*args, direct=direct)
+        _, per_plain = api.chebyshev_probe_moments(*args, direct=direct, plain=True)
+        assert torch.equal(per, per_plain), direct

@@ -98,12 +98,22 @@ __device__ __forceinline__ void spmm_tile_f2(const float* X, const float* Hs, in
     for (int v = 0; v < 4; ++v) {
       const float2 x2 = make_float2(xv[v], xv[v]);
 #pragma unroll
-      for (int j = 0; j < 4; ++j) acc[2 * j + (v >> 1)][v & 1] = __ffma2_rn(hp[j], x2, acc[2 * j + (v >> 1)][v & 1]);
+      for (int j = 0; j < 4; ++j) {
+        float2& a = acc[2 * j + (v >> 1)][v & 1];
+        a = __ffma2_rn(hp[j], x2, a);
+      }
     }
     const float2 h2 = make_float2(h8, h8);
     acc[8][0] = __ffma2_rn(h2, make_float2(t.x, t.y), acc[8][0]);
     acc[8][1] = __ffma2_rn(h2, make_float2(t.z, t.w), acc[8][1]);
   }
+}
+
+// The accumulator of row i, probe v (0..3) in the layout spmm_tile_f2 fills.
+__device__ __forceinline__ float acc_at(const float2 (&acc)[9][2], int i, int v) {
+  if (i == 8) return (v & 1) ? acc[8][v >> 1].y : acc[8][v >> 1].x;
+  const float2 p = acc[2 * (i >> 1) + (v >> 1)][v & 1];
+  return (i & 1) ? p.y : p.x;
 }
 
 // The same tile product with every row packed over probe pairs: acc[i][h] += H^[i][l] *
@@ -146,13 +156,6 @@ __device__ __forceinline__ void two_sum_acc(float& s, float& c, float q) {
   const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bb)), __fsub_rn(q, bb));
   s = t;
   c = __fadd_rn(c, err);
-}
-
-// The accumulator of row i, probe v (0..3) in the layout spmm_tile_f2 fills.
-__device__ __forceinline__ float acc_at(const float2 (&acc)[9][2], int i, int v) {
-  if (i == 8) return (v & 1) ? acc[8][v >> 1].y : acc[8][v >> 1].x;
-  const float2 p = acc[2 * (i >> 1) + (v >> 1)][v & 1];
-  return (i & 1) ? p.y : p.x;
 }
 
 }  // namespace tbk

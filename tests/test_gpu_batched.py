@@ -249,3 +249,36 @@ def test_batched_neighbor_lists_equal_single_cluster_lists(api, ctx):
     assert e.value.code == L.TBK_ERR_ARG
     assert [nnz[i] for i in range(n)] == [g.nnzb for g in gs]
     assert all(bool((c == -7).all()) for c in cols)
+
+
+@pytest.mark.parametrize("s", [256, 512])
+def test_batch_at_wide_panels(api, ctx, s):
+    """A batch at 256 and 512 probes per cluster runs the producer-warp step kernel (probe chunks of
+    256 and 512) with per-atom partial sums and the fused adjoint with per-cluster coefficients:
+    moments equal the single-cluster calls to the FP64 grouping of the partial sums (1e-9·n),
+    G and forces equal them to FP32 summation order, and energies, G and forces match the oracle."""
+    from gpu_common import oracle_estimator_forces
+    sizes, kTs = [37, 64, 21], [0.5, 0.1, 0.5]
+    b = _batch(api, ctx, sizes, kTs, s=s)
+    b = [(wk, H, e0, e1, min(p, 70 + 23 * i)) for i, (wk, H, e0, e1, p) in enumerate(b)]
+    model = api.Solver(b[0][0], ctx).model
+    Hs, e0, e1, seeds = [x[1] for x in b], [x[2] for x in b], [x[3] for x in b], [x[0].probe_seed for x in b]
+    orders, ne = [x[4] for x in b], [x[0].n_electrons for x in b]
+    pos = [torch.as_tensor(x[0].positions, dtype=torch.float64, device="cuda") for x in b]
+    mom, obs, Gs, Fs = api.batched_energies_and_forces(ctx, Hs, model, pos, e0, e1, seeds, s, orders, ne,
+                                                       kTs, want_G=True)
+    for (wk, H, lo, hi, p), m, o, G, F, ps in zip(b, mom, obs, Gs, Fs, pos):
+        n = wk.n_atoms * 9
+        ref = api.chebyshev_moments(ctx, H, lo, hi, wk.probe_seed, s, p)
+        assert np.abs(m.cpu().numpy() - ref.cpu().numpy()).max() < 1e-9 * n
+        G1, F1 = api.density_and_forces(ctx, H, model, ps, None, lo, hi, wk.probe_seed, s, p, o[0],
+                                        wk.kT, False, False, want_G=True)
+        gmax = G1.abs().max().item()
+        assert torch.allclose(G, G1, rtol=0, atol=2e-5 * gmax)
+        assert torch.allclose(F, F1, rtol=0, atol=1e-4)
+        rp, col, Hd = oracle_H(wk)
+        est = oracle_estimator(wk, Hd, lo, hi, p)
+        for j, key in ((1, "Omega"), (2, "E"), (3, "N")):
+            assert abs(o[j] - est[key]) / wk.n_atoms < 1e-4, key
+        _, Fo = oracle_estimator_forces(wk, rp, col, dict(est, mu=o[0]), lo, hi, p)
+        assert np.abs(F.cpu().numpy() - Fo).max() < 1e-3

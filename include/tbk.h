@@ -125,6 +125,11 @@ int64_t tbk_launch_count(tbk_ctx* ctx);
    and the call that launched it returns TBK_ERR_TIMEOUT.  Nothing faults; the context stays
    usable and the next calls compute normally.  Host-side only. */
 int tbk_test_stall_next_step(tbk_ctx* ctx);
+/* The same test for the fused adjoint step (the TMA-fed Clenshaw step with the sampled outer
+   products): the next such launch on ctx gets a producer that copies nothing; its consumers give
+   up after 2 s, the adjoint call returns TBK_ERR_TIMEOUT, and the context stays usable.  Host-side
+   only. */
+int tbk_test_stall_next_adjoint(tbk_ctx* ctx);
 
 /* tbk_autotune: time, on this operator (9x9 blocks, mixed precision) with n_probes a multiple
    of 128, the probe chunk (128, 256 or 512 probes) per task of the TMA-fed recurrence step and

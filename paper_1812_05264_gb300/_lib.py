@@ -73,6 +73,7 @@ SIGNATURES = {
     "tbk_create": [C.POINTER(_P), C.c_int, _P],
     "tbk_destroy": [_P],
     "tbk_test_stall_next_step": [_P],
+    "tbk_test_stall_next_adjoint": [_P],
     "tbk_autotune": [_P, C.POINTER(tbk_bsr), _D, _D, _I, C.POINTER(_I)],
     "tbk_kernel_timer": [_P, _I],
     "tbk_kernel_timer_read": [_P, _I, C.POINTER(_D), C.POINTER(_L)],

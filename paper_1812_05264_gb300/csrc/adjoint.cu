@@ -163,7 +163,7 @@ clenshaw_sddmm_bulk(const int n_atoms, const int32_t* __restrict__ row_ptr,
                     const float* __restrict__ ypan, const float4 cf, const uint64_t seed,
                     const int s, const double w, double* __restrict__ Gacc, int* __restrict__ err,
                     const BatchRows batch, const float4* __restrict__ cf_cl,
-                    const float* __restrict__ ym1, const float* __restrict__ yp1) {
+                    const float* __restrict__ ym1, const float* __restrict__ yp1, const int stall) {
   using C = SdCfg<CW, SD>;
   // every tile, the diagonal one included, streams through a ring of R = D + 1 stages
   constexpr int R = C::D + 1;
@@ -204,7 +204,8 @@ clenshaw_sddmm_bulk(const int n_atoms, const int32_t* __restrict__ row_ptr,
     if (yp1 && (any || cf.w != 0.f)) { extra_src[n_extra] = yp1; extra_kind[n_extra++] = X_YP1; }
   }
   if (warp == CW) {
-    if (lane == 0) {
+    // (stall: a test of the bounded waits; nothing is copied, the consumers give up and report)
+    if (lane == 0 && !stall) {
       int it = 0, y_it = 0;
       bool ok = true;
       for (int a = blockIdx.x; a < n_atoms && ok; a += gridDim.x) {
@@ -845,7 +846,8 @@ static void launch_fused_cw(tbk_ctx* ctx, const HOp& op, const void* bin, const 
   clenshaw_sddmm_bulk<CW, SD><<<G, C::THREADS, C::SMEM, ctx->stream>>>(
       op.n_atoms, op.row_ptr, op.col, (const float*)op.hv, (const float*)bin, (const float*)bprev,
       (float*)bout, (const float*)ypan, cf, seed, s, w, Gacc, err, batch, cf_cl, (const float*)ym1,
-      (const float*)yp1);
+      (const float*)yp1, ctx->stall_next_adjoint);
+  ctx->stall_next_adjoint = 0;
   post_launch(ctx, "clenshaw_sddmm_bulk");
 }
 

@@ -54,6 +54,7 @@ struct tbk_ctx {
   void* pinned = nullptr;        // small pinned host buffer for scalar read-back
   size_t pinned_bytes = 0;
   int stall_next_step = 0;       // test hook: the next TMA-fed step's producer issues no copies
+  int stall_next_adjoint = 0;    // test hook: the next fused adjoint step's producer issues no copies
   struct Tuned {                 // tbk_autotune's choices, per operator shape and probe count
     int64_t n_rows, nnzb;
     int s, cw, windowed;        // windowed: the outer-product schedule (0 fused, 1 windowed, 2 tensor cores)

@@ -161,6 +161,13 @@ int tbk_test_stall_next_step(tbk_ctx* ctx) {
   TBK_API_END
 }
 
+int tbk_test_stall_next_adjoint(tbk_ctx* ctx) {
+  TBK_API_BEGIN
+  TBK_CHECK_ARG(ctx != nullptr, "ctx is NULL");
+  ctx->stall_next_adjoint = 1;
+  TBK_API_END
+}
+
 int tbk_kernel_timer(tbk_ctx* ctx, int32_t mask) {
   TBK_API_BEGIN
   TBK_CHECK_ARG(ctx != nullptr, "ctx is NULL");

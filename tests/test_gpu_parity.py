@@ -597,3 +597,21 @@ def test_every_step_kernel_forms_the_same_panels(api, ctx, s):
         _, per = api.chebyshev_probe_moments(*args, direct=direct)
         _, per_plain = api.chebyshev_probe_moments(*args, direct=direct, plain=True)
         assert torch.equal(per, per_plain), direct
+
+
+def test_fused_adjoint_bounded_wait_reports_timeout_and_context_recovers(api, ctx):
+    """The fused adjoint step (producer warp, four consumer warps, 512 probes) whose producer copies
+    nothing: its consumers give up after their wall-time limit, the adjoint call returns
+    TBK_ERR_TIMEOUT, nothing faults, and the same context then computes the same G and forces."""
+    from paper_1812_05264_gb300 import _lib as L
+    wk = small_fcc(40, n_probes=512)
+    sv, pos, res = _gpu_run(api, ctx, wk, 30, fp64=False)
+    args = (ctx, res.H, sv.model, pos, None, res.emin, res.emax, wk.probe_seed, 512, 30, res.mu, wk.kT,
+            False, False)
+    G0, F0 = api.density_and_forces(*args, windowed="fused")
+    L.call("tbk_test_stall_next_adjoint", ctx.handle)
+    with pytest.raises(L.TbkError) as e:
+        api.density_and_forces(*args, windowed="fused")
+    assert e.value.code == L.TBK_ERR_TIMEOUT
+    G1, F1 = api.density_and_forces(*args, windowed="fused")
+    assert torch.equal(G0, G1) and torch.equal(F0, F1)

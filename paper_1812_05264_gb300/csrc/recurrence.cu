@@ -623,6 +623,7 @@ cheb_step_self(const int n_atoms, const int32_t* __restrict__ row_ptr, const int
       sd = __ldg(batch.seed + cl);
       rloc = (int64_t)9 * (a - __ldg(batch.atom0 + cl));
     }
+    float cs0 = 0.f, cc0 = 0.f, cs1 = 0.f, cc1 = 0.f;  // the task's compensated partial sums
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
       const int64_t row = (int64_t)9 * a + i;
@@ -657,9 +658,13 @@ cheb_step_self(const int n_atoms, const int32_t* __restrict__ row_ptr, const int
           q0 = fmaf(yo[v], xin[v], q0);
           q1 = fmaf(yo[v], yo[v], q1);
         }
-        sum0 += (double)q0;
-        sum1 += (double)q1;
+        two_sum_acc(cs0, cc0, q0);
+        two_sum_acc(cs1, cc1, q1);
       }
+    }
+    if (partials) {
+      sum0 += (double)cs0 + (double)cc0;
+      sum1 += (double)cs1 + (double)cc1;
     }
     if (per_task && partials) {
       for (int o = 16; o > 0; o >>= 1) {

@@ -615,3 +615,31 @@ def test_fused_adjoint_bounded_wait_reports_timeout_and_context_recovers(api, ct
     assert e.value.code == L.TBK_ERR_TIMEOUT
     G1, F1 = api.density_and_forces(*args, windowed="fused")
     assert torch.equal(G0, G1) and torch.equal(F0, F1)
+
+
+@pytest.mark.parametrize("s", [128, 512])
+def test_isolated_atoms_and_separate_clusters(api, ctx, s):
+    """Degenerate rows: atoms with no neighbour (their rows store only the diagonal block) and two
+    clusters far apart in one operator, through the TMA-fed step (single-warp kernel at 128 probes,
+    producer-warp kernel at 512) and the fused adjoint step, against the oracle's estimator:
+    moments within 2e-5 n, every G entry within 2e-5 of max G, forces within 1e-3 eV/A."""
+    wk = small_fcc(24, n_probes=s, kT=0.5)
+    far = wl.fcc_sphere(13, jitter=0.05, seed=3) + np.array([40.0, 0.0, 0.0])
+    iso = np.array([[0.0, 40.0, 0.0], [0.0, 0.0, 40.0], [-40.0, 0.0, 0.0]])
+    wk.positions = np.vstack([wk.positions, far, iso])
+    wk.n_electrons = 11.0 * wk.n_atoms
+    p = 60
+    rp, col, H = oracle_H(wk)
+    assert np.diff(rp).min() == 1 and np.diff(rp)[-3:].max() == 1
+    sv, pos, res = _gpu_run(api, ctx, wk, p, fp64=False)
+    est = oracle_estimator(wk, H, res.emin, res.emax, p)
+    n = H.shape[0]
+    assert np.abs(res.moments.cpu().numpy() - est["moments"]).max() < 2e-5 * n
+    Gd, Fo = oracle_estimator_forces(wk, rp, col, est, res.emin, res.emax, p)
+    G, F = api.density_and_forces(ctx, res.H, sv.model, pos, None, res.emin, res.emax, wk.probe_seed, s, p,
+                                  est["mu"], wk.kT, False, False, windowed="fused")
+    Gref = blocks_of(Gd, rp, col, 9)
+    assert np.abs(G.cpu().numpy() - Gref).max() < 2e-5 * np.abs(Gref).max()
+    assert np.abs(F.cpu().numpy() - Fo).max() < 1e-3
+    # an isolated atom feels no force
+    assert np.abs(F.cpu().numpy()[-3:]).max() < 1e-9

@@ -282,3 +282,33 @@ def test_batch_at_wide_panels(api, ctx, s):
             assert abs(o[j] - est[key]) / wk.n_atoms < 1e-4, key
         _, Fo = oracle_estimator_forces(wk, rp, col, dict(est, mu=o[0]), lo, hi, p)
         assert np.abs(F.cpu().numpy() - Fo).max() < 1e-3
+
+
+def test_batch_with_one_and_two_atom_clusters(api, ctx):
+    """Degenerate members: a one-atom cluster (one 9 x 9 block, a 9-row Krylov space for the
+    bounds) and a dimer next to a 37-atom cluster: bounds, moments, energies and forces equal the
+    single-cluster calls, the energies and forces match the oracle, and the lone atom feels no force."""
+    from gpu_common import oracle_estimator_forces
+    sizes, kTs = [1, 2, 37], [0.5, 0.1, 0.5]
+    b = _batch(api, ctx, sizes, kTs)
+    b = [(wk, H, e0, e1, min(p, 80)) for (wk, H, e0, e1, p) in b]
+    Hs = [x[1] for x in b]
+    lo, hi = api.batched_spectral_bounds(ctx, Hs)
+    for H, l_, h_ in zip(Hs, lo, hi):
+        assert (l_, h_) == api.spectral_bounds(ctx, H)
+    model = api.Solver(b[0][0], ctx).model
+    e0, e1, seeds = [x[2] for x in b], [x[3] for x in b], [x[0].probe_seed for x in b]
+    orders, ne = [x[4] for x in b], [x[0].n_electrons for x in b]
+    pos = [torch.as_tensor(x[0].positions, dtype=torch.float64, device="cuda") for x in b]
+    mom, obs, Gs, Fs = api.batched_energies_and_forces(ctx, Hs, model, pos, e0, e1, seeds, 128, orders, ne,
+                                                       kTs, want_G=True)
+    for (wk, H, l_, h_, p), m, o, G, F, ps in zip(b, mom, obs, Gs, Fs, pos):
+        ref = api.chebyshev_moments(ctx, H, l_, h_, wk.probe_seed, 128, p)
+        assert np.abs(m.cpu().numpy() - ref.cpu().numpy()).max() < 1e-9 * wk.n_atoms * 9
+        rp, col, Hd = oracle_H(wk)
+        est = oracle_estimator(wk, Hd, l_, h_, p)
+        for j, key in ((1, "Omega"), (2, "E"), (3, "N")):
+            assert abs(o[j] - est[key]) / wk.n_atoms < 1e-4, (wk.n_atoms, key)
+        _, Fo = oracle_estimator_forces(wk, rp, col, dict(est, mu=o[0]), l_, h_, p)
+        assert np.abs(F.cpu().numpy() - Fo).max() < 1e-3, wk.n_atoms
+    assert np.abs(Fs[0].cpu().numpy()).max() < 1e-12

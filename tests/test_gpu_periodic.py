@@ -76,3 +76,22 @@ def test_bloch_oracle_estimator_on_the_gpu_probes(api, ctx, lattice):
     mu = physics.chemical_potential(wk_b.ravel(), wk.n_electrons, wk.kT)
     Om, E, N = physics.observables(wk_b.ravel(), mu, wk.kT)
     assert abs(N - wk.n_electrons) < 1e-8
+
+
+@pytest.mark.parametrize("s", [128, 512])
+def test_periodic_density_matrix_mixed_fused_kernel(api, ctx, s):
+    """The benchmarked precision and kernels on the periodic lattice: G from the fused adjoint
+    step (FP32 panels, 128 and 512 probes, blocks wrapping across the cell) against the oracle's
+    Daleckii-Krein gradient of the same estimator, every entry within 2e-5 of max G."""
+    wk = wl.sc9_periodic(L=6, kT=0.05, n_probes=s, order=None)
+    rp, col, H = oracle_H(wk)
+    sv = api.Solver(wk, ctx)
+    pos = torch.as_tensor(wk.positions, dtype=torch.float64, device="cuda")
+    p = 120
+    res = sv.energies(pos, order=p, fp64=False)
+    est = oracle_estimator(wk, H, res.emin, res.emax, p)
+    G, _ = api.density_and_forces(ctx, res.H, None, None, sv.box, res.emin, res.emax, wk.probe_seed, s, p,
+                                  est["mu"], wk.kT, False, False, want_forces=False, windowed="fused")
+    Gd = och.estimator_gradient(est["w"], est["V"], est["R"], res.emin, res.emax, est["mu"], wk.kT, p=p)
+    ref = blocks_of(Gd, rp, col, 9)
+    assert np.abs(G.cpu().numpy() - ref).max() < 2e-5 * np.abs(ref).max()

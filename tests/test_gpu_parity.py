@@ -643,3 +643,28 @@ def test_isolated_atoms_and_separate_clusters(api, ctx, s):
     assert np.abs(F.cpu().numpy() - Fo).max() < 1e-3
     # an isolated atom feels no force
     assert np.abs(F.cpu().numpy()[-3:]).max() < 1e-9
+
+
+@pytest.mark.parametrize("s,sched", [(128, "fused"), (512, "fused"), (512, "windowed")])
+def test_jackson_damping_through_the_benchmarked_kernels(api, ctx, s, sched):
+    """Jackson-damped coefficients through the mixed one-call path (TMA-fed step, doubled moments,
+    fused or windowed adjoint): mu, Omega, E, N within 1e-4 eV/atom, every G entry within 2e-5 of
+    max G and forces within 1e-3 eV/A of the oracle's damped estimator."""
+    wk = small_fcc(30, n_probes=s, kT=0.5)
+    wk.jackson = True
+    p = 90
+    rp, col, H = oracle_H(wk)
+    sv, pos, res = _gpu_run(api, ctx, wk, 20, fp64=False)
+    mom, obs, G, F = api.energies_and_forces(ctx, res.H, sv.model, pos, None, res.emin, res.emax, wk.probe_seed,
+                                             s, p, wk.n_electrons, wk.kT, True, False, want_G=True,
+                                             windowed=sched)
+    est = oracle_estimator(wk, H, res.emin, res.emax, p)
+    n = wk.n_atoms
+    mu, Om, E, N = obs
+    assert abs(mu - est["mu"]) < 1e-4
+    for got, key in ((Om, "Omega"), (E, "E"), (N, "N")):
+        assert abs(got - est[key]) / n < 1e-4, key
+    Gd, Fo = oracle_estimator_forces(wk, rp, col, dict(est, mu=mu), res.emin, res.emax, p)
+    Gref = blocks_of(Gd, rp, col, 9)
+    assert np.abs(G.cpu().numpy() - Gref).max() < 2e-5 * np.abs(Gref).max()
+    assert np.abs(F.cpu().numpy() - Fo).max() < 1e-3

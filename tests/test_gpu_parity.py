@@ -381,22 +381,26 @@ def test_tensor_core_step_matches_fp32_kernels_and_oracle(api, ctx, s):
     assert abs(E - est["E"]) / wk.n_atoms < 1e-4
 
 
-def test_doubled_adjoint_checkpoints_and_orders(api, ctx):
-    """The fused (doubled-moment) adjoint: segment replays equal storing every panel, and odd and
-    even orders match the oracle's estimator forces."""
-    wk = small_fcc(30, n_probes=128, kT=0.5)
+@pytest.mark.parametrize("s", [128, 512])
+def test_doubled_adjoint_checkpoints_and_orders(api, ctx, s):
+    """The fused (doubled-moment) adjoint at 128 and 512 probes: segment replays equal storing
+    every panel, and odd and even orders (down to p = 2 and 3) match the oracle's estimator G
+    (every entry within 2e-5 of max G) and forces."""
+    wk = small_fcc(30, n_probes=s, kT=0.5)
     rp, col, H = oracle_H(wk)
     for p in (2, 3, 37, 90):
         s_, pos, res = _gpu_run(api, ctx, wk, p, fp64=False)
         est = oracle_estimator(wk, H, res.emin, res.emax, p)
-        args = (ctx, res.H, s_.model, pos, None, res.emin, res.emax, wk.probe_seed, 128, p,
+        args = (ctx, res.H, s_.model, pos, None, res.emin, res.emax, wk.probe_seed, s, p,
                 est["mu"], wk.kT, False, False)
         G1, F1 = api.density_and_forces(*args)
-        _, F = oracle_estimator_forces(wk, rp, col, est, res.emin, res.emax, p)
+        Gd, F = oracle_estimator_forces(wk, rp, col, est, res.emin, res.emax, p)
+        Gref = blocks_of(Gd, rp, col, 9)
+        assert np.abs(G1.cpu().numpy() - Gref).max() < 2e-5 * np.abs(Gref).max(), p
         assert np.abs(F1.cpu().numpy() - F).max() < 1e-3, p
         if p >= 37:
             # below the p/2 + 8 panels of the all-stored plan, above the checkpoint plan's need
-            panel = wk.n_atoms * 9 * 128 * 4
+            panel = wk.n_atoms * 9 * s * 4
             G2, F2 = api.density_and_forces(*args, max_panel_bytes=(24 if p == 37 else 30) * panel)
             assert torch.equal(G1, G2) and torch.equal(F1, F2), p
 
